@@ -1,0 +1,265 @@
+/*
+ * emri.h -- C-ABI of libemri, the GB300-native (sm_103a) batched
+ * Analytic-Kludge (AK) EMRI log-likelihood of Saltas & Oliveri,
+ * "emri_mc: A GPU-based Python code for Bayesian inference of EMRI
+ * waveforms" (arXiv:2311.17174).
+ *
+ * One likelihood evaluation follows the paper's pipeline (Sec. 3,
+ * "Overview" and "Waveform computation"): integrate the AK orbit of Eq. (1),
+ * form the detector-projected harmonic sum of Eq. (2) with the LISA response
+ * and Doppler phase, propagate with the damping Xi of Eqs. (4)-(6) and the
+ * GW-speed delay, Fourier transform, and take the noise-weighted inner
+ * product of Eq. (8) against the data.  Every step runs in the library's own
+ * CUDA kernels; there is no CPU fallback and no cuFFT/cuBLAS.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an int status (enum emri_status); on failure
+ *    emri_last_error() gives a message (thread-local, valid until the next
+ *    call on the same thread).
+ *  - The caller owns every pointer it passes: device pointers for batch
+ *    inputs and outputs (for example torch tensors), host pointers where a
+ *    parameter says "host".  The library owns contexts, datasets, workspaces
+ *    and plans and frees them in the matching destroy call.
+ *  - Calls that take a stream (cudaStream_t passed as void*, NULL = the
+ *    legacy default stream) are asynchronous on it; results are ready once
+ *    the stream has been synchronised.
+ *  - Walker parameters are structure-of-arrays, theta[EMRI_NPARAM][W]
+ *    (row p holds parameter p of every walker, W contiguous doubles), in the
+ *    order of enum emri_param.  Angles in radians, masses in solar masses,
+ *    frequencies in Hz.
+ *  - Without a usable CUDA device every call fails with EMRI_ECUDA.
+ */
+#ifndef EMRI_H
+#define EMRI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EMRI_NPARAM 16
+
+/* Parameter rows of theta (paper Sec. 2: theta = {M, mu, S, ...}; the first
+ * three are the ones the orbit needs, Sec. 3 "Extending the parameters"). */
+enum emri_param {
+  EMRI_P_M = 0,      /* central mass M [M_sun], detector frame          */
+  EMRI_P_MU = 1,     /* orbiting mass mu [M_sun]                         */
+  EMRI_P_SPIN = 2,   /* S/M^2 in [0, 1]                                  */
+  EMRI_P_E0 = 3,     /* eccentricity at t0 (at the LSO in backward mode) */
+  EMRI_P_NU0 = 4,    /* orbital frequency nu at t0 [Hz] (forward mode)   */
+  EMRI_P_PHI0 = 5,   /* orbital phase Phi at t0                          */
+  EMRI_P_GAMMA0 = 6, /* periastron angle gamma~ at t0                    */
+  EMRI_P_ALPHA0 = 7, /* Lense-Thirring angle alpha at t0                 */
+  EMRI_P_THETA_S = 8, EMRI_P_PHI_S = 9,   /* source direction (ecliptic) */
+  EMRI_P_THETA_K = 10, EMRI_P_PHI_K = 11, /* spin direction              */
+  EMRI_P_LAMBDA = 12,/* angle between L and S                            */
+  EMRI_P_Z = 13,     /* redshift                                          */
+  EMRI_P_XI0 = 14,   /* damping parameter Xi_0 of Eq. (6)                */
+  EMRI_P_ALPHA_T = 15/* GW-speed parameter alpha_T (constant) of Eq. (5) */
+};
+
+enum emri_status {
+  EMRI_OK = 0,
+  EMRI_EINVAL = 1,     /* bad argument (size, pointer, option)            */
+  EMRI_ENOMEM = 2,     /* device or host allocation failed               */
+  EMRI_EBUDGET = 3,    /* request exceeds the context's HBM budget       */
+  EMRI_EAGAIN = 4,     /* serving queue full, retry                       */
+  EMRI_ETIMEDOUT = 5,  /* poll timeout                                     */
+  EMRI_ECUDA = 6,      /* CUDA error or no device                         */
+  EMRI_ENOTFOUND = 7   /* unknown ticket / not started                    */
+};
+
+enum emri_precision {
+  EMRI_FP64 = 0,  /* every step in FP64                                    */
+  EMRI_MIXED = 1  /* orbit and phases FP64/fixed point, harmonic sum and
+                     FFT FP32, inner products accumulated in FP64           */
+};
+
+enum emri_mode {
+  EMRI_FORWARD = 0,          /* integrate forward from (nu0, e0) at t0     */
+  EMRI_BACKWARD_FROM_LSO = 1 /* last sample at the LSO with e = e0, integrate
+                                backwards (paper Sec. 3)                   */
+};
+
+/* per-walker status bits */
+#define EMRI_ST_PLUNGE 1u   /* orbit reached the LSO inside the window; the
+                               waveform is zero from that sample on        */
+#define EMRI_ST_BADPARAM 2u /* parameters outside their domain; outputs 0
+                               (lnL = -inf is not used: lnL = 0, check bit) */
+#define EMRI_ST_NONFINITE 4u/* the orbit became non-finite                 */
+
+typedef struct emri_ctx emri_ctx;
+typedef struct emri_dataset emri_dataset;
+
+/* Uniform time grid: samples t_j = t0 + j dt, j = 0..n-1 (paper Sec. 3: the
+ * orbit is an initial-value problem evaluated on a time grid). */
+typedef struct {
+  int64_t n;   /* samples per channel, a power of two in [2^10, 2^22]      */
+  double dt;   /* sampling step [s]                                        */
+  double t0;   /* time of sample 0 [s]; sets the LISA orbital phase        */
+} emri_grid;
+
+typedef struct {
+  int precision;    /* enum emri_precision                                   */
+  int n_max;        /* harmonic cutoff n_max of Eq. (2), 1..32               */
+  int doppler;      /* 1: Doppler phase modulation on, 0: off               */
+  int pn_terms;     /* 1: full AK equations; 0: Newtonian radiation reaction */
+  int mode;         /* enum emri_mode                                         */
+  int knot_spacing; /* samples per orbit knot interval (power of two, 64..
+                       1024); 0 = library default for the precision         */
+  double n_xi;      /* exponent n of Eq. (6); default 2                      */
+  double omega_m;   /* flat Lambda-CDM matter density; default 0.315         */
+  double h0;        /* Hubble constant [km/s/Mpc]; default 67.4              */
+} emri_opts;
+
+/* Fill *o with the defaults: FP64, n_max 10, Doppler on, full AK, forward,
+ * default knot spacing, n_xi 2, Omega_m 0.315, H0 67.4. */
+void emri_opts_default(emri_opts* o);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char* emri_last_error(void);
+
+/* Library version string. */
+const char* emri_version(void);
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the
+ * device memory the library holds for workspaces and resident datasets
+ * (0 = 80% of the device's free memory at creation).  Builds the FFT twiddle
+ * and quadrature tables.  *out receives the context (caller destroys). */
+int emri_ctx_create(int device, size_t hbm_budget_bytes, emri_ctx** out);
+
+/* Stop serving if running, free every workspace, table and the context. */
+int emri_ctx_destroy(emri_ctx* ctx);
+
+/* Number of CUDA kernels the library has launched on this context so far
+ * (host counter, incremented at each launch). */
+int emri_ctx_launches(const emri_ctx* ctx, int64_t* count);
+
+/* Device bytes the context holds (workspaces, tables, datasets) and its
+ * budget; either output may be NULL. */
+int emri_ctx_memory(const emri_ctx* ctx, size_t* used, size_t* budget);
+
+/* Resident dataset (paper Sec. 3: the waveform of the fiducial parameters is
+ * the mock data the sampler compares against; the PSD weights Eq. (8)).
+ *   data:  data_kind 0: packed spectrum D_k = DFT(d_I + i d_II) in natural
+ *          order, n complex doubles (interleaved re, im);
+ *          data_kind 1: time series, two channels d[2][n] doubles.
+ *          Host or device pointer; copied.
+ *   psd:   one-sided noise PSD S_n(f_k) at f_k = k/(n dt), k = 0..n/2
+ *          (n/2+1 doubles, host or device); copied.
+ *   fmin, fmax: band [Hz]; bins with fmin <= |f_k| <= fmax, excluding DC
+ *          and Nyquist, get the weight w_k = 2 dt^2 df / S_n(|f_k|), others
+ *          zero, so that sum_k w_k Re(conj(A_k) B_k) over all n bins is the
+ *          one-sided 4 Re sum a~* b~ / S_n df of the two channels.
+ * The dataset lives in device memory counted against the HBM budget. */
+int emri_dataset_create(emri_ctx* ctx, const emri_grid* grid, const void* data, int data_kind,
+                        const double* psd, double fmin, double fmax, emri_dataset** out);
+int emri_dataset_destroy(emri_dataset* ds);
+
+/* <d|d> of the dataset (host double). */
+int emri_dataset_dd(const emri_dataset* ds, double* dd_out);
+
+/* Per-walker propagation constants (step S0; Eqs. (4)-(6)) into
+ * out_dev[6][W] (device): d_L [cm], Xi, d_GW = Xi d_L [cm],
+ * dt_GW = -(alpha_T/2) t_lookback(z) [s], r_hi, r_lo with
+ * r = frac(dt_GW / (n dt)) split into two doubles. */
+int emri_prologue(emri_ctx* ctx, const emri_grid* grid, const double* theta_dev, int w,
+                  const emri_opts* opts, double* out_dev, void* stream);
+
+/* Time-domain waveform of W walkers (steps S1-S4; Eqs. (1)-(2)): the two
+ * LISA channels at unit distance (1 cm), packed as z_j = h_I(t_j) + i
+ * h_II(t_j), into z_out_dev[W][n] complex: double2 (16 B) for EMRI_FP64,
+ * float2 (8 B) for EMRI_MIXED.  status_dev (nullable) receives W status
+ * words.  W = 0 is a no-op. */
+int emri_ak_waveform(emri_ctx* ctx, const emri_grid* grid, const double* theta_dev, int w,
+                     const emri_opts* opts, void* z_out_dev, uint32_t* status_dev, void* stream);
+
+/* In-place batched FFT (step S5) of `batch` contiguous complex sequences of
+ * length n (power of two, 2^10..2^22): Z_k = sum_j z_j exp(s 2 pi i j k / n)
+ * with s = -1 for direction -1 (forward) and +1 for direction +1
+ * (unnormalised inverse).  precision EMRI_FP64: double2, EMRI_MIXED: float2.
+ * Natural order in and out. */
+int emri_fft_batch(emri_ctx* ctx, void* z_dev, int64_t n, int batch, int precision, int direction,
+                   void* stream);
+
+/* Batched log-likelihood (steps S0-S7; Eq. (8)) of W walkers against a
+ * dataset:  lnL = <d|h> - <h|h>/2 (the constant -<d|d>/2 left out) with
+ * h = h_u / d_GW delayed by dt_GW,
+ *   <d|h_u> = sum_k w_k Re(conj(D_k) H_u,k exp(-2 pi i k_s r)),
+ *   <h_u|h_u> = sum_k w_k |H_u,k|^2,
+ * H_u = DFT of the unit-distance packed channels, k_s the signed bin index.
+ * Outputs (device, W doubles each): lnl_dev; dh_dev, hh_dev (nullable) the
+ * unit-distance sums <d|h_u>, <h_u|h_u>; status_dev (nullable).  Reduction
+ * order is fixed per (n, opts), so a walker's result does not depend on the
+ * other walkers in the call.  W = 0 is a no-op. */
+int emri_loglike_batch(emri_ctx* ctx, const emri_dataset* ds, const double* theta_dev, int w,
+                       const emri_opts* opts, double* lnl_dev, double* dh_dev, double* hh_dev,
+                       uint32_t* status_dev, void* stream);
+
+/* ------------------------------------------------------- uneven batching
+ * Several independent chains, each with its own dataset (its own n), walker
+ * count and options, evaluated in one multi-work launch sequence (the work
+ * items of all chains share each kernel launch).  Pointers in emri_work are
+ * device pointers owned by the caller; outputs as emri_loglike_batch. */
+typedef struct {
+  const emri_dataset* ds;
+  const double* theta_dev; /* [EMRI_NPARAM][w] */
+  int w;
+  emri_opts opts;
+  double* lnl_dev;
+  double* dh_dev;          /* nullable */
+  double* hh_dev;          /* nullable */
+  uint32_t* status_dev;    /* nullable */
+} emri_work;
+
+int emri_loglike_multi(emri_ctx* ctx, const emri_work* items, int n_items, void* stream);
+
+/* ------------------------------------------------------------- serving
+ * A continuous-batching request loop on the context's device: requests
+ * arriving while others run are admitted as HBM budget and slots free up,
+ * and run concurrently on the device. */
+typedef struct {
+  int slots;            /* concurrent requests on the device (streams), >= 1  */
+  int queue_capacity;   /* pending requests before submit returns EAGAIN      */
+  size_t budget_bytes;  /* workspace budget for admitted requests (0 = ctx's)  */
+} emri_serve_cfg;
+
+typedef struct {
+  int64_t arrival_ns;   /* submit time (CLOCK_MONOTONIC)                      */
+  int64_t start_ns;     /* admission (work enqueued on the device)            */
+  int64_t done_ns;      /* results observed complete                          */
+  int32_t status;       /* emri_status of the request                         */
+  int32_t slot;         /* stream slot that ran it                            */
+} emri_req_stats;
+
+int emri_serve_start(emri_ctx* ctx, const emri_serve_cfg* cfg);
+int emri_serve_stop(emri_ctx* ctx);
+
+/* Enqueue W walkers (theta_host[EMRI_NPARAM][W], host, copied before return)
+ * against a dataset.  *ticket identifies the request.  EMRI_EAGAIN when the
+ * queue is full; EMRI_EBUDGET when the request alone exceeds the budget. */
+int emri_serve_submit(emri_ctx* ctx, const emri_dataset* ds, const double* theta_host, int w,
+                      const emri_opts* opts, uint64_t* ticket);
+
+/* Wait up to timeout_us (<0: forever) for a request; on completion copy its
+ * W log-likelihoods to lnl_host, statuses to status_host (nullable) and the
+ * timestamps to stats (nullable), then release the ticket.
+ * EMRI_ETIMEDOUT if not done in time, EMRI_ENOTFOUND for an unknown ticket. */
+int emri_serve_poll(emri_ctx* ctx, uint64_t ticket, double* lnl_host, uint32_t* status_host,
+                    emri_req_stats* stats, int64_t timeout_us);
+
+/* ----------------------------------------------------------- autotuner
+ * Time the library's schedule choices (knot spacing, walkers per wave, FFT
+ * split) for this grid, n_max and precision on the context's device and keep
+ * the fastest as the context's plan for that shape; with cache_path
+ * non-NULL the plans are also read from / appended to that JSON-lines file.
+ * choice_out (nullable, host) receives {knot_spacing, wave_walkers, fft_n1}. */
+int emri_autotune(emri_ctx* ctx, const emri_grid* grid, int n_max, int precision,
+                  const char* cache_path, int64_t* choice_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EMRI_H */

@@ -92,6 +92,7 @@ def lib():
                 "orc_weights": (None, [d, i64, C.c_double, C.c_double, C.c_double, d]),
                 "orc_inner": (C.c_double, [d, d, d, d, d, i64]),
                 "orc_prologue": (None, [d, po, i64, C.c_double, d]),
+                "orc_delay_apply": (None, [d, d, i64, C.c_double, C.c_double, d, d]),
                 "orc_loglike": (None, [d, i32, po, i64, C.c_double, C.c_double, d, d, d,
                                        d, d, d, u32, i32]),
             }
@@ -264,6 +265,41 @@ def prologue(theta, n: int, dt: float, opts: Opts | None = None) -> np.ndarray:
     out = np.zeros(6)
     lib().orc_prologue(_dp(t), C.byref(o), int(n), float(dt), _dp(out))
     return out
+
+
+def delay_apply(x, r_hi: float, r_lo: float) -> np.ndarray:
+    """x_k exp(-2 pi i frac(k_s r)) (natural order, signed k_s)."""
+    a = np.asarray(x, dtype=np.complex128)
+    re, im = _f64(a.real), _f64(a.imag)
+    ore, oim = np.zeros_like(re), np.zeros_like(im)
+    lib().orc_delay_apply(_dp(re), _dp(im), a.size, float(r_hi), float(r_lo), _dp(ore), _dp(oim))
+    return ore + 1j * oim
+
+
+def injection_data(theta_inj, n: int, dt: float, psd, noise_seed: int | None, opts: Opts | None = None,
+                   snr: float | None = None, fmin: float = 1e-4, nthreads=None):
+    """Data spectrum d = DFT(h(theta_inj)) + noise, built by the oracle.
+
+    h is the unit-distance waveform delayed by the injection's GW-speed delay
+    and divided by its d_GW.  With ``snr`` set, the injection's redshift is
+    first solved so that sqrt(<h|h>) equals it (the returned theta carries
+    that z).  Returns (data, theta_inj, weights, rho_unit)."""
+    from paper_2311_17174_gb300 import inputs as _in
+    o = opts or Opts()
+    th = np.array(theta_inj, dtype=np.float64).copy()
+    hI, hII, _ = waveform(th, n, dt, o, nthreads=nthreads)
+    H = packed_spectrum(hI[0], hII[0])
+    w = weights(psd, n, dt, fmin, 1.0 / (2 * dt))
+    rho_u = float(np.sqrt(inner(H, H, w)))
+    if snr is not None:
+        target = rho_u / snr
+        f = lambda z: prologue(np.concatenate([th[:13], [z], th[14:]]), n, dt, o)[2]
+        th[13] = _in.solve_distance(target, f)
+    pro = prologue(th, n, dt, o)
+    d = delay_apply(H, pro[4], pro[5]) / pro[2]
+    if noise_seed is not None:
+        d = d + _in.noise_spectrum(noise_seed, psd, n, dt)
+    return d, th, w, rho_u
 
 
 # --------------------------------------------------------- inner product

@@ -636,6 +636,22 @@ double orc_inner(const double* ar, const double* ai, const double* br, const dou
   return (double)s;
 }
 
+/* exposed: X_k * exp(-2 pi i frac(k_s r)) for a natural-order spectrum, with
+ * r = r_hi + r_lo and signed k_s (the delay factor of the likelihood) */
+void orc_delay_apply(const double* re, const double* im, int64_t n, double r_hi, double r_lo,
+                     double* ore, double* oim) {
+  Q r = (Q)r_hi + (Q)r_lo;
+  for (int64_t j = 0; j < n; ++j) {
+    int64_t ks = (2 * j <= n) ? j : j - n;
+    Q ph = (Q)ks * r;
+    ph -= floorf128(ph);
+    R a = 2 * PI_R * (R)ph;
+    R fr = cosl(a), fi = -sinl(a);
+    ore[j] = (double)(re[j] * fr - im[j] * fi);
+    oim[j] = (double)(re[j] * fi + im[j] * fr);
+  }
+}
+
 /* Per-walker propagation constants: out = {d_L [cm], Xi, d_GW [cm], dt_GW [s],
  * r_hi, r_lo} with r = frac(dt_GW / T), T = N dt. */
 void orc_prologue(const double* th, const orc_opts* o, int64_t n, double dt, double out[6]) {

@@ -1,0 +1,570 @@
+// emri_api.cu -- the C-ABI of libemri (include/emri.h): contexts, datasets,
+// workspaces and the launch sequence of the batched AK log-likelihood.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/emri.h"
+#include "emri_api_internal.h"
+#include "emri_common.cuh"
+#include "emri_internal.h"
+
+using namespace emri;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+namespace emri {
+int set_err(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_err(cudaError_t e, const char* where) {
+  return set_err(EMRI_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+}  // namespace emri
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_err(e_, #call); \
+  } while (0)
+
+extern "C" const char* emri_last_error(void) { return g_err.c_str(); }
+extern "C" const char* emri_version(void) { return "emri-gb300 0.1 (sm_103a)"; }
+
+extern "C" void emri_opts_default(emri_opts* o) {
+  if (!o) return;
+  o->precision = EMRI_FP64;
+  o->n_max = 10;
+  o->doppler = 1;
+  o->pn_terms = 1;
+  o->mode = EMRI_FORWARD;
+  o->knot_spacing = 0;
+  o->n_xi = 2.0;
+  o->omega_m = 0.315;
+  o->h0 = 67.4;
+}
+
+namespace emri {
+
+static bool pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+
+int normalize_opts(const emri_opts* in, int64_t n, OptsN* o) {
+  emri_opts d;
+  emri_opts_default(&d);
+  const emri_opts& a = in ? *in : d;
+  if (a.precision != EMRI_FP64 && a.precision != EMRI_MIXED)
+    return set_err(EMRI_EINVAL, "opts.precision must be EMRI_FP64 or EMRI_MIXED");
+  if (a.n_max < 1 || a.n_max > 32) return set_err(EMRI_EINVAL, "opts.n_max must be in [1, 32]");
+  if (a.mode != EMRI_FORWARD && a.mode != EMRI_BACKWARD_FROM_LSO)
+    return set_err(EMRI_EINVAL, "opts.mode must be EMRI_FORWARD or EMRI_BACKWARD_FROM_LSO");
+  if (a.mode == EMRI_BACKWARD_FROM_LSO)
+    return set_err(EMRI_EINVAL, "backward-from-LSO integration is not available in this build");
+  o->precision = a.precision;
+  o->n_max = a.n_max;
+  o->doppler = a.doppler ? 1 : 0;
+  o->pn_terms = a.pn_terms ? 1 : 0;
+  o->mode = a.mode;
+  int ks = a.knot_spacing;
+  if (ks == 0) ks = a.precision == EMRI_FP64 ? 128 : 256;
+  if (!pow2(ks) || ks < 64 || ks > 1024 || ks > n)
+    return set_err(EMRI_EINVAL, "opts.knot_spacing must be a power of two in [64, 1024] and <= n");
+  o->ks = ks;
+  o->n_xi = a.n_xi > 0 ? a.n_xi : 2.0;
+  o->omega_m = a.omega_m > 0 ? a.omega_m : 0.315;
+  o->h0 = a.h0 > 0 ? a.h0 : 67.4;
+  if (!(o->omega_m > 0 && o->omega_m < 1)) return set_err(EMRI_EINVAL, "opts.omega_m must be in (0, 1)");
+  return EMRI_OK;
+}
+
+int check_grid(const emri_grid* g) {
+  if (!g) return set_err(EMRI_EINVAL, "grid is NULL");
+  if (!pow2(g->n) || g->n < (1 << 10) || g->n > (1 << 22))
+    return set_err(EMRI_EINVAL, "grid.n must be a power of two in [2^10, 2^22] (got %lld)", (long long)g->n);
+  if (!(g->dt > 0) || !isfinite(g->dt)) return set_err(EMRI_EINVAL, "grid.dt must be positive");
+  if (!isfinite(g->t0)) return set_err(EMRI_EINVAL, "grid.t0 must be finite");
+  return EMRI_OK;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_32 with the
+// three-term recurrence; Abramowitz & Stegun 25.4.29).
+static void gauss_legendre32(double* x, double* w) {
+  const int n = 32;
+  for (int i = 0; i < n; ++i) {
+    double z = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-17) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// ----------------------------------------------------------- workspace
+int Workspace::reserve(emri_ctx* ctx, size_t bytes, cudaStream_t s) {
+  if (bytes <= cap) return EMRI_OK;
+  size_t want = std::max(bytes, cap + cap / 4);
+  if (ptr) {
+    cudaStreamSynchronize(last_stream);
+    cudaFree(ptr);
+    ctx->used -= cap;
+    ptr = nullptr;
+    cap = 0;
+  }
+  if (ctx->used + want > ctx->budget) {
+    want = bytes;
+    if (ctx->used + want > ctx->budget)
+      return set_err(EMRI_EBUDGET, "workspace of %zu bytes exceeds the HBM budget (%zu of %zu in use)", bytes,
+                     ctx->used, ctx->budget);
+  }
+  cudaError_t e = cudaMalloc(&ptr, want);
+  if (e != cudaSuccess) {
+    ptr = nullptr;
+    return set_err(EMRI_ENOMEM, "cudaMalloc(%zu): %s", want, cudaGetErrorString(e));
+  }
+  cap = want;
+  ctx->used += want;
+  (void)s;
+  return EMRI_OK;
+}
+
+void Workspace::acquire(cudaStream_t s) {
+  if (!ev) cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (has_ev && s != last_stream) cudaStreamWaitEvent(s, ev, 0);
+}
+
+void Workspace::release(cudaStream_t s) {
+  cudaEventRecord(ev, s);
+  has_ev = true;
+  last_stream = s;
+}
+
+void Workspace::destroy(emri_ctx* ctx) {
+  if (ptr) {
+    cudaDeviceSynchronize();
+    cudaFree(ptr);
+    ctx->used -= cap;
+  }
+  if (ev) cudaEventDestroy(ev);
+  ptr = nullptr;
+  cap = 0;
+  ev = nullptr;
+}
+
+size_t loglike_layout(const FftPlan& p, const OptsN& o, int w, int wave, Carve* c, LoglikeBufs* b) {
+  const int64_t nk = p.n / o.ks;
+  const size_t cs = o.precision ? sizeof(float2) : sizeof(double2);
+  Carve dummy(nullptr);
+  Carve& cv = c ? *c : dummy;
+  LoglikeBufs t;
+  t.wc = cv.take<WalkerC>(w);
+  t.knots = cv.take<Knot>((size_t)w * (nk + 1));
+  t.dtab = cv.take<char>((size_t)w * p.n1 * cs);
+  t.partial = cv.take<double2>((size_t)w * p.n2);
+  t.z = cv.take<char>((size_t)wave * p.n * cs);
+  if (b) *b = t;
+  return cv.off + 256;
+}
+
+int pick_wave(emri_ctx* ctx, const FftPlan& p, const OptsN& o, int w) {
+  const size_t cs = o.precision ? sizeof(float2) : sizeof(double2);
+  const size_t per = (size_t)p.n * cs;
+  int plan = ctx_plan_wave(ctx, p.n, o);
+  if (plan > 0) return std::min(plan, w);
+  // default: waves of up to 16 GiB of time series
+  size_t cap = (size_t)16 << 30;
+  int wave = (int)std::max<size_t>(1, cap / per);
+  return std::min(wave, w);
+}
+
+// The launch sequence of steps S0-S7 for W walkers of one dataset.
+int run_loglike(emri_ctx* ctx, const emri_dataset* ds, const double* theta, int64_t ld, int w, const OptsN& o,
+                int wave, const LoglikeBufs& b, double* lnl, double* dh, double* hh, uint32_t* status,
+                cudaStream_t s, int64_t* launches) {
+  const FftPlan& p = ds->plan;
+  const bool f32 = o.precision != 0;
+  const size_t cs = f32 ? sizeof(float2) : sizeof(double2);
+  int64_t nl = 0;
+  launch_prologue(theta, ld, w, p.n, ds->dt, o, ctx->gl, b.wc, s);
+  launch_delay_table(b.wc, w, p.n1, p.n2, f32, b.dtab, s);
+  launch_orbit(b.wc, w, p.n, ds->dt, ds->t0, o, b.knots, s);
+  nl += 3;
+  const int64_t nk = p.n / o.ks;
+  const void* dperm = f32 ? (const void*)ds->d_perm32 : (const void*)ds->d_perm;
+  const void* wperm = f32 ? (const void*)ds->w_perm32 : (const void*)ds->w_perm;
+  const double dh_scale = f32 ? 1.0 / (ds->d_scale * ds->w_scale) : 1.0;
+  const double hh_scale = f32 ? 1.0 / ds->w_scale : 1.0;
+  for (int i0 = 0; i0 < w; i0 += wave) {
+    const int ww = std::min(wave, w - i0);
+    launch_wave(b.knots + (size_t)i0 * (nk + 1), b.wc + i0, ww, p.n, ds->dt, ds->t0, o, b.z, false, s);
+    launch_fft_pass1(b.z, ww, p, f32, -1, ctx->tw, s);
+    launch_fft_pass2_ip(b.z, ww, p, f32, ctx->tw, b.wc + i0, b.dtab + (size_t)i0 * p.n1 * cs, dperm, wperm,
+                        b.partial + (size_t)i0 * p.n2, s);
+    launch_finalize(b.partial + (size_t)i0 * p.n2, p.n2, b.wc + i0, ww, dh_scale, hh_scale, lnl + i0,
+                    dh ? dh + i0 : nullptr, hh ? hh + i0 : nullptr, status ? status + i0 : nullptr, s);
+    nl += 4;
+  }
+  if (launches) *launches = nl;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_err(e, "loglike launch");
+  return EMRI_OK;
+}
+
+}  // namespace emri
+
+// ===================================================================== ctx
+extern "C" int emri_ctx_create(int device, size_t budget, emri_ctx** out) {
+  if (!out) return set_err(EMRI_EINVAL, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) return set_err(EMRI_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+  if (device < 0 || device >= ndev) return set_err(EMRI_EINVAL, "device %d out of range (%d devices)", device, ndev);
+  CK(cudaSetDevice(device));
+  emri_ctx* c = new emri_ctx();
+  c->device = device;
+  size_t fr = 0, tot = 0;
+  CK(cudaMemGetInfo(&fr, &tot));
+  c->budget = budget ? budget : (size_t)(0.8 * (double)fr);
+  c->used = 0;
+  cudaError_t e2 = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e2 != cudaSuccess) {
+    delete c;
+    return cuda_err(e2, "cudaStreamCreate");
+  }
+  // twiddle and quadrature tables
+  size_t tb = 4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8 + 64 * 8;
+  char* p = nullptr;
+  e2 = cudaMalloc(&p, tb);
+  if (e2 != cudaSuccess) {
+    cudaStreamDestroy(c->stream);
+    delete c;
+    return cuda_err(e2, "cudaMalloc(tables)");
+  }
+  c->tables = p;
+  c->used += tb;
+  c->tw.ta64 = (double2*)p;
+  c->tw.tb64 = (double2*)(p + 4096 * 16);
+  c->tw.ta32 = (float2*)(p + 4096 * 16 + 1024 * 16);
+  c->tw.tb32 = (float2*)(p + 4096 * 16 + 1024 * 16 + 4096 * 8);
+  c->gl = (double*)(p + 4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8);
+  double glh[64];
+  gauss_legendre32(glh, glh + 32);
+  launch_twiddle_init(c->tw, c->stream);
+  cudaMemcpyAsync(c->gl, glh, sizeof glh, cudaMemcpyHostToDevice, c->stream);
+  fft_set_smem_limits();
+  e2 = cudaStreamSynchronize(c->stream);
+  if (e2 == cudaSuccess) e2 = cudaGetLastError();
+  if (e2 != cudaSuccess) {
+    cudaFree(p);
+    cudaStreamDestroy(c->stream);
+    delete c;
+    return cuda_err(e2, "context tables");
+  }
+  c->launches = 1;
+  *out = c;
+  return EMRI_OK;
+}
+
+extern "C" int emri_ctx_destroy(emri_ctx* c) {
+  if (!c) return EMRI_OK;
+  cudaSetDevice(c->device);
+  serve_shutdown(c);
+  c->ws.destroy(c);
+  if (c->tables) cudaFree(c->tables);
+  cudaStreamDestroy(c->stream);
+  delete c;
+  return EMRI_OK;
+}
+
+extern "C" int emri_ctx_launches(const emri_ctx* c, int64_t* count) {
+  if (!c || !count) return set_err(EMRI_EINVAL, "NULL argument");
+  *count = c->launches.load();
+  return EMRI_OK;
+}
+
+extern "C" int emri_ctx_memory(const emri_ctx* c, size_t* used, size_t* budget) {
+  if (!c) return set_err(EMRI_EINVAL, "NULL context");
+  if (used) *used = c->used;
+  if (budget) *budget = c->budget;
+  return EMRI_OK;
+}
+
+// ================================================================= dataset
+__global__ void k_absmax(const double* __restrict__ v, int64_t n, int stride2, unsigned long long* out) {
+  // max |v| over n doubles (stride2 = 2: complex magnitudes), positive-double bit order
+  double m = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double a = stride2 == 2 ? hypot(v[2 * i], v[2 * i + 1]) : fabs(v[i]);
+    m = a > m ? a : m;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    double o = __shfl_xor_sync(0xffffffffu, m, off);
+    m = o > m ? o : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+extern "C" int emri_dataset_create(emri_ctx* ctx, const emri_grid* grid, const void* data, int kind,
+                                   const double* psd, double fmin, double fmax, emri_dataset** out) {
+  if (!ctx || !out || !data || !psd) return set_err(EMRI_EINVAL, "NULL argument");
+  *out = nullptr;
+  int rc = check_grid(grid);
+  if (rc) return rc;
+  if (kind != 0 && kind != 1) return set_err(EMRI_EINVAL, "data_kind must be 0 (spectrum) or 1 (time series)");
+  if (!(fmax > fmin) || fmin < 0) return set_err(EMRI_EINVAL, "need 0 <= fmin < fmax");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  const int64_t n = grid->n;
+  emri_dataset* ds = new emri_dataset();
+  ds->ctx = ctx;
+  ds->n = n;
+  ds->dt = grid->dt;
+  ds->t0 = grid->t0;
+  ds->fmin = fmin;
+  ds->fmax = fmax;
+  ds->plan = make_fft_plan(n);
+  const size_t keep = (size_t)n * (16 + 8 + 8 + 4) + 1024;
+  const size_t tmp = (size_t)n * (16 + 16 + 8) + (size_t)(n / 2 + 1) * 8 + 4096;
+  if (ctx->used + keep + tmp > ctx->budget) {
+    delete ds;
+    return set_err(EMRI_EBUDGET, "dataset of %zu bytes exceeds the HBM budget", keep);
+  }
+  char* kp = nullptr;
+  char* tp = nullptr;
+  cudaError_t e = cudaMalloc(&kp, keep);
+  if (e == cudaSuccess) e = cudaMalloc(&tp, tmp);
+  if (e != cudaSuccess) {
+    cudaFree(kp);
+    delete ds;
+    return set_err(EMRI_ENOMEM, "dataset allocation: %s", cudaGetErrorString(e));
+  }
+  ds->mem = kp;
+  ds->bytes = keep;
+  ctx->used += keep;
+  Carve k(kp), t(tp);
+  ds->d_perm = k.take<double2>(n);
+  ds->w_perm = k.take<double>(n);
+  ds->d_perm32 = k.take<float2>(n);
+  ds->w_perm32 = k.take<float>(n);
+  double2* dnat = t.take<double2>(n);
+  double2* scratch = t.take<double2>(n);
+  double* wnat = t.take<double>(n);
+  double* psd_d = t.take<double>(n / 2 + 1);
+  unsigned long long* mx = t.take<unsigned long long>(4);
+  double* ddv = (double*)(mx + 2);
+  cudaStream_t s = ctx->stream;
+  int rc2 = EMRI_OK;
+  do {
+    if (kind == 0) {
+      if ((e = cudaMemcpyAsync(dnat, data, (size_t)n * 16, cudaMemcpyDefault, s)) != cudaSuccess) break;
+    } else {
+      double* d2 = (double*)scratch;   // [2][n] doubles fit in the n-complex scratch
+      if ((e = cudaMemcpyAsync(d2, data, (size_t)n * 16, cudaMemcpyDefault, s)) != cudaSuccess) break;
+      launch_pack_time_series(d2, n, dnat, s);
+      launch_fft_pass1(dnat, 1, ds->plan, false, -1, ctx->tw, s);
+      launch_fft_pass2_store(dnat, scratch, 1, ds->plan, false, -1, ctx->tw, s);
+      if ((e = cudaMemcpyAsync(dnat, scratch, (size_t)n * 16, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) break;
+    }
+    if ((e = cudaMemcpyAsync(psd_d, psd, (size_t)(n / 2 + 1) * 8, cudaMemcpyDefault, s)) != cudaSuccess) break;
+    launch_weights(psd_d, n, grid->dt, fmin, fmax, wnat, s);
+    cudaMemsetAsync(mx, 0, 16, s);
+    k_absmax<<<152, 256, 0, s>>>((const double*)dnat, n, 2, mx);
+    k_absmax<<<152, 256, 0, s>>>(wnat, n, 1, mx + 1);
+    unsigned long long hm[2];
+    if ((e = cudaMemcpyAsync(hm, mx, 16, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+    double dmax, wmax;
+    memcpy(&dmax, &hm[0], 8);
+    memcpy(&wmax, &hm[1], 8);
+    if (!(wmax > 0) || !isfinite(wmax) || !isfinite(dmax)) {
+      rc2 = set_err(EMRI_EINVAL, "dataset has no positive finite weight in the band or a non-finite value");
+      break;
+    }
+    ds->d_scale = dmax > 0 ? 1.0 / dmax : 1.0;
+    ds->w_scale = 1.0 / wmax;
+    launch_dataset_permute(dnat, wnat, ds->plan, ds->d_perm, ds->w_perm, ds->d_perm32, ds->w_perm32, ds->d_scale,
+                           ds->w_scale, s);
+    launch_inner_dd(dnat, wnat, n, ddv, s);
+    if ((e = cudaMemcpyAsync(&ds->dd, ddv, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+    e = cudaGetLastError();
+  } while (0);
+  cudaFree(tp);
+  if (e != cudaSuccess || rc2 != EMRI_OK) {
+    ctx->used -= keep;
+    cudaFree(kp);
+    delete ds;
+    return rc2 != EMRI_OK ? rc2 : cuda_err(e, "dataset preparation");
+  }
+  ctx->launches += kind == 1 ? 9 : 6;
+  *out = ds;
+  return EMRI_OK;
+}
+
+extern "C" int emri_dataset_destroy(emri_dataset* ds) {
+  if (!ds) return EMRI_OK;
+  emri_ctx* c = ds->ctx;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  cudaFree(ds->mem);
+  c->used -= ds->bytes;
+  delete ds;
+  return EMRI_OK;
+}
+
+extern "C" int emri_dataset_dd(const emri_dataset* ds, double* dd_out) {
+  if (!ds || !dd_out) return set_err(EMRI_EINVAL, "NULL argument");
+  *dd_out = ds->dd;
+  return EMRI_OK;
+}
+
+// =========================================================== batch calls
+extern "C" int emri_prologue(emri_ctx* ctx, const emri_grid* grid, const double* theta, int w,
+                             const emri_opts* opts, double* out, void* stream) {
+  if (!ctx) return set_err(EMRI_EINVAL, "NULL context");
+  int rc = check_grid(grid);
+  if (rc) return rc;
+  if (w < 0) return set_err(EMRI_EINVAL, "w must be >= 0");
+  if (w == 0) return EMRI_OK;
+  if (!theta || !out) return set_err(EMRI_EINVAL, "NULL pointer");
+  OptsN o;
+  if ((rc = normalize_opts(opts, grid->n, &o))) return rc;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  size_t need = (size_t)w * sizeof(WalkerC) + 256;
+  if ((rc = ctx->ws.reserve(ctx, need, s))) return rc;
+  ctx->ws.acquire(s);
+  WalkerC* wc = (WalkerC*)ctx->ws.ptr;
+  launch_prologue(theta, w, w, grid->n, grid->dt, o, ctx->gl, wc, s);
+  launch_prologue_export(wc, w, out, s);
+  ctx->ws.release(s);
+  ctx->launches += 2;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_err(e, "prologue launch");
+  return EMRI_OK;
+}
+
+extern "C" int emri_ak_waveform(emri_ctx* ctx, const emri_grid* grid, const double* theta, int w,
+                                const emri_opts* opts, void* z_out, uint32_t* status, void* stream) {
+  if (!ctx) return set_err(EMRI_EINVAL, "NULL context");
+  int rc = check_grid(grid);
+  if (rc) return rc;
+  if (w < 0) return set_err(EMRI_EINVAL, "w must be >= 0");
+  if (w == 0) return EMRI_OK;
+  if (!theta || !z_out) return set_err(EMRI_EINVAL, "NULL pointer");
+  OptsN o;
+  if ((rc = normalize_opts(opts, grid->n, &o))) return rc;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t nk = grid->n / o.ks;
+  Carve probe(nullptr);
+  probe.take<WalkerC>(w);
+  probe.take<Knot>((size_t)w * (nk + 1));
+  if ((rc = ctx->ws.reserve(ctx, probe.off + 512, s))) return rc;
+  ctx->ws.acquire(s);
+  Carve cv(ctx->ws.ptr);
+  WalkerC* wc = cv.take<WalkerC>(w);
+  Knot* kn = cv.take<Knot>((size_t)w * (nk + 1));
+  launch_prologue(theta, w, w, grid->n, grid->dt, o, ctx->gl, wc, s);
+  launch_orbit(wc, w, grid->n, grid->dt, grid->t0, o, kn, s);
+  launch_wave(kn, wc, w, grid->n, grid->dt, grid->t0, o, z_out, true, s);
+  if (status) cudaMemcpy2DAsync(status, sizeof(uint32_t), &wc[0].status, sizeof(WalkerC), sizeof(uint32_t), w,
+                                cudaMemcpyDeviceToDevice, s);
+  ctx->ws.release(s);
+  ctx->launches += 3;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_err(e, "waveform launch");
+  return EMRI_OK;
+}
+
+extern "C" int emri_fft_batch(emri_ctx* ctx, void* z, int64_t n, int batch, int precision, int direction,
+                              void* stream) {
+  if (!ctx) return set_err(EMRI_EINVAL, "NULL context");
+  emri_grid g{n, 1.0, 0.0};
+  int rc = check_grid(&g);
+  if (rc) return rc;
+  if (batch < 0) return set_err(EMRI_EINVAL, "batch must be >= 0");
+  if (precision != EMRI_FP64 && precision != EMRI_MIXED) return set_err(EMRI_EINVAL, "bad precision");
+  if (direction != -1 && direction != 1) return set_err(EMRI_EINVAL, "direction must be -1 or +1");
+  if (batch == 0) return EMRI_OK;
+  if (!z) return set_err(EMRI_EINVAL, "NULL pointer");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool f32 = precision == EMRI_MIXED;
+  const size_t cs = f32 ? 8 : 16;
+  const FftPlan p = make_fft_plan(n);
+  const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(batch, ((int64_t)1 << 30) / ((int64_t)n * cs)));
+  if ((rc = ctx->ws.reserve(ctx, (size_t)chunk * n * cs + 256, s))) return rc;
+  ctx->ws.acquire(s);
+  int64_t nl = 0;
+  cudaError_t e = cudaSuccess;
+  for (int b0 = 0; b0 < batch && e == cudaSuccess; b0 += chunk) {
+    const int bb = std::min(chunk, batch - b0);
+    char* zb = (char*)z + (size_t)b0 * n * cs;
+    launch_fft_pass1(zb, bb, p, f32, direction, ctx->tw, s);
+    launch_fft_pass2_store(zb, ctx->ws.ptr, bb, p, f32, direction, ctx->tw, s);
+    e = cudaMemcpyAsync(zb, ctx->ws.ptr, (size_t)bb * n * cs, cudaMemcpyDeviceToDevice, s);
+    nl += 2;
+  }
+  ctx->ws.release(s);
+  ctx->launches += nl;
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_err(e, "fft launch");
+  return EMRI_OK;
+}
+
+extern "C" int emri_loglike_batch(emri_ctx* ctx, const emri_dataset* ds, const double* theta, int w,
+                                  const emri_opts* opts, double* lnl, double* dh, double* hh, uint32_t* status,
+                                  void* stream) {
+  if (!ctx || !ds) return set_err(EMRI_EINVAL, "NULL context or dataset");
+  if (ds->ctx != ctx) return set_err(EMRI_EINVAL, "dataset belongs to another context");
+  if (w < 0) return set_err(EMRI_EINVAL, "w must be >= 0");
+  if (w == 0) return EMRI_OK;
+  if (!theta || !lnl) return set_err(EMRI_EINVAL, "NULL pointer");
+  OptsN o;
+  int rc = normalize_opts(opts, ds->n, &o);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int wave = pick_wave(ctx, ds->plan, o, w);
+  const size_t need = loglike_layout(ds->plan, o, w, wave, nullptr, nullptr);
+  if ((rc = ctx->ws.reserve(ctx, need, s))) return rc;
+  ctx->ws.acquire(s);
+  Carve cv(ctx->ws.ptr);
+  LoglikeBufs b;
+  loglike_layout(ds->plan, o, w, wave, &cv, &b);
+  int64_t nl = 0;
+  rc = run_loglike(ctx, ds, theta, w, w, o, wave, b, lnl, dh, hh, status, s, &nl);
+  ctx->ws.release(s);
+  ctx->launches += nl;
+  return rc;
+}

@@ -1,0 +1,108 @@
+// emri_api_internal.h -- host-side objects behind the C-ABI handles.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "../../include/emri.h"
+#include "emri_internal.h"
+
+namespace emri {
+struct Server;
+}
+
+struct emri_ctx;
+
+namespace emri {
+
+// A growable device buffer reused across calls; cross-stream use is ordered
+// through an event recorded after the last call that used it.
+struct Workspace {
+  char* ptr = nullptr;
+  size_t cap = 0;
+  cudaEvent_t ev = nullptr;
+  bool has_ev = false;
+  cudaStream_t last_stream = nullptr;
+  int reserve(emri_ctx* ctx, size_t bytes, cudaStream_t s);
+  void acquire(cudaStream_t s);
+  void release(cudaStream_t s);
+  void destroy(emri_ctx* ctx);
+};
+
+// Carve a workspace into per-call buffers (256-byte aligned); with a NULL
+// base it only measures.
+struct Carve {
+  char* base;
+  size_t off = 0;
+  explicit Carve(void* p) : base((char*)p) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* r = (T*)(base ? base + off : nullptr);
+    off += count * sizeof(T);
+    return r;
+  }
+};
+
+struct LoglikeBufs {
+  WalkerC* wc;
+  Knot* knots;
+  char* dtab;
+  double2* partial;
+  char* z;
+};
+
+// autotuned schedule of one (n, n_max, precision) shape
+struct Plan {
+  int ks = 0;
+  int wave = 0;
+};
+
+}  // namespace emri
+
+struct emri_ctx {
+  int device = 0;
+  size_t budget = 0;
+  size_t used = 0;
+  std::mutex mu;
+  cudaStream_t stream = nullptr;
+  char* tables = nullptr;
+  emri::Twiddles tw{};
+  double* gl = nullptr;
+  emri::Workspace ws;
+  std::atomic<int64_t> launches{0};
+  emri::Server* server = nullptr;
+  std::map<std::tuple<int64_t, int, int>, emri::Plan> plans;   // (n, n_max, precision)
+};
+
+struct emri_dataset {
+  emri_ctx* ctx = nullptr;
+  int64_t n = 0;
+  double dt = 0, t0 = 0, fmin = 0, fmax = 0;
+  emri::FftPlan plan{};
+  char* mem = nullptr;
+  size_t bytes = 0;
+  double2* d_perm = nullptr;
+  double* w_perm = nullptr;
+  float2* d_perm32 = nullptr;
+  float* w_perm32 = nullptr;
+  double d_scale = 1.0, w_scale = 1.0;
+  double dd = 0.0;
+};
+
+namespace emri {
+int set_err(int code, const char* fmt, ...);
+int cuda_err(cudaError_t e, const char* where);
+int normalize_opts(const emri_opts* in, int64_t n, OptsN* o);
+int check_grid(const emri_grid* g);
+size_t loglike_layout(const FftPlan& p, const OptsN& o, int w, int wave, Carve* c, LoglikeBufs* b);
+int pick_wave(emri_ctx* ctx, const FftPlan& p, const OptsN& o, int w);
+int run_loglike(emri_ctx* ctx, const emri_dataset* ds, const double* theta, int64_t ld, int w, const OptsN& o,
+                int wave, const LoglikeBufs& b, double* lnl, double* dh, double* hh, uint32_t* status,
+                cudaStream_t s, int64_t* launches);
+int ctx_plan_wave(emri_ctx* ctx, int64_t n, const OptsN& o);
+void serve_shutdown(emri_ctx* ctx);
+}  // namespace emri

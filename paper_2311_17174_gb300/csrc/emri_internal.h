@@ -1,0 +1,80 @@
+// emri_internal.h -- host-side declarations shared by the libemri
+// translation units (kernel launchers and normalised options).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace emri {
+
+struct WalkerC;
+struct Knot;
+
+// Options after defaults and validation.
+struct OptsN {
+  int precision;   // 0 FP64, 1 mixed
+  int n_max;
+  int doppler;
+  int pn_terms;
+  int mode;        // 0 forward, 1 backward from LSO
+  int ks;          // knot spacing (samples)
+  double n_xi, omega_m, h0;
+};
+
+// FFT split of n = n1 * n2 (n2 = column length, n1 = row length).
+struct FftPlan {
+  int64_t n;
+  int n1, n2;
+  int log2n;
+};
+FftPlan make_fft_plan(int64_t n);
+
+// Twiddle tables: ta[i] = exp(-2 pi i i/4096), i < 4096; tb[i] = exp(-2 pi i i/2^22), i < 1024.
+struct Twiddles {
+  double2* ta64;
+  double2* tb64;
+  float2* ta32;
+  float2* tb32;
+};
+
+void launch_twiddle_init(Twiddles t, cudaStream_t s);
+
+void launch_prologue(const double* theta, int64_t ld, int w, int64_t n, double dt, const OptsN& o,
+                     const double* gl, WalkerC* out, cudaStream_t s);
+void launch_delay_table(const WalkerC* wc, int w, int n1, int n2, bool fp32, void* tab, cudaStream_t s);
+void launch_prologue_export(const WalkerC* wc, int w, double* out, cudaStream_t s);
+
+// orbit: knots[w][nk+1], nk = n / ks
+void launch_orbit(WalkerC* wc, int w, int64_t n, double dt, double t0, const OptsN& o, Knot* knots,
+                  cudaStream_t s);
+
+// waveform: z[w][n] (double2 or float2); unit_scale multiplies by mu_s c (cm units)
+void launch_wave(const Knot* knots, const WalkerC* wc, int w, int64_t n, double dt, double t0,
+                 const OptsN& o, void* z, bool unit_scale, cudaStream_t s);
+
+// FFT pass 1 (columns, in place, with the inter-pass twiddle); sign -1 forward, +1 inverse
+void launch_fft_pass1(void* z, int batch, const FftPlan& p, bool fp32, int sign, const Twiddles& t,
+                      cudaStream_t s);
+// FFT pass 2 to natural order into out (out-of-place)
+void launch_fft_pass2_store(const void* y, void* out, int batch, const FftPlan& p, bool fp32, int sign,
+                            const Twiddles& t, cudaStream_t s);
+// FFT pass 2 fused with the weighted inner products; partial[w][n2] = (dh, hh)
+void launch_fft_pass2_ip(const void* y, int w, const FftPlan& p, bool fp32, const Twiddles& t,
+                         const WalkerC* wc, const void* delay_tab, const void* data_perm,
+                         const void* wt_perm, double2* partial, cudaStream_t s);
+// per-walker fixed-order reduction of the partials and lnL
+// dh_scale / hh_scale undo the dataset's FP32 scaling (1 for FP64)
+void launch_finalize(const double2* partial, int n2, const WalkerC* wc, int w, double dh_scale, double hh_scale,
+                     double* lnl, double* dh, double* hh, uint32_t* status, cudaStream_t s);
+void fft_set_smem_limits();
+
+// dataset preparation: permute the natural-order spectrum and weights into
+// the pass-2 order (k2-major), and build FP32 scaled copies
+void launch_dataset_permute(const double2* d_nat, const double* w_nat, const FftPlan& p, double2* d_perm,
+                            double* w_perm, float2* d_perm32, float* w_perm32, double d_scale,
+                            double w_scale, cudaStream_t s);
+void launch_weights(const double* psd, int64_t n, double dt, double fmin, double fmax, double* w,
+                    cudaStream_t s);
+void launch_pack_time_series(const double* d2, int64_t n, double2* z, cudaStream_t s);
+void launch_inner_dd(const double2* d, const double* w, int64_t n, double* out, cudaStream_t s);
+
+}  // namespace emri

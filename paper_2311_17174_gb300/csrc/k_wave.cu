@@ -1,0 +1,423 @@
+// k_wave.cu -- steps S2-S4: dense orbit, LISA response and the
+// Peters-Mathews harmonic sum of Eq. (2), one CTA per 256-sample tile.
+//
+// Per tile (prologue, a few threads):
+//  * the cubic Hermite interpolant of every orbit quantity over each knot
+//    interval the tile touches (values and rates at both knots);
+//  * the Bessel amplitudes of every harmonic at the tile's start, middle and
+//    end, fitted by a quadratic in time.  The amplitudes depend on time only
+//    through e(t), which moves by ~1e-4 relative per tile, so the quadratic
+//    is exact to ~1e-11 and the per-sample cost of a harmonic drops from a
+//    Bessel evaluation to a few FMAs.
+// Per sample (one thread each):
+//  * phases Phi_D (Doppler folded in), 2 gamma~ and alpha from the Hermite
+//    polynomials, reduced modulo one cycle;
+//  * geometry: L(t) on its precession cone, L.N, the polarisation angle psi
+//    and the angle beta (only 2 psi and 2 beta enter, taken as rational
+//    functions of the two atan2 arguments), the detector-frame source angles
+//    and the antenna patterns of the two Michelson channels;
+//  * the harmonic sum written as three running sums
+//      C = sum_n n pa_n cos(n Phi), S = sum_n n sqrt(1-e^2) pb_n sin(n Phi),
+//      R = sum_n 2 pc_n cos(n Phi),
+//    with cos(n Phi), sin(n Phi) by complex rotation, so that
+//      h+ = A[(1+c^2)(C cos 2g - S sin 2g) + (1-c^2) R],
+//      hx = -2 c A [S cos 2g + C sin 2g],
+//    which is Eq. (2)'s sum of A+_n and Ax_n regrouped;
+//  * h_I,II = (sqrt3/2)(F+_I,II h+ + Fx_I,II hx), written as z = h_I + i h_II.
+// FP64 variant: everything in double.  Mixed variant: the three phases are
+// evaluated in 64-bit fixed point (linear term) plus an FP32 correction, so
+// no FP64 instruction runs per sample; the rest is FP32.
+#include "emri_common.cuh"
+#include "emri_internal.h"
+
+namespace emri {
+
+constexpr int kTile = 256;
+
+// --------------------------------------------------------------- Bessel
+// J_m(x) by its power series, m >= 0, for x <= ~0.6 (m + 2).
+template <typename T>
+__device__ __forceinline__ T bessel_series(int m, T x) {
+  const T half = T(0.5) * x;
+  T lead = T(1);
+  T p = half;
+  int k = m;
+  while (k) {                       // (x/2)^m by squaring
+    if (k & 1) lead *= p;
+    p *= p;
+    k >>= 1;
+  }
+  T fact = T(1);
+  for (int i = 2; i <= m; ++i) fact *= T(i);
+  lead /= fact;
+  const T q = -half * half;
+  T term = lead, sum = lead;
+  for (int kk = 1; kk < 40; ++kk) {
+    term *= q / (T(kk) * T(m + kk));
+    sum += term;
+    if (fabs(term) <= T(1e-17) * fabs(sum)) break;
+  }
+  return sum;
+}
+
+template <typename T>
+__device__ __forceinline__ T bessel_j(int n, T x) {
+  const int m = n < 0 ? -n : n;
+  T v = bessel_series<T>(m, x);
+  return (n < 0 && (m & 1)) ? -v : v;
+}
+
+// Amplitudes of harmonic n at eccentricity e:
+//   a = n pa, b = n sqrt(1-e^2) pb, c = 2 pc  with the Peters-Mathews brackets
+//   pa = J_{n-2} - 2e J_{n-1} + (2/n) J_n + 2e J_{n+1} - J_{n+2},
+//   pb = J_{n-2} - 2 J_n + J_{n+2},  pc = J_n   (argument n e).
+template <typename T>
+__device__ __forceinline__ void harmonic_amps(int n, T e, T out[3]) {
+  const T x = T(n) * e;
+  const T jm2 = bessel_j<T>(n - 2, x), jm1 = bessel_j<T>(n - 1, x), j0 = bessel_j<T>(n, x);
+  const T jp1 = bessel_j<T>(n + 1, x), jp2 = bessel_j<T>(n + 2, x);
+  const T pa = jm2 - T(2) * e * jm1 + (T(2) / T(n)) * j0 + T(2) * e * jp1 - jp2;
+  const T pb = jm2 - T(2) * j0 + jp2;
+  out[0] = T(n) * pa;
+  out[1] = T(n) * sqrt(T(1) - e * e) * pb;
+  out[2] = T(2) * j0;
+}
+
+// ----------------------------------------------------- interval polynomials
+// Cubic Hermite p(s) = c0 + c1 s + c2 s^2 + c3 s^3 on s in [0,1] from values
+// y0, y1 and rates r0, r1 over an interval of length h.
+__device__ __forceinline__ void hermite(double y0, double d, double r0, double r1, double h, double c[4]) {
+  c[0] = y0;
+  c[1] = h * r0;
+  c[2] = 3.0 * d - h * (2.0 * r0 + r1);
+  c[3] = h * (r0 + r1) - 2.0 * d;
+}
+
+struct IvD {           // FP64 interval data
+  double ph[4], gm[4], al[4], am[4], ec[4];
+};
+
+struct IvM {           // mixed interval data: fixed-point phases + FP32 corrections
+  unsigned long long ph_base, gm_base, al_base;
+  long long ph_inc, gm_inc, al_inc;   // cycles per sample, Q0.64
+  float ph_c[2], gm_c[2], al_c[2];    // s^2, s^3 coefficients [cycles]
+  float am[4];
+  double ec[4];
+};
+
+__device__ __forceinline__ double frac0(double hi, double lo) {
+  return (hi - floor(hi)) + lo;
+}
+
+__device__ __forceinline__ void interval_phase(double ahi, double alo, double ar, double bhi, double blo,
+                                               double br, double h, double c[4]) {
+  const double d = (bhi - ahi) + (blo - alo);
+  hermite(frac0(ahi, alo), d, ar, br, h, c);
+}
+
+__device__ void build_iv(const Knot& a, const Knot& b, double h, IvD& o) {
+  interval_phase(a.phd_hi, a.phd_lo, a.phd_rate, b.phd_hi, b.phd_lo, b.phd_rate, h, o.ph);
+  interval_phase(a.gam_hi, a.gam_lo, a.gam_rate, b.gam_hi, b.gam_lo, b.gam_rate, h, o.gm);
+  interval_phase(a.alp_hi, a.alp_lo, a.alp_rate, b.alp_hi, b.alp_lo, b.alp_rate, h, o.al);
+  hermite(a.amp, b.amp - a.amp, a.amp_rate, b.amp_rate, h, o.am);
+  hermite(a.e, b.e - a.e, a.e_rate, b.e_rate, h, o.ec);
+}
+
+__device__ __forceinline__ unsigned long long to_q64(double f) {
+  f -= floor(f);                                   // [0, 1)
+  return (unsigned long long)(f * 18446744073709551616.0);
+}
+
+__device__ __forceinline__ long long to_q64s(double f) {   // |f| < 0.5
+  return (long long)llrint(f * 18446744073709551616.0);
+}
+
+__device__ void build_iv_mixed(const Knot& a, const Knot& b, double h, int ks, IvM& o) {
+  double c[4];
+  interval_phase(a.phd_hi, a.phd_lo, a.phd_rate, b.phd_hi, b.phd_lo, b.phd_rate, h, c);
+  o.ph_base = to_q64(c[0]);
+  o.ph_inc = to_q64s(c[1] / ks);
+  o.ph_c[0] = (float)c[2];
+  o.ph_c[1] = (float)c[3];
+  interval_phase(a.gam_hi, a.gam_lo, a.gam_rate, b.gam_hi, b.gam_lo, b.gam_rate, h, c);
+  o.gm_base = to_q64(c[0]);
+  o.gm_inc = to_q64s(c[1] / ks);
+  o.gm_c[0] = (float)c[2];
+  o.gm_c[1] = (float)c[3];
+  interval_phase(a.alp_hi, a.alp_lo, a.alp_rate, b.alp_hi, b.alp_lo, b.alp_rate, h, c);
+  o.al_base = to_q64(c[0]);
+  o.al_inc = to_q64s(c[1] / ks);
+  o.al_c[0] = (float)c[2];
+  o.al_c[1] = (float)c[3];
+  hermite(a.amp, b.amp - a.amp, a.amp_rate, b.amp_rate, h, c);
+  for (int q = 0; q < 4; ++q) o.am[q] = (float)c[q];
+  hermite(a.e, b.e - a.e, a.e_rate, b.e_rate, h, o.ec);
+}
+
+template <typename T>
+__device__ __forceinline__ T poly3(const T c[4], T s) {
+  return ((c[3] * s + c[2]) * s + c[1]) * s + c[0];
+}
+
+// fixed-point phase: (base + tau*inc) mod 1 to 32 bits, plus the FP32
+// correction c2 s^2 + c3 s^3; returns the phase in cycles in [-0.5, 0.5)
+__device__ __forceinline__ float phase_fx(unsigned long long base, long long inc, const float c[2], int tau,
+                                          float s) {
+  const unsigned long long p = base + (unsigned long long)tau * (unsigned long long)inc;   // mod 2^64
+  const int top = (int)(unsigned)(p >> 32);
+  float f = (float)top * 2.3283064365386963e-10f;  // 2^-32
+  f += (c[1] * s + c[0]) * s * s;
+  return f - rintf(f);
+}
+
+// --------------------------------------------------- response + harmonics
+template <typename T>
+struct Geo {
+  T nx, ny, nz, sx, sy, sz, e1x, e1y, e1z, e2x, e2y, e2z, cl, sl, sin_ths, cos_ths, sin_phs, cos_phs;
+};
+
+template <typename T>
+__device__ __forceinline__ Geo<T> load_geo(const WalkerC& c) {
+  Geo<T> g;
+  g.nx = T(c.nx); g.ny = T(c.ny); g.nz = T(c.nz);
+  g.sx = T(c.sx); g.sy = T(c.sy); g.sz = T(c.sz);
+  g.e1x = T(c.e1x); g.e1y = T(c.e1y); g.e1z = T(c.e1z);
+  g.e2x = T(c.e2x); g.e2y = T(c.e2y); g.e2z = T(c.e2z);
+  g.cl = T(c.coslam); g.sl = T(c.sinlam);
+  g.sin_ths = T(c.sin_ths); g.cos_ths = T(c.cos_ths); g.sin_phs = T(c.sin_phs); g.cos_phs = T(c.cos_phs);
+  return g;
+}
+
+// (x, y) -> (cos 2 atan2(y, x), sin 2 atan2(y, x)); (1, 0) when degenerate
+template <typename T>
+__device__ __forceinline__ void double_angle(T x, T y, T& c2, T& s2, bool degenerate) {
+  const T r2 = x * x + y * y;
+  if (degenerate || !(r2 > T(0))) {
+    c2 = T(1);
+    s2 = T(0);
+  } else {
+    const T inv = T(1) / r2;
+    c2 = (x * x - y * y) * inv;
+    s2 = T(2) * x * y * inv;
+  }
+}
+
+// Channels at one sample.  cph/sph: cos/sin of the Doppler orbital phase;
+// c2gt/s2gt: of 2 gamma~; ca/sa: of alpha; cb/sb: of phibar; A = x^(2/3);
+// st: tile-relative time in [0, 1) for the harmonic amplitudes bq.
+template <typename T>
+__device__ __forceinline__ void channels(const Geo<T>& g, T cph, T sph, T c2gt, T s2gt, T ca, T sa, T cb,
+                                         T sb, T A, T st, const T* __restrict__ bq, int n_max, T& hI,
+                                         T& hII) {
+  // L(t) = S cos lam + sin lam (e1 cos alpha + e2 sin alpha)
+  const T lx = g.sx * g.cl + g.sl * (g.e1x * ca + g.e2x * sa);
+  const T ly = g.sy * g.cl + g.sl * (g.e1y * ca + g.e2y * sa);
+  const T lz = g.sz * g.cl + g.sl * (g.e1z * ca + g.e2z * sa);
+  const T c = lx * g.nx + ly * g.ny + lz * g.nz;          // L.N
+  // detector normal z_d = z/2 - (sqrt3/2)(cos phibar x + sin phibar y)
+  const T h3 = T(kSqrt3Half);
+  const T zx = -h3 * cb, zy = -h3 * sb, zz = T(0.5);
+  const T zn = zx * g.nx + zy * g.ny + zz * g.nz;         // z_d.N = cos(theta_d)
+  const T lzd = lx * zx + ly * zy + lz * zz;
+  // psi: tan psi = [L.z_d - (L.N)(z_d.N)] / [N.(L x z_d)]
+  const T py = lzd - c * zn;
+  const T cxx = ly * zz - lz * zy, cxy = lz * zx - lx * zz, cxz = lx * zy - ly * zx;
+  const T px = g.nx * cxx + g.ny * cxy + g.nz * cxz;
+  T c2psi, s2psi;
+  double_angle(px, py, c2psi, s2psi, false);
+  // beta: from L x N to L x S about L: cos ~ N.S - cos(lam)(L.N), sin ~ L.(N x S)
+  const T nsx = g.ny * g.sz - g.nz * g.sy, nsy = g.nz * g.sx - g.nx * g.sz, nsz = g.nx * g.sy - g.ny * g.sx;
+  const T xb = (g.nx * g.sx + g.ny * g.sy + g.nz * g.sz) - g.cl * c;
+  const T yb = lx * nsx + ly * nsy + lz * nsz;
+  T c2b, s2b;
+  const T one_c2 = T(1) - c * c;
+  double_angle(xb, yb, c2b, s2b, !(one_c2 > T(1e-24)) || !(g.sl > T(1e-12)));
+  const T c2g = c2gt * c2b - s2gt * s2b;
+  const T s2g = s2gt * c2b + c2gt * s2b;
+  // detector-frame azimuth: phi = phibar + atan2(sqrt3 cos thS + sin thS cos(phibar-phiS), 2 sin thS sin(phibar-phiS))
+  const T cdp = cb * g.cos_phs + sb * g.sin_phs;
+  const T sdp = sb * g.cos_phs - cb * g.sin_phs;
+  T c2x, s2x;
+  double_angle(T(2) * g.sin_ths * sdp, T(1.7320508075688772) * g.cos_ths + g.sin_ths * cdp, c2x, s2x, false);
+  const T c2b_ = cb * cb - sb * sb, s2b_ = T(2) * sb * cb;
+  const T c2p = c2b_ * c2x - s2b_ * s2x;
+  const T s2p = s2b_ * c2x + c2b_ * s2x;
+  // antenna patterns; channel II has phi -> phi - pi/4
+  const T ct = zn, q = T(0.5) * (T(1) + ct * ct);
+  const T fpI = q * c2p * c2psi - ct * s2p * s2psi;
+  const T fxI = q * c2p * s2psi + ct * s2p * c2psi;
+  const T fpII = q * s2p * c2psi + ct * c2p * s2psi;
+  const T fxII = q * s2p * s2psi - ct * c2p * c2psi;
+  // harmonic sum
+  T cn = T(1), sn = T(0), Cs = T(0), Ss = T(0), Rs = T(0);
+  for (int n = 0; n < n_max; ++n) {
+    const T cn1 = cn * cph - sn * sph;
+    sn = sn * cph + cn * sph;
+    cn = cn1;
+    const T* b = bq + 9 * n;
+    const T an = (b[2] * st + b[1]) * st + b[0];
+    const T bn = (b[5] * st + b[4]) * st + b[3];
+    const T rn = (b[8] * st + b[7]) * st + b[6];
+    Cs += an * cn;
+    Ss += bn * sn;
+    Rs += rn * cn;
+  }
+  const T hp = A * ((T(1) + c * c) * (Cs * c2g - Ss * s2g) + one_c2 * Rs);
+  const T hx = T(-2) * c * A * (Ss * c2g + Cs * s2g);
+  hI = h3 * (fpI * hp + fxI * hx);
+  hII = h3 * (fpII * hp + fxII * hx);
+}
+
+// Bessel amplitude fit for the tile: nodes at tile-relative time 0, 1/2, 1.
+template <typename T, typename IV>
+__device__ __forceinline__ void tile_harmonics(const IV* iv, int ni, int64_t j0, int64_t kfirst, int ks,
+                                               int n_max, T* bnode, T* bq) {
+  const int t = threadIdx.x;
+  if (t < 3 * n_max) {
+    const int node = t / n_max, n = t % n_max + 1;
+    const int64_t jn = j0 + (kTile / 2) * node;
+    int64_t ki = jn / ks - kfirst;
+    if (ki > ni - 1) ki = ni - 1;
+    const double s = (double)(jn - (kfirst + ki) * ks) / (double)ks;
+    const double e = poly3<double>(iv[ki].ec, s);
+    T out[3];
+    harmonic_amps<T>(n, T(e), out);
+    bnode[(node * 32 + (n - 1)) * 3 + 0] = out[0];
+    bnode[(node * 32 + (n - 1)) * 3 + 1] = out[1];
+    bnode[(node * 32 + (n - 1)) * 3 + 2] = out[2];
+  }
+  __syncthreads();
+  if (t < 3 * n_max) {
+    const int n = t / 3, f = t % 3;
+    const T f0 = bnode[(0 * 32 + n) * 3 + f], fh = bnode[(1 * 32 + n) * 3 + f], f1 = bnode[(2 * 32 + n) * 3 + f];
+    bq[9 * n + 3 * f + 0] = f0;
+    bq[9 * n + 3 * f + 1] = T(-3) * f0 + T(4) * fh - f1;
+    bq[9 * n + 3 * f + 2] = T(2) * f0 - T(4) * fh + T(2) * f1;
+  }
+}
+
+// ------------------------------------------------------------- kernels
+__global__ void __launch_bounds__(kTile) k2_wave_f64(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
+                                                     int64_t n, double dt, double t0, int ks, int n_max,
+                                                     double2* __restrict__ z, int unit_scale) {
+  __shared__ IvD iv[kTile / 64];
+  __shared__ double bnode[3 * 32 * 3];
+  __shared__ double bq[32 * 9];
+  __shared__ double fb0;
+  const int wk = blockIdx.y;
+  const WalkerC& C = wcs[wk];
+  const int64_t nk = n / ks;
+  const Knot* kn = knots + (int64_t)wk * (nk + 1);
+  const int64_t j0 = (int64_t)blockIdx.x * kTile;
+  const int64_t kfirst = j0 / ks;
+  const int ni = ks >= kTile ? 1 : kTile / ks;
+  const int t = threadIdx.x;
+  const double h = (double)ks * dt;
+  if (t < ni) build_iv(kn[kfirst + t], kn[kfirst + t + 1], h, iv[t]);
+  if (t == 32) {
+    double f = (t0 + (double)j0 * dt) / kYear;
+    fb0 = f - floor(f);
+  }
+  __syncthreads();
+  tile_harmonics<double, IvD>(iv, ni, j0, kfirst, ks, n_max, bnode, bq);
+  __syncthreads();
+
+  const int64_t j = j0 + t;
+  double2 out = make_double2(0.0, 0.0);
+  if (j < C.j_plunge) {
+    const int ki = ks >= kTile ? 0 : t / ks;
+    const double s = (double)(j - (kfirst + ki) * ks) / (double)ks;
+    const IvD& v = iv[ki];
+    double fph = poly3<double>(v.ph, s);
+    fph -= rint(fph);
+    double fgm = 2.0 * poly3<double>(v.gm, s);
+    fgm -= rint(fgm);
+    double fal = poly3<double>(v.al, s);
+    fal -= rint(fal);
+    const double A = poly3<double>(v.am, s);
+    double fb = fb0 + (double)t * (dt / kYear);
+    fb -= rint(fb);
+    double sph, cph, s2g, c2g, sa, ca, sb, cb;
+    sincospi(2.0 * fph, &sph, &cph);
+    sincospi(2.0 * fgm, &s2g, &c2g);
+    sincospi(2.0 * fal, &sa, &ca);
+    sincospi(2.0 * fb, &sb, &cb);
+    const Geo<double> g = load_geo<double>(C);
+    double hI, hII;
+    channels<double>(g, cph, sph, c2g, s2g, ca, sa, cb, sb, A, (double)t / kTile, bq, n_max, hI, hII);
+    if (unit_scale) {
+      hI *= C.amp_scale;
+      hII *= C.amp_scale;
+    }
+    out = make_double2(hI, hII);
+  }
+  z[(int64_t)wk * n + j] = out;
+}
+
+__global__ void __launch_bounds__(kTile) k2_wave_mixed(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
+                                                       int64_t n, double dt, double t0, int ks, int n_max,
+                                                       float2* __restrict__ z, int unit_scale) {
+  __shared__ IvM iv[kTile / 64];
+  __shared__ float bnode[3 * 32 * 3];
+  __shared__ float bq[32 * 9];
+  __shared__ float fb0;
+  const int wk = blockIdx.y;
+  const WalkerC& C = wcs[wk];
+  const int64_t nk = n / ks;
+  const Knot* kn = knots + (int64_t)wk * (nk + 1);
+  const int64_t j0 = (int64_t)blockIdx.x * kTile;
+  const int64_t kfirst = j0 / ks;
+  const int ni = ks >= kTile ? 1 : kTile / ks;
+  const int t = threadIdx.x;
+  const double h = (double)ks * dt;
+  if (t < ni) build_iv_mixed(kn[kfirst + t], kn[kfirst + t + 1], h, ks, iv[t]);
+  if (t == 32) {
+    double f = (t0 + (double)j0 * dt) / kYear;
+    fb0 = (float)(f - floor(f));
+  }
+  __syncthreads();
+  tile_harmonics<float, IvM>(iv, ni, j0, kfirst, ks, n_max, bnode, bq);
+  __syncthreads();
+
+  const int64_t j = j0 + t;
+  float2 out = make_float2(0.f, 0.f);
+  if (j < C.j_plunge) {
+    const int ki = ks >= kTile ? 0 : t / ks;
+    const int tau = (int)(j - (kfirst + ki) * ks);
+    const float s = (float)tau / (float)ks;
+    const IvM& v = iv[ki];
+    const float fph = phase_fx(v.ph_base, v.ph_inc, v.ph_c, tau, s);
+    float c2[2] = {2.f * v.gm_c[0], 2.f * v.gm_c[1]};
+    const float fgm = phase_fx(v.gm_base << 1, (long long)((unsigned long long)v.gm_inc << 1), c2, tau, s);
+    const float fal = phase_fx(v.al_base, v.al_inc, v.al_c, tau, s);
+    const float A = poly3<float>(v.am, s);
+    float fb = fb0 + (float)t * (float)(dt / kYear);
+    fb -= rintf(fb);
+    float sph, cph, s2g, c2g, sa, ca, sb, cb;
+    sincospif(2.f * fph, &sph, &cph);
+    sincospif(2.f * fgm, &s2g, &c2g);
+    sincospif(2.f * fal, &sa, &ca);
+    sincospif(2.f * fb, &sb, &cb);
+    const Geo<float> g = load_geo<float>(C);
+    float hI, hII;
+    channels<float>(g, cph, sph, c2g, s2g, ca, sa, cb, sb, A, (float)t / kTile, bq, n_max, hI, hII);
+    if (unit_scale) {
+      hI *= (float)C.amp_scale;
+      hII *= (float)C.amp_scale;
+    }
+    out = make_float2(hI, hII);
+  }
+  z[(int64_t)wk * n + j] = out;
+}
+
+void launch_wave(const Knot* knots, const WalkerC* wc, int w, int64_t n, double dt, double t0,
+                 const OptsN& o, void* z, bool unit_scale, cudaStream_t s) {
+  if (w <= 0) return;
+  dim3 grid((unsigned)(n / kTile), (unsigned)w);
+  if (o.precision == 0)
+    k2_wave_f64<<<grid, kTile, 0, s>>>(knots, wc, n, dt, t0, o.ks, o.n_max, (double2*)z, unit_scale ? 1 : 0);
+  else
+    k2_wave_mixed<<<grid, kTile, 0, s>>>(knots, wc, n, dt, t0, o.ks, o.n_max, (float2*)z, unit_scale ? 1 : 0);
+}
+
+}  // namespace emri

@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark: batched AK log-likelihoods per second at 2^21 samples.
+
+Workload (one "step"): one MCMC ensemble step of the 1024-walker ensemble
+configuration -- 1024 walkers scattered N(0, 1e-4) about an injected
+source, 2^21 samples at dt = 15 s (~1 yr), harmonics n <= 20, two channels,
+seeded data at SNR 50 -- evaluated with emri_loglike_batch in FP64 end to
+end.  The headline ``value`` is lnL/s of that FP64 step over all ranks; the
+mixed-precision step on the same walkers is reported beside it, with its
+largest |lnL_mixed - lnL_fp64|.
+
+Inputs are resident in HBM when a timed step starts; between timed steps
+a 512 MiB buffer is written to flush L2 (untimed).  ``e2e`` repeats the FP64
+measurement through the C-ABI with host buffers: the walker parameters are
+copied from pinned host memory and the lnL copied back inside the timed
+region.  Multi-GPU (torchrun): every rank evaluates its own ensemble step on
+its own GPU (walkers are independent units; no collective on the data path)
+and the max time over ranks is used.
+
+``--impl reference`` times the CPU oracle (the plain reference
+implementation) on the same workload, a bounded sample of walkers per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "AK log-likelihoods/sec at 2^21 samples (mixed vs FP64, same GPU); p50/p99 latency"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 / FP32 vector peaks of a GB300 derived from unit counts and clock:
+# 152 SMs x 2 FP64 FMA/clk (resp. 128 FP32 FMA/clk) x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--walkers", type=int, default=1024)
+    ap.add_argument("--logn", type=int, default=21)
+    ap.add_argument("--n-max", type=int, default=20)
+    ap.add_argument("--cpu-walkers", type=int, default=0, help="oracle sample size (0: one per core)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                    rows.append(f)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        mx = float(rows[0][2])
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()) if rows else None,
+                "reasons": reasons}
+
+
+# ------------------------------------------------------------- workload
+def build_workload(ctx, args, seed_offset=0):
+    """Walkers, resident dataset and device buffers of the ensemble step.
+
+    Data: the injection's unit-distance waveform and spectrum from the
+    library's own waveform and FFT calls, scaled to SNR 50 and added to the
+    seeded noise; the injection's redshift is set from the target distance
+    with the library's prologue (bisection)."""
+    import torch
+    from paper_2311_17174_gb300 import emri, inputs as I
+
+    n = 1 << args.logn
+    wl = I.config_c2(walkers=args.walkers, n=n, n_max=args.n_max)
+    g = emri.grid(n, wl.dt)
+    psd = I.psd_bc04(n, wl.dt)
+    dev = f"cuda:{torch.cuda.current_device()}"
+    inj = torch.tensor(wl.injection[:, None].copy(), dtype=torch.float64, device=dev)
+    z = torch.zeros((1, n), dtype=torch.complex128, device=dev)
+    o64 = emri.opts(precision=emri.FP64, n_max=wl.n_max)
+    ctx.ak_waveform(g, inj, o64, z)
+    ctx.fft_batch(z, n, 1, emri.FP64, -1)
+    torch.cuda.synchronize()
+    H = z[0].cpu().numpy()
+    probe = ctx.dataset(g, H, psd, wl.fmin, 1.0 / (2 * wl.dt))
+    rho_u = float(np.sqrt(probe.dd()))
+    probe.close()
+    target = rho_u / wl.snr
+    out = torch.zeros((6, 1), dtype=torch.float64, device=dev)
+
+    def dgw(zz):
+        t = wl.injection.copy()
+        t[I.I_Z] = zz
+        ctx.prologue(g, torch.tensor(t[:, None].copy(), dtype=torch.float64, device=dev), o64, out)
+        torch.cuda.synchronize()
+        return float(out[2, 0])
+
+    z_inj = I.solve_distance(target, dgw)
+    data = H * (wl.snr / rho_u) + I.noise_spectrum(wl.noise_seed + seed_offset, psd, n, wl.dt)
+    ds = ctx.dataset(g, data, psd, wl.fmin, 1.0 / (2 * wl.dt))
+    theta = wl.theta.copy()
+    theta[:, I.I_Z] *= z_inj / wl.injection[I.I_Z]
+    return wl, ds, theta, z_inj
+
+
+def time_steps(ctx, ds, theta_dev, o, lnl, steps, warmup, flush, barrier):
+    import torch
+    for _ in range(warmup):
+        ctx.loglike_batch(ds, theta_dev, o, lnl)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.loglike_batch(ds, theta_dev, o, lnl)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return times
+
+
+def flop_model(n_max: int) -> float:
+    """Algorithmic FP64 flops per sample of the factored harmonic sum and
+    response (see the design notes): 24 per harmonic (rotation 6, three
+    quadratic amplitudes 12, three accumulations 6) plus 280 per sample
+    (phases, four sincos, geometry, antenna patterns, channel sums)."""
+    return 24.0 * n_max + 280.0
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_sample(theta, wl, data_fd, psd, walkers: int, threads: int):
+    import oracle as O
+    w = O.weights(psd, wl.n, wl.dt, wl.fmin, 1.0 / (2 * wl.dt))
+    t0 = time.perf_counter()
+    O.loglike(theta[:walkers], wl.n, wl.dt, data_fd, w, O.Opts(n_max=wl.n_max), nthreads=threads)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(args, wl, theta, data_fd, psd):
+    cores = os.cpu_count() or 1
+    walkers = args.cpu_walkers or cores
+    threads = min(walkers, cores)
+    secs = oracle_sample(theta, wl, data_fd, psd, walkers, threads)
+    return {"value": walkers / secs, "unit": "lnL/s", "cores": threads, "kind": "oracle",
+            "sample": f"{walkers} walkers of the ensemble step, full 2^{args.logn} samples, n<=20, FP64/long "
+                      f"double oracle, OpenMP over walkers on {threads} host threads, {secs:.1f} s"}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle on the same workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2311_17174_gb300 import inputs as I
+    import oracle as O
+    n = 1 << args.logn
+    wl = I.config_c2(walkers=args.walkers, n=n, n_max=args.n_max)
+    psd = I.psd_bc04(n, wl.dt)
+    data = I.noise_spectrum(wl.noise_seed, psd, n, wl.dt)
+    cores = os.cpu_count() or 1
+    walkers = args.cpu_walkers or cores
+    threads = min(walkers, cores)
+    O.build()
+    for _ in range(args.warmup):
+        oracle_sample(wl.theta, wl, data, psd, min(walkers, threads), threads)
+    secs = [oracle_sample(wl.theta, wl, data, psd, walkers, threads) for _ in range(args.steps)]
+    tot = sum(secs)
+    value = walkers * args.steps / tot
+    line = {"metric": METRIC, "value": value, "unit": "lnL/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": wl.name, "walkers_per_step": walkers, "samples": n, "n_max": wl.n_max,
+                       "note": "each step is a bounded sample of the ensemble step's walkers"},
+            "cpu_baseline": {"value": value, "unit": "lnL/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{walkers} walkers per step, full length, {threads} threads"},
+            "e2e": {"value": value, "unit": "lnL/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2311_17174_gb300 import emri
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    ctx = emri.Context(local)
+    wl, ds, theta, z_inj = build_workload(ctx, args, seed_offset=rank)
+    W = theta.shape[0]
+    dev = f"cuda:{local}"
+    theta_dev = torch.tensor(theta.T.copy(), dtype=torch.float64, device=dev)
+    lnl = torch.zeros(W, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    o64 = emri.opts(precision=emri.FP64, n_max=wl.n_max)
+    omix = emri.opts(precision=emri.MIXED, n_max=wl.n_max)
+
+    # ---- FP64 headline
+    clocks = ClockSampler(local)
+    launches0 = ctx.launches()
+    ctx.profile(True)
+    for _ in range(args.warmup):
+        ctx.loglike_batch(ds, theta_dev, o64, lnl)
+    torch.cuda.synchronize()
+    ctx.profile(True)   # reset: keep only the timed steps
+    launches0 = ctx.launches()
+    clocks.start()
+    times = time_steps(ctx, ds, theta_dev, o64, lnl, args.steps, 0, flush, barrier)
+    clk = clocks.stop()
+    launches = ctx.launches() - launches0
+    ktimes = ctx.kernel_times()
+    ctx.profile(False)
+    lnl64 = lnl.cpu().numpy().copy()
+    tot_ms = float(sum(times))
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = W * world * args.steps / (tot_ms / 1e3)
+
+    # ---- mixed precision on the same walkers
+    mixed = None
+    if not args.no_mixed:
+        ctx.profile(True)
+        tm = time_steps(ctx, ds, theta_dev, omix, lnl, args.steps, 2, flush, barrier)
+        kt_mix = ctx.kernel_times()
+        ctx.profile(False)
+        mt = float(sum(tm))
+        if world > 1:
+            t = torch.tensor([mt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            mt = float(t.item())
+        lm = lnl.cpu().numpy()
+        mixed = {"value": W * world * args.steps / (mt / 1e3), "unit": "lnL/s", "ms_per_step": mt / args.steps,
+                 "dlnl_max_vs_fp64": float(np.max(np.abs(lm - lnl64))),
+                 "kernels_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in kt_mix.items() if v[1]}}
+
+    # ---- end to end through the C-ABI with host buffers (FP64)
+    th_host = torch.tensor(theta.T.copy(), dtype=torch.float64).pin_memory()
+    out_host = torch.zeros(W, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        theta_dev.copy_(th_host, non_blocking=True)
+        ctx.loglike_batch(ds, theta_dev, o64, lnl)
+        out_host.copy_(lnl, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_tot = float(sum(e2e_ms))
+    if world > 1:
+        t = torch.tensor([e2e_tot], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_tot = float(t.item())
+
+    # ---- roofline of the dominant kernel (FP64 step)
+    per_step = {k: v[0] / args.steps for k, v in ktimes.items() if v[1]}
+    dom = max(per_step, key=per_step.get)
+    roof = None
+    if dom == "wave":
+        launches_wave = ktimes["wave"][1]
+        avg_ms = ktimes["wave"][0] / launches_wave
+        walkers_per_launch = W * args.steps / launches_wave
+        flops = flop_model(wl.n_max) * wl.n * walkers_per_launch
+        achieved = flops / (avg_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k2_wave_f64",
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (FP64 vector unit)",
+                "flops_per_launch": flops, "avg_launch_ms": avg_ms}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "kernel": dom}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            import oracle
+            oracle.build()
+            cpu = cpu_baseline(args, wl, theta, ds_data_host(ctx, wl, z_inj), psd_host(wl))
+        except Exception as exc:  # the baseline is reported, not required
+            cpu = {"value": None, "unit": "lnL/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"failed: {exc}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "lnL/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "walkers": W, "samples": wl.n, "dt": wl.dt, "n_max": wl.n_max,
+                       "snr": wl.snr, "precision": "fp64 end to end", "l2": "flushed between timed steps",
+                       "parallelism": f"replicas x{world} (walker blocks per GPU)"},
+            "mixed": mixed,
+            "e2e": {"value": W * world * args.steps / (e2e_tot / 1e3), "unit": "lnL/s",
+                    "h2d_bytes_per_step": int(th_host.numel() * 8), "d2h_bytes_per_step": int(out_host.numel() * 8)},
+            "gpu_launches": int(launches),
+            "kernels_ms_per_step": {k: round(v, 3) for k, v in per_step.items()},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    ds.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def psd_host(wl):
+    from paper_2311_17174_gb300 import inputs as I
+    return I.psd_bc04(wl.n, wl.dt)
+
+
+def ds_data_host(ctx, wl, z_inj):
+    """Data spectrum for the CPU baseline: the same seeded noise (the oracle's
+    timing does not depend on the injection's amplitude)."""
+    from paper_2311_17174_gb300 import inputs as I
+    return I.noise_spectrum(wl.noise_seed, psd_host(wl), wl.n, wl.dt)
+
+
+if __name__ == "__main__":
+    main()

@@ -141,6 +141,29 @@ int emri_ctx_launches(const emri_ctx* ctx, int64_t* count);
  * budget; either output may be NULL. */
 int emri_ctx_memory(const emri_ctx* ctx, size_t* used, size_t* budget);
 
+/* Kernel kinds of the likelihood path, for per-kernel timing. */
+enum emri_kernel {
+  EMRI_K_PROLOGUE = 0,   /* S0 per-walker constants                      */
+  EMRI_K_DELAY = 1,      /* S0 per-walker delay table                    */
+  EMRI_K_ORBIT = 2,      /* S1 orbit integration                         */
+  EMRI_K_WAVE = 3,       /* S2-S4 harmonic sum and response              */
+  EMRI_K_FFT1 = 4,       /* S5 FFT pass 1                                */
+  EMRI_K_FFT2_IP = 5,    /* S5-S6 FFT pass 2 fused with inner products   */
+  EMRI_K_FINALIZE = 6,   /* S7 reduction and lnL                         */
+  EMRI_K_FFT2_STORE = 7, /* S5 FFT pass 2 to natural order (emri_fft_batch) */
+  EMRI_NKERNEL = 8
+};
+
+/* Enable (1) or disable (0) per-kernel timing on this context and reset the
+ * accumulators.  While enabled, every launch of the likelihood path is
+ * bracketed by CUDA events recorded on the stream it is launched on. */
+int emri_ctx_profile(emri_ctx* ctx, int enable);
+
+/* Wait for the recorded events and return, per enum emri_kernel, the summed
+ * device time [ms] and the launch count since profiling was enabled (host
+ * arrays of EMRI_NKERNEL entries; either may be NULL). */
+int emri_ctx_kernel_times(emri_ctx* ctx, double* ms, int64_t* launches);
+
 /* Resident dataset (paper Sec. 3: the waveform of the fiducial parameters is
  * the mock data the sampler compares against; the PSD weights Eq. (8)).
  *   data:  data_kind 0: packed spectrum D_k = DFT(d_I + i d_II) in natural

@@ -361,11 +361,15 @@ static void geometry_at(const geom* g, double t, R alpha, double out[6]) {
   cross3(L, zd, lxz);
   double py = dot3(L, zd) - c * dot3(zd, N), px = dot3(N, lxz);
   double psi = (fabs(px) + fabs(py) > 1e-300) ? atan2(py, px) : 0.0;
+  /* beta: angle about L from L x N to L x S.  L x S = sin(lam) (p x S) with
+   * p = e1 cos a + e2 sin a, so the direction p x S is used: the same angle
+   * for sin(lam) > 0, and well conditioned as lam -> 0. */
+  double pv[3] = {g->e1x * ca + g->e2x * sa, g->e1y * ca + g->e2y * sa, g->e1z * ca + g->e2z * sa};
   double u[3], v[3], uv[3];
   cross3(L, N, u);
-  cross3(L, S, v);
-  double nu_ = sqrt(dot3(u, u)), nv = sqrt(dot3(v, v)), beta = 0.0;
-  if (nu_ > 1e-12 && nv > 1e-12) {
+  cross3(pv, S, v);
+  double nu_ = sqrt(dot3(u, u)), beta = 0.0;
+  if (nu_ > 1e-12) {
     cross3(u, v, uv);
     beta = atan2(dot3(L, uv), dot3(u, v));
   }

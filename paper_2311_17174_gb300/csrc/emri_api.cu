@@ -208,9 +208,10 @@ int run_loglike(emri_ctx* ctx, const emri_dataset* ds, const double* theta, int6
   const bool f32 = o.precision != 0;
   const size_t cs = f32 ? sizeof(float2) : sizeof(double2);
   int64_t nl = 0;
-  launch_prologue(theta, ld, w, p.n, ds->dt, o, ctx->gl, b.wc, s);
-  launch_delay_table(b.wc, w, p.n1, p.n2, f32, b.dtab, s);
-  launch_orbit(b.wc, w, p.n, ds->dt, ds->t0, o, b.knots, s);
+  Profiler* pf = &ctx->prof;
+  { KTimer t(pf, EMRI_K_PROLOGUE, s); launch_prologue(theta, ld, w, p.n, ds->dt, o, ctx->gl, b.wc, s); }
+  { KTimer t(pf, EMRI_K_DELAY, s); launch_delay_table(b.wc, w, p.n1, p.n2, f32, b.dtab, s); }
+  { KTimer t(pf, EMRI_K_ORBIT, s); launch_orbit(b.wc, w, p.n, ds->dt, ds->t0, o, b.knots, s); }
   nl += 3;
   const int64_t nk = p.n / o.ks;
   const void* dperm = f32 ? (const void*)ds->d_perm32 : (const void*)ds->d_perm;
@@ -219,12 +220,21 @@ int run_loglike(emri_ctx* ctx, const emri_dataset* ds, const double* theta, int6
   const double hh_scale = f32 ? 1.0 / ds->w_scale : 1.0;
   for (int i0 = 0; i0 < w; i0 += wave) {
     const int ww = std::min(wave, w - i0);
-    launch_wave(b.knots + (size_t)i0 * (nk + 1), b.wc + i0, ww, p.n, ds->dt, ds->t0, o, b.z, false, s);
-    launch_fft_pass1(b.z, ww, p, f32, -1, ctx->tw, s);
-    launch_fft_pass2_ip(b.z, ww, p, f32, ctx->tw, b.wc + i0, b.dtab + (size_t)i0 * p.n1 * cs, dperm, wperm,
-                        b.partial + (size_t)i0 * p.n2, s);
-    launch_finalize(b.partial + (size_t)i0 * p.n2, p.n2, b.wc + i0, ww, dh_scale, hh_scale, lnl + i0,
-                    dh ? dh + i0 : nullptr, hh ? hh + i0 : nullptr, status ? status + i0 : nullptr, s);
+    {
+      KTimer t(pf, EMRI_K_WAVE, s);
+      launch_wave(b.knots + (size_t)i0 * (nk + 1), b.wc + i0, ww, p.n, ds->dt, ds->t0, o, b.z, false, ctx->bt, s);
+    }
+    { KTimer t(pf, EMRI_K_FFT1, s); launch_fft_pass1(b.z, ww, p, f32, -1, ctx->tw, s); }
+    {
+      KTimer t(pf, EMRI_K_FFT2_IP, s);
+      launch_fft_pass2_ip(b.z, ww, p, f32, ctx->tw, b.wc + i0, b.dtab + (size_t)i0 * p.n1 * cs, dperm, wperm,
+                          b.partial + (size_t)i0 * p.n2, s);
+    }
+    {
+      KTimer t(pf, EMRI_K_FINALIZE, s);
+      launch_finalize(b.partial + (size_t)i0 * p.n2, p.n2, b.wc + i0, ww, dh_scale, hh_scale, lnl + i0,
+                      dh ? dh + i0 : nullptr, hh ? hh + i0 : nullptr, status ? status + i0 : nullptr, s);
+    }
     nl += 4;
   }
   if (launches) *launches = nl;
@@ -234,6 +244,74 @@ int run_loglike(emri_ctx* ctx, const emri_dataset* ds, const double* theta, int6
 }
 
 }  // namespace emri
+
+// -------------------------------------------------------------- profiler
+cudaEvent_t Profiler::get() {
+  cudaEvent_t e;
+  if (!pool.empty()) {
+    e = pool.back();
+    pool.pop_back();
+  } else {
+    cudaEventCreate(&e);
+  }
+  return e;
+}
+
+cudaEvent_t Profiler::begin(cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(mu);
+  cudaEvent_t e = get();
+  cudaEventRecord(e, s);
+  return e;
+}
+
+void Profiler::end(int kind, cudaEvent_t b, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(mu);
+  cudaEvent_t e = get();
+  cudaEventRecord(e, s);
+  pending.emplace_back(kind, b, e);
+}
+
+void Profiler::drain() {
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto& t : pending) {
+    cudaEventSynchronize(std::get<2>(t));
+    float m = 0.f;
+    cudaEventElapsedTime(&m, std::get<1>(t), std::get<2>(t));
+    ms[std::get<0>(t)] += m;
+    count[std::get<0>(t)] += 1;
+    pool.push_back(std::get<1>(t));
+    pool.push_back(std::get<2>(t));
+  }
+  pending.clear();
+}
+
+void Profiler::reset() {
+  drain();
+  std::lock_guard<std::mutex> lk(mu);
+  for (int i = 0; i < EMRI_NKERNEL; ++i) {
+    ms[i] = 0.0;
+    count[i] = 0;
+  }
+}
+
+extern "C" int emri_ctx_profile(emri_ctx* c, int enable) {
+  if (!c) return set_err(EMRI_EINVAL, "NULL context");
+  cudaSetDevice(c->device);
+  c->prof.reset();
+  c->prof.on = enable != 0;
+  return EMRI_OK;
+}
+
+extern "C" int emri_ctx_kernel_times(emri_ctx* c, double* ms, int64_t* launches) {
+  if (!c) return set_err(EMRI_EINVAL, "NULL context");
+  cudaSetDevice(c->device);
+  c->prof.drain();
+  for (int i = 0; i < EMRI_NKERNEL; ++i) {
+    if (ms) ms[i] = c->prof.ms[i];
+    if (launches) launches[i] = c->prof.count[i];
+  }
+  return EMRI_OK;
+}
 
 // ===================================================================== ctx
 extern "C" int emri_ctx_create(int device, size_t budget, emri_ctx** out) {
@@ -256,7 +334,7 @@ extern "C" int emri_ctx_create(int device, size_t budget, emri_ctx** out) {
     return cuda_err(e2, "cudaStreamCreate");
   }
   // twiddle and quadrature tables
-  size_t tb = 4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8 + 64 * 8;
+  size_t tb = 4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8 + 64 * 8 + 35 * 32 * 12 + 35 * 12 + 256;
   char* p = nullptr;
   e2 = cudaMalloc(&p, tb);
   if (e2 != cudaSuccess) {
@@ -271,9 +349,17 @@ extern "C" int emri_ctx_create(int device, size_t budget, emri_ctx** out) {
   c->tw.ta32 = (float2*)(p + 4096 * 16 + 1024 * 16);
   c->tw.tb32 = (float2*)(p + 4096 * 16 + 1024 * 16 + 4096 * 8);
   c->gl = (double*)(p + 4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8);
+  {
+    char* q = (char*)(c->gl + 64);
+    c->bt.r64 = (double*)q;
+    c->bt.f64 = (double*)(q + 35 * 32 * 8);
+    c->bt.r32 = (float*)(q + 35 * 32 * 8 + 35 * 8);
+    c->bt.f32 = (float*)(q + 35 * 32 * 8 + 35 * 8 + 35 * 32 * 4);
+  }
   double glh[64];
   gauss_legendre32(glh, glh + 32);
   launch_twiddle_init(c->tw, c->stream);
+  launch_bessel_tables(c->bt, c->stream);
   cudaMemcpyAsync(c->gl, glh, sizeof glh, cudaMemcpyHostToDevice, c->stream);
   fft_set_smem_limits();
   e2 = cudaStreamSynchronize(c->stream);
@@ -284,7 +370,7 @@ extern "C" int emri_ctx_create(int device, size_t budget, emri_ctx** out) {
     delete c;
     return cuda_err(e2, "context tables");
   }
-  c->launches = 1;
+  c->launches = 2;
   *out = c;
   return EMRI_OK;
 }
@@ -293,6 +379,9 @@ extern "C" int emri_ctx_destroy(emri_ctx* c) {
   if (!c) return EMRI_OK;
   cudaSetDevice(c->device);
   serve_shutdown(c);
+  c->prof.on = false;
+  c->prof.drain();
+  for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
   c->ws.destroy(c);
   if (c->tables) cudaFree(c->tables);
   cudaStreamDestroy(c->stream);
@@ -494,7 +583,7 @@ extern "C" int emri_ak_waveform(emri_ctx* ctx, const emri_grid* grid, const doub
   Knot* kn = cv.take<Knot>((size_t)w * (nk + 1));
   launch_prologue(theta, w, w, grid->n, grid->dt, o, ctx->gl, wc, s);
   launch_orbit(wc, w, grid->n, grid->dt, grid->t0, o, kn, s);
-  launch_wave(kn, wc, w, grid->n, grid->dt, grid->t0, o, z_out, true, s);
+  launch_wave(kn, wc, w, grid->n, grid->dt, grid->t0, o, z_out, true, ctx->bt, s);
   if (status) cudaMemcpy2DAsync(status, sizeof(uint32_t), &wc[0].status, sizeof(WalkerC), sizeof(uint32_t), w,
                                 cudaMemcpyDeviceToDevice, s);
   ctx->ws.release(s);

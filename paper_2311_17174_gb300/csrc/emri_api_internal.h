@@ -6,6 +6,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <vector>
 
 #include "../../include/emri.h"
 #include "emri_internal.h"
@@ -55,6 +56,36 @@ struct LoglikeBufs {
   char* z;
 };
 
+// Per-kernel event timing (enabled by emri_ctx_profile).
+struct Profiler {
+  bool on = false;
+  std::mutex mu;
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> pending;
+  std::vector<cudaEvent_t> pool;
+  double ms[EMRI_NKERNEL] = {};
+  int64_t count[EMRI_NKERNEL] = {};
+  cudaEvent_t get();
+  // bracket one launch: begin() before, end() after
+  cudaEvent_t begin(cudaStream_t s);
+  void end(int kind, cudaEvent_t b, cudaStream_t s);
+  void drain();
+  void reset();
+};
+
+// RAII helper: times one launch when profiling is on
+struct KTimer {
+  Profiler* p;
+  int kind;
+  cudaStream_t s;
+  cudaEvent_t b = nullptr;
+  KTimer(Profiler* p_, int k, cudaStream_t s_) : p(p_), kind(k), s(s_) {
+    if (p && p->on) b = p->begin(s);
+  }
+  ~KTimer() {
+    if (b) p->end(kind, b, s);
+  }
+};
+
 // autotuned schedule of one (n, n_max, precision) shape
 struct Plan {
   int ks = 0;
@@ -71,10 +102,12 @@ struct emri_ctx {
   cudaStream_t stream = nullptr;
   char* tables = nullptr;
   emri::Twiddles tw{};
+  emri::BesselTab bt{};
   double* gl = nullptr;
   emri::Workspace ws;
   std::atomic<int64_t> launches{0};
   emri::Server* server = nullptr;
+  emri::Profiler prof;
   std::map<std::tuple<int64_t, int, int>, emri::Plan> plans;   // (n, n_max, precision)
 };
 

@@ -38,6 +38,15 @@ struct Twiddles {
 
 void launch_twiddle_init(Twiddles t, cudaStream_t s);
 
+// Bessel series tables: r[m*32 + k] = 1/(k (m+k)), f[m] = 1/m!, m < 35
+struct BesselTab {
+  double* r64;
+  float* r32;
+  double* f64;
+  float* f32;
+};
+void launch_bessel_tables(BesselTab t, cudaStream_t s);
+
 void launch_prologue(const double* theta, int64_t ld, int w, int64_t n, double dt, const OptsN& o,
                      const double* gl, WalkerC* out, cudaStream_t s);
 void launch_delay_table(const WalkerC* wc, int w, int n1, int n2, bool fp32, void* tab, cudaStream_t s);
@@ -49,7 +58,7 @@ void launch_orbit(WalkerC* wc, int w, int64_t n, double dt, double t0, const Opt
 
 // waveform: z[w][n] (double2 or float2); unit_scale multiplies by mu_s c (cm units)
 void launch_wave(const Knot* knots, const WalkerC* wc, int w, int64_t n, double dt, double t0,
-                 const OptsN& o, void* z, bool unit_scale, cudaStream_t s);
+                 const OptsN& o, void* z, bool unit_scale, const BesselTab& bt, cudaStream_t s);
 
 // FFT pass 1 (columns, in place, with the inter-pass twiddle); sign -1 forward, +1 inverse
 void launch_fft_pass1(void* z, int batch, const FftPlan& p, bool fp32, int sign, const Twiddles& t,

@@ -35,9 +35,11 @@ namespace emri {
 constexpr int kTile = 256;
 
 // --------------------------------------------------------------- Bessel
-// J_m(x) by its power series, m >= 0, for x <= ~0.6 (m + 2).
+// J_m(x) by its power series sum_k (-x^2/4)^k (x/2)^m / (k! (m+k)!), m >= 0;
+// rk[m*32 + k] = 1/(k (m+k)) and ifact[m] = 1/m! come from tables, so a term
+// costs two multiplications.
 template <typename T>
-__device__ __forceinline__ T bessel_series(int m, T x) {
+__device__ __forceinline__ T bessel_series(int m, T x, const T* __restrict__ rk, const T* __restrict__ ifact) {
   const T half = T(0.5) * x;
   T lead = T(1);
   T p = half;
@@ -47,40 +49,67 @@ __device__ __forceinline__ T bessel_series(int m, T x) {
     p *= p;
     k >>= 1;
   }
-  T fact = T(1);
-  for (int i = 2; i <= m; ++i) fact *= T(i);
-  lead /= fact;
+  lead *= ifact[m];
   const T q = -half * half;
+  const T* r = rk + m * 32;
   T term = lead, sum = lead;
-  for (int kk = 1; kk < 40; ++kk) {
-    term *= q / (T(kk) * T(m + kk));
+  for (int kk = 1; kk < 32; ++kk) {
+    term *= q * r[kk];
     sum += term;
     if (fabs(term) <= T(1e-17) * fabs(sum)) break;
   }
   return sum;
 }
 
-template <typename T>
-__device__ __forceinline__ T bessel_j(int n, T x) {
-  const int m = n < 0 ? -n : n;
-  T v = bessel_series<T>(m, x);
-  return (n < 0 && (m & 1)) ? -v : v;
-}
-
 // Amplitudes of harmonic n at eccentricity e:
 //   a = n pa, b = n sqrt(1-e^2) pb, c = 2 pc  with the Peters-Mathews brackets
 //   pa = J_{n-2} - 2e J_{n-1} + (2/n) J_n + 2e J_{n+1} - J_{n+2},
-//   pb = J_{n-2} - 2 J_n + J_{n+2},  pc = J_n   (argument n e).
+//   pb = J_{n-2} - 2 J_n + J_{n+2},  pc = J_n   (argument x = n e).
+// J_{n+2}, J_{n+1} by series, the lower orders by the (stable) downward
+// recurrence J_{m-1} = (2m/x) J_m - J_{m+1}, which also gives J_{-1} = -J_1.
 template <typename T>
-__device__ __forceinline__ void harmonic_amps(int n, T e, T out[3]) {
-  const T x = T(n) * e;
-  const T jm2 = bessel_j<T>(n - 2, x), jm1 = bessel_j<T>(n - 1, x), j0 = bessel_j<T>(n, x);
-  const T jp1 = bessel_j<T>(n + 1, x), jp2 = bessel_j<T>(n + 2, x);
+__device__ __forceinline__ void harmonic_amps(int n, T e, T out[3], const T* __restrict__ rk,
+                                              const T* __restrict__ ifact) {
+  T jm2, jm1, j0, jp1, jp2;
+  if (e < T(1e-12)) {               // J_m(0) = delta_m0
+    jm2 = n == 2 ? T(1) : T(0);
+    jm1 = n == 1 ? T(1) : T(0);
+    j0 = jp1 = jp2 = T(0);
+  } else {
+    const T x = T(n) * e;
+    const T ix = T(1) / x;
+    jp2 = bessel_series<T>(n + 2, x, rk, ifact);
+    jp1 = bessel_series<T>(n + 1, x, rk, ifact);
+    j0 = T(2 * (n + 1)) * ix * jp1 - jp2;
+    jm1 = T(2 * n) * ix * j0 - jp1;
+    jm2 = T(2 * (n - 1)) * ix * jm1 - j0;
+  }
   const T pa = jm2 - T(2) * e * jm1 + (T(2) / T(n)) * j0 + T(2) * e * jp1 - jp2;
   const T pb = jm2 - T(2) * j0 + jp2;
   out[0] = T(n) * pa;
   out[1] = T(n) * sqrt(T(1) - e * e) * pb;
   out[2] = T(2) * j0;
+}
+
+// Reciprocal tables for the series (built once per context).
+__global__ void k_bessel_tables(double* r64, float* r32, double* f64, float* f32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 35 * 32) {
+    const int m = i / 32, k = i % 32;
+    const double v = k == 0 ? 0.0 : 1.0 / ((double)k * (double)(m + k));
+    r64[i] = v;
+    r32[i] = (float)v;
+  }
+  if (i < 35) {
+    double f = 1.0;
+    for (int j = 2; j <= i; ++j) f *= (double)j;
+    f64[i] = 1.0 / f;
+    f32[i] = (float)(1.0 / f);
+  }
+}
+
+void launch_bessel_tables(BesselTab t, cudaStream_t s) {
+  k_bessel_tables<<<(35 * 32 + 255) / 256, 256, 0, s>>>(t.r64, t.r32, t.f64, t.f32);
 }
 
 // ----------------------------------------------------- interval polynomials
@@ -174,6 +203,7 @@ __device__ __forceinline__ float phase_fx(unsigned long long base, long long inc
 template <typename T>
 struct Geo {
   T nx, ny, nz, sx, sy, sz, e1x, e1y, e1z, e2x, e2y, e2z, cl, sl, sin_ths, cos_ths, sin_phs, cos_phs;
+  T ns, ne1, ne2;   // N.S, N.e1, N.e2
 };
 
 template <typename T>
@@ -185,6 +215,9 @@ __device__ __forceinline__ Geo<T> load_geo(const WalkerC& c) {
   g.e2x = T(c.e2x); g.e2y = T(c.e2y); g.e2z = T(c.e2z);
   g.cl = T(c.coslam); g.sl = T(c.sinlam);
   g.sin_ths = T(c.sin_ths); g.cos_ths = T(c.cos_ths); g.sin_phs = T(c.sin_phs); g.cos_phs = T(c.cos_phs);
+  g.ns = T(c.nx * c.sx + c.ny * c.sy + c.nz * c.sz);
+  g.ne1 = T(c.nx * c.e1x + c.ny * c.e1y + c.nz * c.e1z);
+  g.ne2 = T(c.nx * c.e2x + c.ny * c.e2y + c.nz * c.e2z);
   return g;
 }
 
@@ -225,13 +258,14 @@ __device__ __forceinline__ void channels(const Geo<T>& g, T cph, T sph, T c2gt, 
   const T px = g.nx * cxx + g.ny * cxy + g.nz * cxz;
   T c2psi, s2psi;
   double_angle(px, py, c2psi, s2psi, false);
-  // beta: from L x N to L x S about L: cos ~ N.S - cos(lam)(L.N), sin ~ L.(N x S)
-  const T nsx = g.ny * g.sz - g.nz * g.sy, nsy = g.nz * g.sx - g.nx * g.sz, nsz = g.nx * g.sy - g.ny * g.sx;
-  const T xb = (g.nx * g.sx + g.ny * g.sy + g.nz * g.sz) - g.cl * c;
-  const T yb = lx * nsx + ly * nsy + lz * nsz;
+  // beta: angle about L from L x N to L x S = sin(lam) (p x S), p = e1 cos a + e2 sin a:
+  //   cos beta ~ (L x N).(p x S) = sin(lam) N.S - cos(lam) N.p
+  //   sin beta ~ L.((L x N) x (p x S)) = N.(S x p) = cos a N.e2 - sin a N.e1
+  const T xb = g.sl * g.ns - g.cl * (ca * g.ne1 + sa * g.ne2);
+  const T yb = ca * g.ne2 - sa * g.ne1;
   T c2b, s2b;
   const T one_c2 = T(1) - c * c;
-  double_angle(xb, yb, c2b, s2b, !(one_c2 > T(1e-24)) || !(g.sl > T(1e-12)));
+  double_angle(xb, yb, c2b, s2b, !(one_c2 > T(1e-24)));
   const T c2g = c2gt * c2b - s2gt * s2b;
   const T s2g = s2gt * c2b + c2gt * s2b;
   // detector-frame azimuth: phi = phibar + atan2(sqrt3 cos thS + sin thS cos(phibar-phiS), 2 sin thS sin(phibar-phiS))
@@ -268,20 +302,24 @@ __device__ __forceinline__ void channels(const Geo<T>& g, T cph, T sph, T c2gt, 
   hII = h3 * (fpII * hp + fxII * hx);
 }
 
-// Bessel amplitude fit for the tile: nodes at tile-relative time 0, 1/2, 1.
+// Bessel amplitude fit for the tile: nodes at tile-relative sample offsets
+// 0, L/2, L (L = 256, or the last valid offset when the orbit plunges inside
+// the tile), quadratic in st = t / L.
 template <typename T, typename IV>
 __device__ __forceinline__ void tile_harmonics(const IV* iv, int ni, int64_t j0, int64_t kfirst, int ks,
-                                               int n_max, T* bnode, T* bq) {
+                                               int n_max, double span, T* bnode, T* bq, const T* __restrict__ rk,
+                                               const T* __restrict__ ifact) {
   const int t = threadIdx.x;
   if (t < 3 * n_max) {
     const int node = t / n_max, n = t % n_max + 1;
-    const int64_t jn = j0 + (kTile / 2) * node;
-    int64_t ki = jn / ks - kfirst;
+    const double pos = (double)j0 + 0.5 * span * node;
+    int64_t ki = (int64_t)floor(pos / ks) - kfirst;
     if (ki > ni - 1) ki = ni - 1;
-    const double s = (double)(jn - (kfirst + ki) * ks) / (double)ks;
+    if (ki < 0) ki = 0;
+    const double s = (pos - (double)((kfirst + ki) * ks)) / (double)ks;
     const double e = poly3<double>(iv[ki].ec, s);
     T out[3];
-    harmonic_amps<T>(n, T(e), out);
+    harmonic_amps<T>(n, T(e), out, rk, ifact);
     bnode[(node * 32 + (n - 1)) * 3 + 0] = out[0];
     bnode[(node * 32 + (n - 1)) * 3 + 1] = out[1];
     bnode[(node * 32 + (n - 1)) * 3 + 2] = out[2];
@@ -296,10 +334,18 @@ __device__ __forceinline__ void tile_harmonics(const IV* iv, int ni, int64_t j0,
   }
 }
 
+// span of the Bessel fit: the tile, or up to the last sample before a plunge
+__device__ __forceinline__ int tile_span(int64_t j0, int64_t jp) {
+  if (jp >= j0 + kTile) return kTile;
+  const int64_t l = jp - 1 - j0;
+  return l < 1 ? 1 : (int)l;
+}
+
 // ------------------------------------------------------------- kernels
-__global__ void __launch_bounds__(kTile) k2_wave_f64(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
-                                                     int64_t n, double dt, double t0, int ks, int n_max,
-                                                     double2* __restrict__ z, int unit_scale) {
+__global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
+                                                        int64_t n, double dt, double t0, int ks, int n_max,
+                                                        double2* __restrict__ z, int unit_scale,
+                                                        const double* __restrict__ rk, const double* __restrict__ ifact) {
   __shared__ IvD iv[kTile / 64];
   __shared__ double bnode[3 * 32 * 3];
   __shared__ double bq[32 * 9];
@@ -319,7 +365,8 @@ __global__ void __launch_bounds__(kTile) k2_wave_f64(const Knot* __restrict__ kn
     fb0 = f - floor(f);
   }
   __syncthreads();
-  tile_harmonics<double, IvD>(iv, ni, j0, kfirst, ks, n_max, bnode, bq);
+  const int span = tile_span(j0, C.j_plunge);
+  tile_harmonics<double, IvD>(iv, ni, j0, kfirst, ks, n_max, (double)span, bnode, bq, rk, ifact);
   __syncthreads();
 
   const int64_t j = j0 + t;
@@ -344,7 +391,7 @@ __global__ void __launch_bounds__(kTile) k2_wave_f64(const Knot* __restrict__ kn
     sincospi(2.0 * fb, &sb, &cb);
     const Geo<double> g = load_geo<double>(C);
     double hI, hII;
-    channels<double>(g, cph, sph, c2g, s2g, ca, sa, cb, sb, A, (double)t / kTile, bq, n_max, hI, hII);
+    channels<double>(g, cph, sph, c2g, s2g, ca, sa, cb, sb, A, (double)t / span, bq, n_max, hI, hII);
     if (unit_scale) {
       hI *= C.amp_scale;
       hII *= C.amp_scale;
@@ -354,9 +401,10 @@ __global__ void __launch_bounds__(kTile) k2_wave_f64(const Knot* __restrict__ kn
   z[(int64_t)wk * n + j] = out;
 }
 
-__global__ void __launch_bounds__(kTile) k2_wave_mixed(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
-                                                       int64_t n, double dt, double t0, int ks, int n_max,
-                                                       float2* __restrict__ z, int unit_scale) {
+__global__ void __launch_bounds__(kTile, 2) k2_wave_mixed(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
+                                                          int64_t n, double dt, double t0, int ks, int n_max,
+                                                          float2* __restrict__ z, int unit_scale,
+                                                          const float* __restrict__ rk, const float* __restrict__ ifact) {
   __shared__ IvM iv[kTile / 64];
   __shared__ float bnode[3 * 32 * 3];
   __shared__ float bq[32 * 9];
@@ -376,7 +424,8 @@ __global__ void __launch_bounds__(kTile) k2_wave_mixed(const Knot* __restrict__ 
     fb0 = (float)(f - floor(f));
   }
   __syncthreads();
-  tile_harmonics<float, IvM>(iv, ni, j0, kfirst, ks, n_max, bnode, bq);
+  const int span = tile_span(j0, C.j_plunge);
+  tile_harmonics<float, IvM>(iv, ni, j0, kfirst, ks, n_max, (double)span, bnode, bq, rk, ifact);
   __syncthreads();
 
   const int64_t j = j0 + t;
@@ -400,7 +449,7 @@ __global__ void __launch_bounds__(kTile) k2_wave_mixed(const Knot* __restrict__ 
     sincospif(2.f * fb, &sb, &cb);
     const Geo<float> g = load_geo<float>(C);
     float hI, hII;
-    channels<float>(g, cph, sph, c2g, s2g, ca, sa, cb, sb, A, (float)t / kTile, bq, n_max, hI, hII);
+    channels<float>(g, cph, sph, c2g, s2g, ca, sa, cb, sb, A, (float)t / (float)span, bq, n_max, hI, hII);
     if (unit_scale) {
       hI *= (float)C.amp_scale;
       hII *= (float)C.amp_scale;
@@ -411,13 +460,15 @@ __global__ void __launch_bounds__(kTile) k2_wave_mixed(const Knot* __restrict__ 
 }
 
 void launch_wave(const Knot* knots, const WalkerC* wc, int w, int64_t n, double dt, double t0,
-                 const OptsN& o, void* z, bool unit_scale, cudaStream_t s) {
+                 const OptsN& o, void* z, bool unit_scale, const BesselTab& bt, cudaStream_t s) {
   if (w <= 0) return;
   dim3 grid((unsigned)(n / kTile), (unsigned)w);
   if (o.precision == 0)
-    k2_wave_f64<<<grid, kTile, 0, s>>>(knots, wc, n, dt, t0, o.ks, o.n_max, (double2*)z, unit_scale ? 1 : 0);
+    k2_wave_f64<<<grid, kTile, 0, s>>>(knots, wc, n, dt, t0, o.ks, o.n_max, (double2*)z, unit_scale ? 1 : 0,
+                                       bt.r64, bt.f64);
   else
-    k2_wave_mixed<<<grid, kTile, 0, s>>>(knots, wc, n, dt, t0, o.ks, o.n_max, (float2*)z, unit_scale ? 1 : 0);
+    k2_wave_mixed<<<grid, kTile, 0, s>>>(knots, wc, n, dt, t0, o.ks, o.n_max, (float2*)z, unit_scale ? 1 : 0,
+                                         bt.r32, bt.f32);
 }
 
 }  // namespace emri

@@ -20,6 +20,9 @@ FP64, MIXED = 0, 1
 FORWARD, BACKWARD_FROM_LSO = 0, 1
 ST_PLUNGE, ST_BADPARAM, ST_NONFINITE = 1, 2, 4
 (OK, EINVAL, ENOMEM, EBUDGET, EAGAIN, ETIMEDOUT, ECUDA, ENOTFOUND) = range(8)
+KERNELS = ("prologue", "delay_table", "orbit", "wave", "fft_pass1", "fft_pass2_ip", "finalize",
+           "fft_pass2_store")
+NKERNEL = len(KERNELS)
 
 
 class EmriError(RuntimeError):
@@ -64,6 +67,8 @@ _SIGS = {
     "emri_ctx_destroy": (C.c_int, [C.c_void_p]),
     "emri_ctx_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "emri_ctx_memory": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+    "emri_ctx_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "emri_ctx_kernel_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "emri_dataset_create": (C.c_int, [C.c_void_p, C.POINTER(Grid), C.c_void_p, C.c_int, C.c_void_p,
                                       C.c_double, C.c_double, C.POINTER(C.c_void_p)]),
     "emri_dataset_destroy": (C.c_int, [C.c_void_p]),
@@ -166,6 +171,16 @@ class Context:
         u, b = C.c_size_t(), C.c_size_t()
         _check(self.lib.emri_ctx_memory(self.h, C.byref(u), C.byref(b)))
         return u.value, b.value
+
+    def profile(self, enable: bool = True):
+        _check(self.lib.emri_ctx_profile(self.h, 1 if enable else 0))
+
+    def kernel_times(self):
+        """{kernel name: (total ms, launches)} since profiling was enabled."""
+        ms = (C.c_double * NKERNEL)()
+        cnt = (C.c_int64 * NKERNEL)()
+        _check(self.lib.emri_ctx_kernel_times(self.h, ms, cnt))
+        return {KERNELS[i]: (ms[i], cnt[i]) for i in range(NKERNEL)}
 
     # --------------------------------------------------------- datasets
     def dataset(self, g: Grid, data, psd, fmin: float, fmax: float, kind: int = 0) -> "Dataset":

@@ -1,0 +1,118 @@
+"""Serving loop: continuous batching, alone-vs-mix determinism, admission.
+
+Every failure here is caused on the host (an over-budget request, a full
+queue, a poll that times out, an unknown ticket); nothing faults the GPU.
+"""
+import threading
+
+import numpy as np
+import pytest
+
+from paper_2311_17174_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def env():
+    from paper_2311_17174_gb300 import emri
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ctx = emri.Context(0)
+    dsets = {}
+    for logn in (14, 15, 16):
+        n = 1 << logn
+        psd = I.psd_bc04(n)
+        dsets[logn] = ctx.dataset(emri.grid(n, 15.0), I.noise_spectrum(900 + logn, psd, n), psd, 1e-4, 1 / 30.0)
+    yield emri, ctx, dsets
+    for d in dsets.values():
+        d.close()
+    ctx.close()
+
+
+def requests(seed, count):
+    g = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        logn = int(g.integers(14, 17))
+        w = int(g.integers(8, 65))
+        th = I.scatter_walkers(7000 + k, I.draw_sources(8000 + k, 1, 1 << logn)[0], w)
+        prec = int(g.integers(0, 2))
+        out.append((logn, th, prec))
+    return out
+
+
+def direct(emri, ctx, ds, th, prec):
+    w = th.shape[0]
+    lnl = torch.zeros(w, dtype=torch.float64, device="cuda:0")
+    ctx.loglike_batch(ds, torch.tensor(th.T.copy(), device="cuda:0"), emri.opts(precision=prec, n_max=8), lnl)
+    torch.cuda.synchronize()
+    return lnl.cpu().numpy()
+
+
+def test_serve_alone_vs_mix_bitwise(env):
+    emri, ctx, dsets = env
+    reqs = requests(1, 16)
+    alone = [direct(emri, ctx, dsets[l], th, p) for (l, th, p) in reqs]
+    ctx.serve_start(slots=4, queue_capacity=64)
+    try:
+        tickets = [None] * len(reqs)
+
+        def submit(i):
+            l, th, p = reqs[i]
+            tickets[i] = ctx.serve_submit(dsets[l], th.T.copy(), emri.opts(precision=p, n_max=8))
+
+        ths = [threading.Thread(target=submit, args=(i,)) for i in range(len(reqs))]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        slots_used = set()
+        for i, (l, th, p) in enumerate(reqs):
+            rc, lnl, st, stats = ctx.serve_poll(tickets[i], th.shape[0], timeout_us=-1)
+            assert rc == emri.OK
+            np.testing.assert_array_equal(lnl, alone[i])
+            assert stats.arrival_ns <= stats.start_ns <= stats.done_ns
+            slots_used.add(stats.slot)
+        assert len(slots_used) > 1   # requests overlapped on several slots
+    finally:
+        ctx.serve_stop()
+
+
+def test_serve_admission_and_errors(env):
+    emri, ctx, dsets = env
+    th = I.scatter_walkers(1, I.draw_sources(2, 1, 1 << 16)[0], 64)
+    ctx.serve_start(slots=2, queue_capacity=2, budget_bytes=64 << 20)
+    try:
+        # a request larger than the serving budget is refused up front
+        big = I.scatter_walkers(3, I.draw_sources(4, 1, 1 << 16)[0], 512)
+        with pytest.raises(emri.EmriError) as ei:
+            ctx.serve_submit(dsets[16], big.T.copy(), emri.opts(n_max=8))
+        assert ei.value.code == emri.EBUDGET
+        # unknown ticket
+        with pytest.raises(emri.EmriError) as ei:
+            ctx.serve_poll(987654321, 1, timeout_us=0)
+        assert ei.value.code == emri.ENOTFOUND
+        # queue capacity: submits beyond it get EAGAIN
+        got, tickets = [], []
+        for _ in range(8):
+            try:
+                tickets.append(ctx.serve_submit(dsets[16], th.T.copy(), emri.opts(n_max=8)))
+            except emri.EmriError as e:
+                got.append(e.code)
+        assert emri.EAGAIN in got
+        # a zero timeout on a fresh request reports ETIMEDOUT or completion, never an error
+        t = tickets[-1]
+        rc, _, _, _ = ctx.serve_poll(t, 64, timeout_us=0)
+        assert rc in (emri.OK, emri.ETIMEDOUT)
+        if rc == emri.ETIMEDOUT:
+            rc, _, _, _ = ctx.serve_poll(t, 64, timeout_us=-1)
+            assert rc == emri.OK
+        for t2 in tickets[:-1]:
+            assert ctx.serve_poll(t2, 64, timeout_us=-1)[0] == emri.OK
+    finally:
+        ctx.serve_stop()
+    with pytest.raises(emri.EmriError) as ei:
+        ctx.serve_submit(dsets[16], th.T.copy(), emri.opts(n_max=8))
+    assert ei.value.code == emri.ENOTFOUND

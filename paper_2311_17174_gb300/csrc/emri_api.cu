@@ -80,7 +80,7 @@ int normalize_opts(const emri_opts* in, int64_t n, OptsN* o) {
   o->pn_terms = a.pn_terms ? 1 : 0;
   o->mode = a.mode;
   int ks = a.knot_spacing;
-  if (ks == 0) ks = a.precision == EMRI_FP64 ? 128 : 256;
+  if (ks == 0) ks = a.precision == EMRI_FP64 ? 128 : 1024;
   if (!pow2(ks) || ks < 64 || ks > 1024 || ks > n)
     return set_err(EMRI_EINVAL, "opts.knot_spacing must be a power of two in [64, 1024] and <= n");
   o->ks = ks;
@@ -182,6 +182,8 @@ size_t loglike_layout(const FftPlan& p, const OptsN& o, int w, int wave, Carve* 
   LoglikeBufs t;
   t.wc = cv.take<WalkerC>(w);
   t.knots = cv.take<Knot>((size_t)w * (nk + 1));
+  t.ivs = cv.take<char>(o.precision ? (size_t)w * nk * kIvMBytes : 0);
+  t.lisa = cv.take<double>((size_t)(p.n / 256) * 6);
   t.dtab = cv.take<char>((size_t)w * p.n1 * cs);
   t.partial = cv.take<double2>((size_t)w * p.n2);
   t.z = cv.take<char>((size_t)wave * p.n * cs);
@@ -212,7 +214,13 @@ int run_loglike(emri_ctx* ctx, const emri_dataset* ds, const double* theta, int6
   { KTimer t(pf, EMRI_K_PROLOGUE, s); launch_prologue(theta, ld, w, p.n, ds->dt, o, ctx->gl, b.wc, s); }
   { KTimer t(pf, EMRI_K_DELAY, s); launch_delay_table(b.wc, w, p.n1, p.n2, f32, b.dtab, s); }
   { KTimer t(pf, EMRI_K_ORBIT, s); launch_orbit(b.wc, w, p.n, ds->dt, ds->t0, o, b.knots, s); }
-  nl += 3;
+  launch_lisa_tiles(p.n, ds->t0, ds->dt, b.lisa, s);
+  nl += 4;
+  if (f32) {
+    KTimer t(pf, EMRI_K_ORBIT, s);
+    launch_intervals_mixed(b.knots, w, p.n, o.ks, ds->dt, b.ivs, s);
+    nl += 1;
+  }
   const int64_t nk = p.n / o.ks;
   const void* dperm = f32 ? (const void*)ds->d_perm32 : (const void*)ds->d_perm;
   const void* wperm = f32 ? (const void*)ds->w_perm32 : (const void*)ds->w_perm;
@@ -222,7 +230,8 @@ int run_loglike(emri_ctx* ctx, const emri_dataset* ds, const double* theta, int6
     const int ww = std::min(wave, w - i0);
     {
       KTimer t(pf, EMRI_K_WAVE, s);
-      launch_wave(b.knots + (size_t)i0 * (nk + 1), b.wc + i0, ww, p.n, ds->dt, ds->t0, o, b.z, false, ctx->bt, s);
+      launch_wave(b.knots + (size_t)i0 * (nk + 1), b.wc + i0, ww, p.n, ds->dt, ds->t0, o, b.z, false, ctx->bt, b.lisa,
+                  b.ivs + (size_t)i0 * nk * kIvMBytes, s);
     }
     { KTimer t(pf, EMRI_K_FFT1, s); launch_fft_pass1(b.z, ww, p, f32, -1, ctx->tw, s); }
     {
@@ -576,18 +585,25 @@ extern "C" int emri_ak_waveform(emri_ctx* ctx, const emri_grid* grid, const doub
   Carve probe(nullptr);
   probe.take<WalkerC>(w);
   probe.take<Knot>((size_t)w * (nk + 1));
+  probe.take<char>(o.precision ? (size_t)w * nk * kIvMBytes : 0);
+  probe.take<double>((size_t)(grid->n / 256) * 6);
   if ((rc = ctx->ws.reserve(ctx, probe.off + 512, s))) return rc;
   ctx->ws.acquire(s);
   Carve cv(ctx->ws.ptr);
   WalkerC* wc = cv.take<WalkerC>(w);
   Knot* kn = cv.take<Knot>((size_t)w * (nk + 1));
-  launch_prologue(theta, w, w, grid->n, grid->dt, o, ctx->gl, wc, s);
-  launch_orbit(wc, w, grid->n, grid->dt, grid->t0, o, kn, s);
-  launch_wave(kn, wc, w, grid->n, grid->dt, grid->t0, o, z_out, true, ctx->bt, s);
+  char* ivs = cv.take<char>(o.precision ? (size_t)w * nk * kIvMBytes : 0);
+  double* lisa = cv.take<double>((size_t)(grid->n / 256) * 6);
+  Profiler* pf = &ctx->prof;
+  { KTimer t(pf, EMRI_K_PROLOGUE, s); launch_prologue(theta, w, w, grid->n, grid->dt, o, ctx->gl, wc, s); }
+  { KTimer t(pf, EMRI_K_ORBIT, s); launch_orbit(wc, w, grid->n, grid->dt, grid->t0, o, kn, s); }
+  launch_lisa_tiles(grid->n, grid->t0, grid->dt, lisa, s);
+  if (o.precision) launch_intervals_mixed(kn, w, grid->n, o.ks, grid->dt, ivs, s);
+  { KTimer t(pf, EMRI_K_WAVE, s); launch_wave(kn, wc, w, grid->n, grid->dt, grid->t0, o, z_out, true, ctx->bt, lisa, ivs, s); }
   if (status) cudaMemcpy2DAsync(status, sizeof(uint32_t), &wc[0].status, sizeof(WalkerC), sizeof(uint32_t), w,
                                 cudaMemcpyDeviceToDevice, s);
   ctx->ws.release(s);
-  ctx->launches += 3;
+  ctx->launches += o.precision ? 5 : 4;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(e, "waveform launch");
   return EMRI_OK;

@@ -51,6 +51,8 @@ struct Carve {
 struct LoglikeBufs {
   WalkerC* wc;
   Knot* knots;
+  char* ivs;       // mixed interval records [w][n/ks]
+  double* lisa;    // per-tile LISA-phase table [n/256][6]
   char* dtab;
   double2* partial;
   char* z;

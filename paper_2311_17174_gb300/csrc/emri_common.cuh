@@ -38,6 +38,15 @@ struct __align__(16) Knot {
 };
 static_assert(sizeof(Knot) == 128, "knot size");
 
+// Walker geometry in the precision of a kernel (see the waveform kernel).
+template <typename T>
+struct Geo {
+  T sx, sy, sz, e1x, e1y, e1z, e2x, e2y, e2z, cl, sl;
+  T nx, ny, nz, ns, ne1, ne2;           // N and N.S, N.e1, N.e2
+  T sin_ths, cos_ths, sin_phs, cos_phs;
+  T amp_scale;
+};
+
 // Per-walker constants written by the prologue kernel and read by the rest.
 struct __align__(16) WalkerC {
   // orbit
@@ -60,9 +69,23 @@ struct __align__(16) WalkerC {
   double sin_ths, cos_ths, sin_phs, cos_phs;
   double dop;                // (R/c) sin(theta_S) [s]
   double pad[3];
+  Geo<float> gf;             // the geometry rounded to FP32 (mixed kernels)
+  float padf[2];
   int64_t j_plunge;          // first zeroed sample (n if none); written by the orbit kernel
   uint32_t status;           // status bits (prologue | orbit)
   uint32_t pad_u;
+};
+
+// Mixed-precision interval record of one knot interval: the three phases
+// (Doppler orbital phase, gamma~, alpha; cycles) as 64-bit fixed point
+// base + inc * tau plus FP32 s^2, s^3 corrections (s = tau / K_s), and the
+// amplitude x^(2/3) and eccentricity cubics in FP32.
+struct IvM {
+  unsigned long long ph_base, gm_base, al_base;
+  long long ph_inc, gm_inc, al_inc;   // cycles per sample, Q0.64
+  float ph_c[2], gm_c[2], al_c[2];
+  float am[4];
+  float ec[4];
 };
 
 // ------------------------------------------------------ double-double (dd)

@@ -57,8 +57,14 @@ void launch_orbit(WalkerC* wc, int w, int64_t n, double dt, double t0, const Opt
                   cudaStream_t s);
 
 // waveform: z[w][n] (double2 or float2); unit_scale multiplies by mu_s c (cm units)
+// lisa: per-tile phibar table [n/256][6] (launch_lisa_tiles); ivs: mixed
+// interval records [w][n/ks] (launch_intervals_mixed; unused for FP64)
 void launch_wave(const Knot* knots, const WalkerC* wc, int w, int64_t n, double dt, double t0,
-                 const OptsN& o, void* z, bool unit_scale, const BesselTab& bt, cudaStream_t s);
+                 const OptsN& o, void* z, bool unit_scale, const BesselTab& bt, const double* lisa, const void* ivs,
+                 cudaStream_t s);
+void launch_intervals_mixed(const Knot* knots, int w, int64_t n, int ks, double dt, void* ivs, cudaStream_t s);
+void launch_lisa_tiles(int64_t n, double t0, double dt, double* tab, cudaStream_t s);
+constexpr size_t kIvMBytes = 104;
 
 // FFT pass 1 (columns, in place, with the inter-pass twiddle); sign -1 forward, +1 inverse
 void launch_fft_pass1(void* z, int batch, const FftPlan& p, bool fp32, int sign, const Twiddles& t,

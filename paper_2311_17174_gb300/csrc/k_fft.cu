@@ -22,7 +22,8 @@
 
 namespace emri {
 
-constexpr int kFftThreads = 512;
+constexpr int kFftThreads = 512;   // pass 1 (column groups)
+constexpr int kPass2Threads = 256; // pass 2 (rows)
 
 FftPlan make_fft_plan(int64_t n) {
   FftPlan p;
@@ -96,12 +97,14 @@ __device__ __forceinline__ C2 twiddle22(const C2* __restrict__ ta, const C2* __r
 }
 
 // ------------------------------------------------- shared-memory Stockham
-// nb transforms of length L (power of two, <= 4096) stored at buf[c*stride + i].
-// Butterflies are distributed over the CTA; each thread stages its outputs in
-// registers so a stage reads everything before anything is overwritten.
+// nb transforms of length L (power of two, <= 4096); element i of transform
+// c lives at buf[i*sj + c*sc].  Butterfly b works on transform b % nb, so
+// consecutive threads touch consecutive transforms when sc = 1 (row-major
+// tiles: conflict-free) or consecutive elements when nb = 1.  Each thread
+// stages its outputs in registers so a stage reads everything before
+// anything is overwritten.
 template <typename C2, int MAXB>
-__device__ void smem_fft(C2* buf, int L, int nb, int stride, int sign, const C2* __restrict__ ta) {
-  using T = typename CT<C2>::T;
+__device__ void smem_fft(C2* buf, int L, int nb, int sj, int sc, int sign, const C2* __restrict__ ta) {
   const int tid = threadIdx.x;
   const int nth = blockDim.x;
   int lg = 0;
@@ -118,10 +121,10 @@ __device__ void smem_fft(C2* buf, int L, int nb, int stride, int sign, const C2*
       const int b = tid + r * nth;
       dst[r] = -1;
       if (b < nbf) {
-        const int c = b / q4, j = b - c * q4;
+        const int c = b % nb, j = b / nb;
         const int k = j & (ns - 1);
-        C2* col = buf + c * stride;
-        C2 a0 = col[j], a1 = col[j + q4], a2 = col[j + 2 * q4], a3 = col[j + 3 * q4];
+        C2* col = buf + c * sc;
+        C2 a0 = col[j * sj], a1 = col[(j + q4) * sj], a2 = col[(j + 2 * q4) * sj], a3 = col[(j + 3 * q4) * sj];
         if (ns > 1) {
           const int u = (k * 4096) / (ns * 4);   // twiddle step in 1/4096 cycles
           a1 = cmul(a1, conj_if(ta[u], sign));
@@ -136,17 +139,18 @@ __device__ void smem_fft(C2* buf, int L, int nb, int stride, int sign, const C2*
         y[r][1] = cadd(b1, b3);
         y[r][2] = csub(b0, b2);
         y[r][3] = csub(b1, b3);
-        dst[r] = c * stride + (j / ns) * ns * 4 + k;
+        dst[r] = c * sc + ((j / ns) * ns * 4 + k) * sj;
       }
     }
     __syncthreads();
+    const int step = ns * sj;
 #pragma unroll
     for (int r = 0; r < MAXB; ++r) {
       if (dst[r] >= 0) {
         buf[dst[r]] = y[r][0];
-        buf[dst[r] + ns] = y[r][1];
-        buf[dst[r] + 2 * ns] = y[r][2];
-        buf[dst[r] + 3 * ns] = y[r][3];
+        buf[dst[r] + step] = y[r][1];
+        buf[dst[r] + 2 * step] = y[r][2];
+        buf[dst[r] + 3 * step] = y[r][3];
       }
     }
     __syncthreads();
@@ -162,14 +166,14 @@ __device__ void smem_fft(C2* buf, int L, int nb, int stride, int sign, const C2*
       const int b = tid + r * nth;
       dst[r] = -1;
       if (b < nbf) {
-        const int c = b / h2, j = b - c * h2;
+        const int c = b % nb, j = b / nb;
         const int k = j & (ns - 1);
-        C2* col = buf + c * stride;
-        C2 a0 = col[j], a1 = col[j + h2];
+        C2* col = buf + c * sc;
+        C2 a0 = col[j * sj], a1 = col[(j + h2) * sj];
         if (ns > 1) a1 = cmul(a1, conj_if(ta[(k * 4096) / (ns * 2)], sign));
         y[r][0] = cadd(a0, a1);
         y[r][1] = csub(a0, a1);
-        dst[r] = c * stride + (j / ns) * ns * 2 + k;
+        dst[r] = c * sc + ((j / ns) * ns * 2 + k) * sj;
       }
     }
     __syncthreads();
@@ -177,12 +181,38 @@ __device__ void smem_fft(C2* buf, int L, int nb, int stride, int sign, const C2*
     for (int r = 0; r < 2 * MAXB; ++r) {
       if (dst[r] >= 0) {
         buf[dst[r]] = y[r][0];
-        buf[dst[r] + ns] = y[r][1];
+        buf[dst[r] + ns * sj] = y[r][1];
       }
     }
     __syncthreads();
   }
-  (void)sizeof(T);
+}
+
+// Copy nrow rows of rowlen contiguous complex values (global row stride gs)
+// to/from a row-major shared tile, with LPT independent 16-byte accesses per
+// thread in flight (rowlen * sizeof(C2) must be a multiple of 16).
+template <typename C2, int LPT>
+__device__ __forceinline__ void tile_load(C2* __restrict__ buf, const C2* __restrict__ g, int64_t gs, int rowlen,
+                                          int nrow) {
+  const int per = rowlen * (int)sizeof(C2) / 16;       // 16-byte vectors per row
+  const int total = per * nrow;
+  const int nth = blockDim.x;
+  for (int base = threadIdx.x; base < total; base += LPT * nth) {
+    float4 v[LPT];
+#pragma unroll
+    for (int r = 0; r < LPT; ++r) {
+      const int i = base + r * nth;
+      if (i < total) {
+        const int row = i / per, q = i - row * per;
+        v[r] = reinterpret_cast<const float4*>(g + (int64_t)row * gs)[q];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < LPT; ++r) {
+      const int i = base + r * nth;
+      if (i < total) reinterpret_cast<float4*>(buf)[i] = v[r];
+    }
+  }
 }
 
 template <typename C2>
@@ -199,41 +229,39 @@ struct FftCfg<float2> {
 };
 
 // ------------------------------------------------------------- pass 1
+// CTA = ncol adjacent columns j1, all n2 rows: the tile is staged row-major
+// (rows of ncol contiguous elements), transformed along the rows index, and
+// written back in place with the inter-pass twiddle.
 template <typename C2>
 __global__ void __launch_bounds__(kFftThreads) k3_pass1(C2* __restrict__ z, int64_t n, int n1, int n2, int ncol,
                                                         int sign, int shift22, const C2* __restrict__ ta,
                                                         const C2* __restrict__ tb) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C2* buf = reinterpret_cast<C2*>(smraw);
-  const int stride = n2 + 1;
   C2* zw = z + (int64_t)blockIdx.y * n;
   const int j10 = blockIdx.x * ncol;
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < ncol * n2; idx += blockDim.x) {
-    const int c = idx % ncol, j2 = idx / ncol;
-    buf[c * stride + j2] = zw[j10 + c + (int64_t)n1 * j2];
-  }
+  tile_load<C2, 8>(buf, zw + j10, n1, ncol, n2);
   __syncthreads();
-  smem_fft<C2, FftCfg<C2>::kMaxB>(buf, n2, ncol, stride, sign, ta);
-  for (int idx = tid; idx < ncol * n2; idx += blockDim.x) {
+  smem_fft<C2, FftCfg<C2>::kMaxB>(buf, n2, ncol, ncol, 1, sign, ta);
+  for (int idx = threadIdx.x; idx < ncol * n2; idx += blockDim.x) {
     const int c = idx % ncol, k2 = idx / ncol;
     const uint32_t m = (uint32_t)((j10 + c) * k2) << shift22;
-    zw[j10 + c + (int64_t)n1 * k2] = cmul(buf[c * stride + k2], twiddle22(ta, tb, m, sign));
+    zw[j10 + c + (int64_t)n1 * k2] = cmul(buf[idx], twiddle22(ta, tb, m, sign));
   }
 }
 
 // --------------------------------------------------- pass 2, natural order
 template <typename C2>
-__global__ void __launch_bounds__(kFftThreads) k4_pass2_store(const C2* __restrict__ y, C2* __restrict__ out,
+__global__ void __launch_bounds__(kPass2Threads, 2) k4_pass2_store(const C2* __restrict__ y, C2* __restrict__ out,
                                                               int64_t n, int n1, int n2, int sign,
                                                               const C2* __restrict__ ta) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C2* buf = reinterpret_cast<C2*>(smraw);
   const int k2 = blockIdx.x;
   const C2* row = y + (int64_t)blockIdx.y * n + (int64_t)n1 * k2;
-  for (int i = threadIdx.x; i < n1; i += blockDim.x) buf[i] = row[i];
+  tile_load<C2, 4>(buf, row, 0, n1, 1);
   __syncthreads();
-  smem_fft<C2, FftCfg<C2>::kMaxB>(buf, n1, 1, n1, sign, ta);
+  smem_fft<C2, FftCfg<C2>::kMaxB>(buf, n1, 1, 1, 1, sign, ta);
   C2* o = out + (int64_t)blockIdx.y * n;
   for (int k1 = threadIdx.x; k1 < n1; k1 += blockDim.x) o[k2 + (int64_t)n2 * k1] = buf[k1];
 }
@@ -280,18 +308,18 @@ struct AccF {
 };
 
 template <typename C2, typename WT, typename Acc>
-__global__ void __launch_bounds__(kFftThreads) k4_pass2_ip(const C2* __restrict__ y, int64_t n, int n1, int n2,
+__global__ void __launch_bounds__(kPass2Threads, 2) k4_pass2_ip(const C2* __restrict__ y, int64_t n, int n1, int n2,
                                                            const C2* __restrict__ ta, const WalkerC* __restrict__ wcs,
                                                            const C2* __restrict__ dtab, const C2* __restrict__ dperm,
                                                            const WT* __restrict__ wperm, double2* __restrict__ partial) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C2* buf = reinterpret_cast<C2*>(smraw);
   __shared__ double2 afac;
-  __shared__ double2 red[kFftThreads / 32];
+  __shared__ double2 red[kPass2Threads / 32];
   using T = typename CT<C2>::T;
   const int k2 = blockIdx.x, wk = blockIdx.y;
   const C2* row = y + (int64_t)wk * n + (int64_t)n1 * k2;
-  for (int i = threadIdx.x; i < n1; i += blockDim.x) buf[i] = row[i];
+  tile_load<C2, 4>(buf, row, 0, n1, 1);
   if (threadIdx.x == 0) {
     // exp(-2 pi i frac(k2 r))
     const double rh = wcs[wk].r_hi, rl = wcs[wk].r_lo;
@@ -302,7 +330,7 @@ __global__ void __launch_bounds__(kFftThreads) k4_pass2_ip(const C2* __restrict_
     afac = make_double2(c, -s);
   }
   __syncthreads();
-  smem_fft<C2, FftCfg<C2>::kMaxB>(buf, n1, 1, n1, -1, ta);
+  smem_fft<C2, FftCfg<C2>::kMaxB>(buf, n1, 1, 1, 1, -1, ta);
   const C2 a = CT<C2>::make((T)afac.x, (T)afac.y);
   const C2 cn = CT<C2>::make((T)wcs[wk].cn_re, (T)wcs[wk].cn_im);
   const C2* tabw = dtab + (int64_t)wk * n1;
@@ -416,7 +444,7 @@ __global__ void k_inner_dd(const double2* __restrict__ d, const double* __restri
 static size_t pass1_smem(const FftPlan& p, bool fp32, int& ncol) {
   ncol = fp32 ? FftCfg<float2>::kCols : FftCfg<double2>::kCols;
   if (ncol > p.n1) ncol = p.n1;
-  return (size_t)ncol * (p.n2 + 1) * (fp32 ? sizeof(float2) : sizeof(double2));
+  return (size_t)ncol * p.n2 * (fp32 ? sizeof(float2) : sizeof(double2));
 }
 
 void launch_fft_pass1(void* z, int batch, const FftPlan& p, bool fp32, int sign, const Twiddles& t,
@@ -437,10 +465,10 @@ void launch_fft_pass2_store(const void* y, void* out, int batch, const FftPlan& 
   if (batch <= 0) return;
   dim3 g(p.n2, batch);
   if (fp32)
-    k4_pass2_store<float2><<<g, kFftThreads, p.n1 * sizeof(float2), s>>>((const float2*)y, (float2*)out, p.n, p.n1,
+    k4_pass2_store<float2><<<g, kPass2Threads, p.n1 * sizeof(float2), s>>>((const float2*)y, (float2*)out, p.n, p.n1,
                                                                           p.n2, sign, t.ta32);
   else
-    k4_pass2_store<double2><<<g, kFftThreads, p.n1 * sizeof(double2), s>>>((const double2*)y, (double2*)out, p.n,
+    k4_pass2_store<double2><<<g, kPass2Threads, p.n1 * sizeof(double2), s>>>((const double2*)y, (double2*)out, p.n,
                                                                             p.n1, p.n2, sign, t.ta64);
 }
 
@@ -450,11 +478,11 @@ void launch_fft_pass2_ip(const void* y, int w, const FftPlan& p, bool fp32, cons
   if (w <= 0) return;
   dim3 g(p.n2, w);
   if (fp32)
-    k4_pass2_ip<float2, float, AccF><<<g, kFftThreads, p.n1 * sizeof(float2), s>>>(
+    k4_pass2_ip<float2, float, AccF><<<g, kPass2Threads, p.n1 * sizeof(float2), s>>>(
         (const float2*)y, p.n, p.n1, p.n2, t.ta32, wc, (const float2*)delay_tab, (const float2*)data_perm,
         (const float*)wt_perm, partial);
   else
-    k4_pass2_ip<double2, double, AccD><<<g, kFftThreads, p.n1 * sizeof(double2), s>>>(
+    k4_pass2_ip<double2, double, AccD><<<g, kPass2Threads, p.n1 * sizeof(double2), s>>>(
         (const double2*)y, p.n, p.n1, p.n2, t.ta64, wc, (const double2*)delay_tab, (const double2*)data_perm,
         (const double*)wt_perm, partial);
 }

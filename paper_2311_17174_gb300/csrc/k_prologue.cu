@@ -144,6 +144,20 @@ __global__ void k0_prologue(const double* __restrict__ theta, int64_t ld, int w,
     c.dt_gw = 0.0; c.r_hi = 0.0; c.r_lo = 0.0; c.cn_re = 1.0; c.cn_im = 0.0;
   }
   c.pad[0] = c.pad[1] = c.pad[2] = 0.0;
+  {
+    Geo<float>& g = c.gf;
+    g.sx = (float)c.sx; g.sy = (float)c.sy; g.sz = (float)c.sz;
+    g.e1x = (float)c.e1x; g.e1y = (float)c.e1y; g.e1z = (float)c.e1z;
+    g.e2x = (float)c.e2x; g.e2y = (float)c.e2y; g.e2z = (float)c.e2z;
+    g.cl = (float)c.coslam; g.sl = (float)c.sinlam;
+    g.nx = (float)c.nx; g.ny = (float)c.ny; g.nz = (float)c.nz;
+    g.ns = (float)(c.nx * c.sx + c.ny * c.sy + c.nz * c.sz);
+    g.ne1 = (float)(c.nx * c.e1x + c.ny * c.e1y + c.nz * c.e1z);
+    g.ne2 = (float)(c.nx * c.e2x + c.ny * c.e2y + c.nz * c.e2z);
+    g.sin_ths = (float)sts; g.cos_ths = (float)cts; g.sin_phs = (float)sps; g.cos_phs = (float)cps;
+    g.amp_scale = (float)c.amp_scale;
+    c.padf[0] = c.padf[1] = 0.f;
+  }
   c.j_plunge = n;
   c.status = st;
   c.pad_u = 0;

@@ -122,16 +122,13 @@ __device__ __forceinline__ void hermite(double y0, double d, double r0, double r
   c[3] = h * (r0 + r1) - 2.0 * d;
 }
 
+template <typename T>
+__device__ __forceinline__ T poly3(const T c[4], T s) {
+  return ((c[3] * s + c[2]) * s + c[1]) * s + c[0];
+}
+
 struct IvD {           // FP64 interval data
   double ph[4], gm[4], al[4], am[4], ec[4];
-};
-
-struct IvM {           // mixed interval data: fixed-point phases + FP32 corrections
-  unsigned long long ph_base, gm_base, al_base;
-  long long ph_inc, gm_inc, al_inc;   // cycles per sample, Q0.64
-  float ph_c[2], gm_c[2], al_c[2];    // s^2, s^3 coefficients [cycles]
-  float am[4];
-  double ec[4];
 };
 
 __device__ __forceinline__ double frac0(double hi, double lo) {
@@ -180,12 +177,52 @@ __device__ void build_iv_mixed(const Knot& a, const Knot& b, double h, int ks, I
   o.al_c[1] = (float)c[3];
   hermite(a.amp, b.amp - a.amp, a.amp_rate, b.amp_rate, h, c);
   for (int q = 0; q < 4; ++q) o.am[q] = (float)c[q];
-  hermite(a.e, b.e - a.e, a.e_rate, b.e_rate, h, o.ec);
+  hermite(a.e, b.e - a.e, a.e_rate, b.e_rate, h, c);
+  for (int q = 0; q < 4; ++q) o.ec[q] = (float)c[q];
 }
 
-template <typename T>
-__device__ __forceinline__ T poly3(const T c[4], T s) {
-  return ((c[3] * s + c[2]) * s + c[1]) * s + c[0];
+// eccentricity on an interval, in the record's precision
+__device__ __forceinline__ double iv_e(const IvD& v, double s) { return poly3<double>(v.ec, s); }
+__device__ __forceinline__ float iv_e(const IvM& v, double s) { return poly3<float>(v.ec, (float)s); }
+
+static_assert(sizeof(IvM) == kIvMBytes, "interval record size");
+
+// Knots -> mixed interval records, one thread per (interval, walker).
+__global__ void k1b_intervals(const Knot* __restrict__ knots, int64_t nk, int ks, double dt, IvM* __restrict__ out) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nk) return;
+  const int64_t wk = blockIdx.y;
+  const Knot* kn = knots + wk * (nk + 1);
+  build_iv_mixed(kn[k], kn[k + 1], (double)ks * dt, ks, out[wk * nk + k]);
+}
+
+// Per-tile quadratic coefficients of cos, sin of the LISA orbital phase
+// phibar = 2 pi t / T at tile offsets 0, 128, 256: tab[tile][0..2] (cos),
+// tab[tile][3..5] (sin), in t/256.
+__global__ void k_lisa_tiles(int64_t ntiles, double t0, double dt, double* __restrict__ tab) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntiles) return;
+  double c[3], sn[3];
+  for (int q = 0; q < 3; ++q) {
+    double f = (t0 + (double)(i * 256 + 128 * q) * dt) / kYear;
+    f -= floor(f);
+    sincospi(2.0 * f, &sn[q], &c[q]);
+  }
+  double* o = tab + i * 6;
+  o[0] = c[0]; o[1] = -3.0 * c[0] + 4.0 * c[1] - c[2]; o[2] = 2.0 * c[0] - 4.0 * c[1] + 2.0 * c[2];
+  o[3] = sn[0]; o[4] = -3.0 * sn[0] + 4.0 * sn[1] - sn[2]; o[5] = 2.0 * sn[0] - 4.0 * sn[1] + 2.0 * sn[2];
+}
+
+void launch_intervals_mixed(const Knot* knots, int w, int64_t n, int ks, double dt, void* ivs, cudaStream_t s) {
+  if (w <= 0) return;
+  const int64_t nk = n / ks;
+  dim3 g((unsigned)((nk + 127) / 128), (unsigned)w);
+  k1b_intervals<<<g, 128, 0, s>>>(knots, nk, ks, dt, (IvM*)ivs);
+}
+
+void launch_lisa_tiles(int64_t n, double t0, double dt, double* tab, cudaStream_t s) {
+  const int64_t nt = n / 256;
+  k_lisa_tiles<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(nt, t0, dt, tab);
 }
 
 // fixed-point phase: (base + tau*inc) mod 1 to 32 bits, plus the FP32
@@ -201,24 +238,17 @@ __device__ __forceinline__ float phase_fx(unsigned long long base, long long inc
 
 // --------------------------------------------------- response + harmonics
 template <typename T>
-struct Geo {
-  T nx, ny, nz, sx, sy, sz, e1x, e1y, e1z, e2x, e2y, e2z, cl, sl, sin_ths, cos_ths, sin_phs, cos_phs;
-  T ns, ne1, ne2;   // N.S, N.e1, N.e2
-};
-
-template <typename T>
-__device__ __forceinline__ Geo<T> load_geo(const WalkerC& c) {
-  Geo<T> g;
-  g.nx = T(c.nx); g.ny = T(c.ny); g.nz = T(c.nz);
+__device__ __forceinline__ void load_geo(const WalkerC& c, Geo<T>& g) {
   g.sx = T(c.sx); g.sy = T(c.sy); g.sz = T(c.sz);
   g.e1x = T(c.e1x); g.e1y = T(c.e1y); g.e1z = T(c.e1z);
   g.e2x = T(c.e2x); g.e2y = T(c.e2y); g.e2z = T(c.e2z);
   g.cl = T(c.coslam); g.sl = T(c.sinlam);
-  g.sin_ths = T(c.sin_ths); g.cos_ths = T(c.cos_ths); g.sin_phs = T(c.sin_phs); g.cos_phs = T(c.cos_phs);
+  g.nx = T(c.nx); g.ny = T(c.ny); g.nz = T(c.nz);
   g.ns = T(c.nx * c.sx + c.ny * c.sy + c.nz * c.sz);
   g.ne1 = T(c.nx * c.e1x + c.ny * c.e1y + c.nz * c.e1z);
   g.ne2 = T(c.nx * c.e2x + c.ny * c.e2y + c.nz * c.e2z);
-  return g;
+  g.sin_ths = T(c.sin_ths); g.cos_ths = T(c.cos_ths); g.sin_phs = T(c.sin_phs); g.cos_phs = T(c.cos_phs);
+  g.amp_scale = T(c.amp_scale);
 }
 
 // (x, y) -> (cos 2 atan2(y, x), sin 2 atan2(y, x)); (1, 0) when degenerate
@@ -235,33 +265,58 @@ __device__ __forceinline__ void double_angle(T x, T y, T& c2, T& s2, bool degene
   }
 }
 
+// cos(n Phi), sin(n Phi) for n = 1, 2, ...: complex rotation (FP32) or the
+// Chebyshev three-term recurrence c_{n+1} = 2 cos(Phi) c_n - c_{n-1} (FP64,
+// whose error growth ~n^2 eps is harmless at n <= 32 in double).
+template <typename T>
+struct HarmStep {
+  T cn, sn, cp, sp, c1, s1;
+  __device__ __forceinline__ void init(T c, T s) {
+    cn = c; sn = s; cp = T(1); sp = T(0); c1 = c; s1 = s;
+  }
+  __device__ __forceinline__ void next();
+};
+template <>
+__device__ __forceinline__ void HarmStep<float>::next() {
+  const float t = cn * c1 - sn * s1;
+  sn = sn * c1 + cn * s1;
+  cn = t;
+}
+template <>
+__device__ __forceinline__ void HarmStep<double>::next() {
+  const double tc = 2.0 * c1 * cn - cp, ts = 2.0 * c1 * sn - sp;
+  cp = cn; sp = sn; cn = tc; sn = ts;
+}
+
 // Channels at one sample.  cph/sph: cos/sin of the Doppler orbital phase;
-// c2gt/s2gt: of 2 gamma~; ca/sa: of alpha; cb/sb: of phibar; A = x^(2/3);
-// st: tile-relative time in [0, 1) for the harmonic amplitudes bq.
+// c2gt/s2gt: of 2 gamma~; ca/sa: of alpha; cb/sb: of phibar (the LISA
+// orbital phase); A = x^(2/3); st: time in [0, 1] of the harmonic-amplitude
+// fit bq.
 template <typename T>
 __device__ __forceinline__ void channels(const Geo<T>& g, T cph, T sph, T c2gt, T s2gt, T ca, T sa, T cb,
                                          T sb, T A, T st, const T* __restrict__ bq, int n_max, T& hI,
                                          T& hII) {
-  // L(t) = S cos lam + sin lam (e1 cos alpha + e2 sin alpha)
-  const T lx = g.sx * g.cl + g.sl * (g.e1x * ca + g.e2x * sa);
-  const T ly = g.sy * g.cl + g.sl * (g.e1y * ca + g.e2y * sa);
-  const T lz = g.sz * g.cl + g.sl * (g.e1z * ca + g.e2z * sa);
-  const T c = lx * g.nx + ly * g.ny + lz * g.nz;          // L.N
+  // L(t) = S cos lam + sin lam p, p = e1 cos alpha + e2 sin alpha
+  const T px_ = g.e1x * ca + g.e2x * sa, py_ = g.e1y * ca + g.e2y * sa, pz_ = g.e1z * ca + g.e2z * sa;
+  const T lx = g.sx * g.cl + g.sl * px_;
+  const T ly = g.sy * g.cl + g.sl * py_;
+  const T lz = g.sz * g.cl + g.sl * pz_;
+  const T u = ca * g.ne1 + sa * g.ne2;                     // N.p
+  const T c = g.cl * g.ns + g.sl * u;                      // L.N
   // detector normal z_d = z/2 - (sqrt3/2)(cos phibar x + sin phibar y)
   const T h3 = T(kSqrt3Half);
   const T zx = -h3 * cb, zy = -h3 * sb, zz = T(0.5);
   const T zn = zx * g.nx + zy * g.ny + zz * g.nz;         // z_d.N = cos(theta_d)
   const T lzd = lx * zx + ly * zy + lz * zz;
-  // psi: tan psi = [L.z_d - (L.N)(z_d.N)] / [N.(L x z_d)]
-  const T py = lzd - c * zn;
-  const T cxx = ly * zz - lz * zy, cxy = lz * zx - lx * zz, cxz = lx * zy - ly * zx;
-  const T px = g.nx * cxx + g.ny * cxy + g.nz * cxz;
+  // psi: tan psi = [L.z_d - (L.N)(z_d.N)] / [N.(L x z_d)] = [..] / [L.(z_d x N)]
+  const T wx = zy * g.nz - zz * g.ny, wy = zz * g.nx - zx * g.nz, wz = zx * g.ny - zy * g.nx;
+  const T pyv = lzd - c * zn;
+  const T pxv = lx * wx + ly * wy + lz * wz;
   T c2psi, s2psi;
-  double_angle(px, py, c2psi, s2psi, false);
-  // beta: angle about L from L x N to L x S = sin(lam) (p x S), p = e1 cos a + e2 sin a:
-  //   cos beta ~ (L x N).(p x S) = sin(lam) N.S - cos(lam) N.p
-  //   sin beta ~ L.((L x N) x (p x S)) = N.(S x p) = cos a N.e2 - sin a N.e1
-  const T xb = g.sl * g.ns - g.cl * (ca * g.ne1 + sa * g.ne2);
+  double_angle(pxv, pyv, c2psi, s2psi, false);
+  // beta: angle about L from L x N to L x S = sin(lam) (p x S):
+  //   cos beta ~ sin(lam) N.S - cos(lam) N.p,  sin beta ~ N.(S x p) = cos a N.e2 - sin a N.e1
+  const T xb = g.sl * g.ns - g.cl * u;
   const T yb = ca * g.ne2 - sa * g.ne1;
   T c2b, s2b;
   const T one_c2 = T(1) - c * c;
@@ -278,23 +333,24 @@ __device__ __forceinline__ void channels(const Geo<T>& g, T cph, T sph, T c2gt, 
   const T s2p = s2b_ * c2x + c2b_ * s2x;
   // antenna patterns; channel II has phi -> phi - pi/4
   const T ct = zn, q = T(0.5) * (T(1) + ct * ct);
-  const T fpI = q * c2p * c2psi - ct * s2p * s2psi;
-  const T fxI = q * c2p * s2psi + ct * s2p * c2psi;
-  const T fpII = q * s2p * c2psi + ct * c2p * s2psi;
-  const T fxII = q * s2p * s2psi - ct * c2p * c2psi;
+  const T P1 = q * c2p, P2 = ct * s2p, Q1 = q * s2p, Q2 = ct * c2p;
+  const T fpI = P1 * c2psi - P2 * s2psi;
+  const T fxI = P1 * s2psi + P2 * c2psi;
+  const T fpII = Q1 * c2psi + Q2 * s2psi;
+  const T fxII = Q1 * s2psi - Q2 * c2psi;
   // harmonic sum
-  T cn = T(1), sn = T(0), Cs = T(0), Ss = T(0), Rs = T(0);
+  HarmStep<T> hs;
+  hs.init(cph, sph);
+  T Cs = T(0), Ss = T(0), Rs = T(0);
   for (int n = 0; n < n_max; ++n) {
-    const T cn1 = cn * cph - sn * sph;
-    sn = sn * cph + cn * sph;
-    cn = cn1;
     const T* b = bq + 9 * n;
     const T an = (b[2] * st + b[1]) * st + b[0];
     const T bn = (b[5] * st + b[4]) * st + b[3];
     const T rn = (b[8] * st + b[7]) * st + b[6];
-    Cs += an * cn;
-    Ss += bn * sn;
-    Rs += rn * cn;
+    Cs += an * hs.cn;
+    Ss += bn * hs.sn;
+    Rs += rn * hs.cn;
+    hs.next();
   }
   const T hp = A * ((T(1) + c * c) * (Cs * c2g - Ss * s2g) + one_c2 * Rs);
   const T hx = T(-2) * c * A * (Ss * c2g + Cs * s2g);
@@ -317,7 +373,7 @@ __device__ __forceinline__ void tile_harmonics(const IV* iv, int ni, int64_t j0,
     if (ki > ni - 1) ki = ni - 1;
     if (ki < 0) ki = 0;
     const double s = (pos - (double)((kfirst + ki) * ks)) / (double)ks;
-    const double e = poly3<double>(iv[ki].ec, s);
+    const double e = (double)iv_e(iv[ki], s);
     T out[3];
     harmonic_amps<T>(n, T(e), out, rk, ifact);
     bnode[(node * 32 + (n - 1)) * 3 + 0] = out[0];
@@ -342,14 +398,23 @@ __device__ __forceinline__ int tile_span(int64_t j0, int64_t jp) {
 }
 
 // ------------------------------------------------------------- kernels
+template <typename T>
+__device__ __forceinline__ void fit3(T f0, T fh, T f1, T* q) {
+  q[0] = f0;
+  q[1] = T(-3) * f0 + T(4) * fh - f1;
+  q[2] = T(2) * f0 - T(4) * fh + T(2) * f1;
+}
+
 __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
                                                         int64_t n, double dt, double t0, int ks, int n_max,
                                                         double2* __restrict__ z, int unit_scale,
-                                                        const double* __restrict__ rk, const double* __restrict__ ifact) {
+                                                        const double* __restrict__ rk, const double* __restrict__ ifact,
+                                                        const double* __restrict__ lisa) {
   __shared__ IvD iv[kTile / 64];
   __shared__ double bnode[3 * 32 * 3];
   __shared__ double bq[32 * 9];
-  __shared__ double fb0;
+  __shared__ double oq[2][3];
+  __shared__ Geo<double> g;
   const int wk = blockIdx.y;
   const WalkerC& C = wcs[wk];
   const int64_t nk = n / ks;
@@ -360,10 +425,8 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
   const int t = threadIdx.x;
   const double h = (double)ks * dt;
   if (t < ni) build_iv(kn[kfirst + t], kn[kfirst + t + 1], h, iv[t]);
-  if (t == 32) {
-    double f = (t0 + (double)j0 * dt) / kYear;
-    fb0 = f - floor(f);
-  }
+  if (t >= 128 && t < 134) oq[(t - 128) / 3][(t - 128) % 3] = lisa[blockIdx.x * 6 + (t - 128)];
+  if (t == 160) load_geo<double>(C, g);
   __syncthreads();
   const int span = tile_span(j0, C.j_plunge);
   tile_harmonics<double, IvD>(iv, ni, j0, kfirst, ks, n_max, (double)span, bnode, bq, rk, ifact);
@@ -382,19 +445,18 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
     double fal = poly3<double>(v.al, s);
     fal -= rint(fal);
     const double A = poly3<double>(v.am, s);
-    double fb = fb0 + (double)t * (dt / kYear);
-    fb -= rint(fb);
-    double sph, cph, s2g, c2g, sa, ca, sb, cb;
+    const double so = (double)t * (1.0 / kTile);
+    const double cb = (oq[0][2] * so + oq[0][1]) * so + oq[0][0];
+    const double sb = (oq[1][2] * so + oq[1][1]) * so + oq[1][0];
+    double sph, cph, s2g, c2g, sa, ca;
     sincospi(2.0 * fph, &sph, &cph);
     sincospi(2.0 * fgm, &s2g, &c2g);
     sincospi(2.0 * fal, &sa, &ca);
-    sincospi(2.0 * fb, &sb, &cb);
-    const Geo<double> g = load_geo<double>(C);
     double hI, hII;
     channels<double>(g, cph, sph, c2g, s2g, ca, sa, cb, sb, A, (double)t / span, bq, n_max, hI, hII);
     if (unit_scale) {
-      hI *= C.amp_scale;
-      hII *= C.amp_scale;
+      hI *= g.amp_scale;
+      hII *= g.amp_scale;
     }
     out = make_double2(hI, hII);
   }
@@ -404,33 +466,35 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
 __global__ void __launch_bounds__(kTile, 2) k2_wave_mixed(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
                                                           int64_t n, double dt, double t0, int ks, int n_max,
                                                           float2* __restrict__ z, int unit_scale,
-                                                          const float* __restrict__ rk, const float* __restrict__ ifact) {
+                                                          const float* __restrict__ rk, const float* __restrict__ ifact,
+                                                          const double* __restrict__ lisa, const IvM* __restrict__ ivs) {
   __shared__ IvM iv[kTile / 64];
   __shared__ float bnode[3 * 32 * 3];
   __shared__ float bq[32 * 9];
-  __shared__ float fb0;
+  __shared__ float oq[2][3];
+  __shared__ Geo<float> g;
+  __shared__ int64_t jplunge;
   const int wk = blockIdx.y;
   const WalkerC& C = wcs[wk];
   const int64_t nk = n / ks;
-  const Knot* kn = knots + (int64_t)wk * (nk + 1);
   const int64_t j0 = (int64_t)blockIdx.x * kTile;
   const int64_t kfirst = j0 / ks;
   const int ni = ks >= kTile ? 1 : kTile / ks;
   const int t = threadIdx.x;
-  const double h = (double)ks * dt;
-  if (t < ni) build_iv_mixed(kn[kfirst + t], kn[kfirst + t + 1], h, ks, iv[t]);
-  if (t == 32) {
-    double f = (t0 + (double)j0 * dt) / kYear;
-    fb0 = (float)(f - floor(f));
+  if (t < ni) iv[t] = ivs[(int64_t)wk * nk + kfirst + t];
+  if (t >= 128 && t < 134) oq[(t - 128) / 3][(t - 128) % 3] = (float)lisa[blockIdx.x * 6 + (t - 128)];
+  if (t == 160) {
+    g = C.gf;
+    jplunge = C.j_plunge;
   }
   __syncthreads();
-  const int span = tile_span(j0, C.j_plunge);
+  const int span = tile_span(j0, jplunge);
   tile_harmonics<float, IvM>(iv, ni, j0, kfirst, ks, n_max, (double)span, bnode, bq, rk, ifact);
   __syncthreads();
 
   const int64_t j = j0 + t;
   float2 out = make_float2(0.f, 0.f);
-  if (j < C.j_plunge) {
+  if (j < jplunge) {
     const int ki = ks >= kTile ? 0 : t / ks;
     const int tau = (int)(j - (kfirst + ki) * ks);
     const float s = (float)tau / (float)ks;
@@ -440,19 +504,18 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_mixed(const Knot* __restrict
     const float fgm = phase_fx(v.gm_base << 1, (long long)((unsigned long long)v.gm_inc << 1), c2, tau, s);
     const float fal = phase_fx(v.al_base, v.al_inc, v.al_c, tau, s);
     const float A = poly3<float>(v.am, s);
-    float fb = fb0 + (float)t * (float)(dt / kYear);
-    fb -= rintf(fb);
-    float sph, cph, s2g, c2g, sa, ca, sb, cb;
+    const float so = (float)t * (1.f / kTile);
+    const float cb = (oq[0][2] * so + oq[0][1]) * so + oq[0][0];
+    const float sb = (oq[1][2] * so + oq[1][1]) * so + oq[1][0];
+    float sph, cph, s2g, c2g, sa, ca;
     sincospif(2.f * fph, &sph, &cph);
     sincospif(2.f * fgm, &s2g, &c2g);
     sincospif(2.f * fal, &sa, &ca);
-    sincospif(2.f * fb, &sb, &cb);
-    const Geo<float> g = load_geo<float>(C);
     float hI, hII;
     channels<float>(g, cph, sph, c2g, s2g, ca, sa, cb, sb, A, (float)t / (float)span, bq, n_max, hI, hII);
     if (unit_scale) {
-      hI *= (float)C.amp_scale;
-      hII *= (float)C.amp_scale;
+      hI *= g.amp_scale;
+      hII *= g.amp_scale;
     }
     out = make_float2(hI, hII);
   }
@@ -460,15 +523,16 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_mixed(const Knot* __restrict
 }
 
 void launch_wave(const Knot* knots, const WalkerC* wc, int w, int64_t n, double dt, double t0,
-                 const OptsN& o, void* z, bool unit_scale, const BesselTab& bt, cudaStream_t s) {
+                 const OptsN& o, void* z, bool unit_scale, const BesselTab& bt, const double* lisa, const void* ivs,
+                 cudaStream_t s) {
   if (w <= 0) return;
   dim3 grid((unsigned)(n / kTile), (unsigned)w);
   if (o.precision == 0)
     k2_wave_f64<<<grid, kTile, 0, s>>>(knots, wc, n, dt, t0, o.ks, o.n_max, (double2*)z, unit_scale ? 1 : 0,
-                                       bt.r64, bt.f64);
+                                       bt.r64, bt.f64, lisa);
   else
     k2_wave_mixed<<<grid, kTile, 0, s>>>(knots, wc, n, dt, t0, o.ks, o.n_max, (float2*)z, unit_scale ? 1 : 0,
-                                         bt.r32, bt.f32);
+                                         bt.r32, bt.f32, lisa, (const IvM*)ivs);
 }
 
 }  // namespace emri

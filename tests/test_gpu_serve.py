@@ -83,7 +83,7 @@ def test_serve_alone_vs_mix_bitwise(env):
 def test_serve_admission_and_errors(env):
     emri, ctx, dsets = env
     th = I.scatter_walkers(1, I.draw_sources(2, 1, 1 << 16)[0], 64)
-    ctx.serve_start(slots=2, queue_capacity=2, budget_bytes=64 << 20)
+    ctx.serve_start(slots=2, queue_capacity=2, budget_bytes=256 << 20)
     try:
         # a request larger than the serving budget is refused up front
         big = I.scatter_walkers(3, I.draw_sources(4, 1, 1 << 16)[0], 512)

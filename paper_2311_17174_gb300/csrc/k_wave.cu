@@ -52,11 +52,12 @@ __device__ __forceinline__ T bessel_series(int m, T x, const T* __restrict__ rk,
   lead *= ifact[m];
   const T q = -half * half;
   const T* r = rk + m * 32;
+  const T eps = sizeof(T) == 8 ? T(1e-17) : T(3e-8);
   T term = lead, sum = lead;
   for (int kk = 1; kk < 32; ++kk) {
     term *= q * r[kk];
     sum += term;
-    if (fabs(term) <= T(1e-17) * fabs(sum)) break;
+    if (fabs(term) <= eps * fabs(sum)) break;
   }
   return sum;
 }
@@ -183,7 +184,7 @@ __device__ void build_iv_mixed(const Knot& a, const Knot& b, double h, int ks, I
 
 // eccentricity on an interval, in the record's precision
 __device__ __forceinline__ double iv_e(const IvD& v, double s) { return poly3<double>(v.ec, s); }
-__device__ __forceinline__ float iv_e(const IvM& v, double s) { return poly3<float>(v.ec, (float)s); }
+__device__ __forceinline__ float iv_e(const IvM& v, float s) { return poly3<float>(v.ec, s); }
 
 static_assert(sizeof(IvM) == kIvMBytes, "interval record size");
 
@@ -363,19 +364,22 @@ __device__ __forceinline__ void channels(const Geo<T>& g, T cph, T sph, T c2gt, 
 // the tile), quadratic in st = t / L.
 template <typename T, typename IV>
 __device__ __forceinline__ void tile_harmonics(const IV* iv, int ni, int64_t j0, int64_t kfirst, int ks,
-                                               int n_max, double span, T* bnode, T* bq, const T* __restrict__ rk,
+                                               int n_max, int span, T* bnode, T* bq, const T* __restrict__ rk,
                                                const T* __restrict__ ifact) {
   const int t = threadIdx.x;
   if (t < 3 * n_max) {
     const int node = t / n_max, n = t % n_max + 1;
-    const double pos = (double)j0 + 0.5 * span * node;
-    int64_t ki = (int64_t)floor(pos / ks) - kfirst;
+    // node at offset span*node/2: integer arithmetic in half samples, so no
+    // FP64 instruction runs here in the FP32 kernel
+    const int64_t pos2 = 2 * j0 + (int64_t)span * node;
+    int64_t ki = pos2 / (2 * ks) - kfirst;
     if (ki > ni - 1) ki = ni - 1;
     if (ki < 0) ki = 0;
-    const double s = (pos - (double)((kfirst + ki) * ks)) / (double)ks;
-    const double e = (double)iv_e(iv[ki], s);
+    const int64_t rem2 = pos2 - 2 * (kfirst + ki) * ks;
+    const T s = T(rem2) / T(2 * ks);
+    const T e = T(iv_e(iv[ki], s));
     T out[3];
-    harmonic_amps<T>(n, T(e), out, rk, ifact);
+    harmonic_amps<T>(n, e, out, rk, ifact);
     bnode[(node * 32 + (n - 1)) * 3 + 0] = out[0];
     bnode[(node * 32 + (n - 1)) * 3 + 1] = out[1];
     bnode[(node * 32 + (n - 1)) * 3 + 2] = out[2];
@@ -429,7 +433,7 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
   if (t == 160) load_geo<double>(C, g);
   __syncthreads();
   const int span = tile_span(j0, C.j_plunge);
-  tile_harmonics<double, IvD>(iv, ni, j0, kfirst, ks, n_max, (double)span, bnode, bq, rk, ifact);
+  tile_harmonics<double, IvD>(iv, ni, j0, kfirst, ks, n_max, span, bnode, bq, rk, ifact);
   __syncthreads();
 
   const int64_t j = j0 + t;
@@ -489,7 +493,7 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_mixed(const Knot* __restrict
   }
   __syncthreads();
   const int span = tile_span(j0, jplunge);
-  tile_harmonics<float, IvM>(iv, ni, j0, kfirst, ks, n_max, (double)span, bnode, bq, rk, ifact);
+  tile_harmonics<float, IvM>(iv, ni, j0, kfirst, ks, n_max, span, bnode, bq, rk, ifact);
   __syncthreads();
 
   const int64_t j = j0 + t;

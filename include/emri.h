@@ -207,6 +207,29 @@ int emri_ak_waveform(emri_ctx* ctx, const emri_grid* grid, const double* theta_d
 int emri_fft_batch(emri_ctx* ctx, void* z_dev, int64_t n, int batch, int precision, int direction,
                    void* stream);
 
+/* ----------------------------------------------------- allocation-free FFT
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot call cudaMalloc -- a plugin limited to the memory its host
+ * application hands it, a process whose device memory is fully reserved by
+ * another allocator, or a real-time loop that must never enter the
+ * allocator.  Same transform, layout and arguments as emri_fft_batch, but no
+ * context: the one scratch sequence the second pass needs, and the twiddle
+ * tables, are file-scope static device arrays of the library
+ * (EMRI_NOALLOC_SCRATCH_BYTES of scratch plus 120 KiB of tables, held on
+ * every GPU that loads the library until the process exits).  Nothing is
+ * allocated by the call.
+ *  - Limit: one sequence must fit the scratch, n * 16 B (FP64) or n * 8 B
+ *    (EMRI_MIXED) <= EMRI_NOALLOC_SCRATCH_BYTES, i.e. n <= 2^21 in FP64 and
+ *    n <= 2^22 in FP32; larger n returns EMRI_EINVAL with a message.  Any
+ *    batch size is accepted (processed in chunks that fit the scratch).
+ *  - The first call on a device (the current device) resolves the arrays'
+ *    addresses with cudaGetSymbolAddress and fills the tables, synchronising
+ *    `stream`; make that first call before any stream capture.
+ *  - All calls on a device share the scratch: calls whose work overlaps on
+ *    the GPU (different streams, unordered host threads) race. */
+#define EMRI_NOALLOC_SCRATCH_BYTES (32u << 20)
+int emri_fft_batch_noalloc(void* z_dev, int64_t n, int batch, int precision, int direction, void* stream);
+
 /* Batched log-likelihood (steps S0-S7; Eq. (8)) of W walkers against a
  * dataset:  lnL = <d|h> - <h|h>/2 (the constant -<d|d>/2 left out) with
  * h = h_u / d_GW delayed by dt_GW,

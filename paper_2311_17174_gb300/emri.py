@@ -78,6 +78,7 @@ _SIGS = {
     "emri_ak_waveform": (C.c_int, [C.c_void_p, C.POINTER(Grid), C.c_void_p, C.c_int, C.POINTER(Opts),
                                    C.c_void_p, C.c_void_p, C.c_void_p]),
     "emri_fft_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "emri_fft_batch_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "emri_loglike_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(Opts),
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "emri_loglike_multi": (C.c_int, [C.c_void_p, C.POINTER(Work), C.c_int, C.c_void_p]),
@@ -130,6 +131,13 @@ def _stream(s):
     if isinstance(s, int):
         return s
     return s.cuda_stream
+
+
+def fft_batch_noalloc(z, n: int, batch: int, precision: int, direction: int = -1, stream=None):
+    """emri_fft_batch_noalloc: the in-place batched FFT without a context and
+    without any device allocation (fixed library scratch; see include/emri.h)."""
+    _check(load().emri_fft_batch_noalloc(_ptr(z), int(n), int(batch), int(precision), int(direction),
+                                         _stream(stream)))
 
 
 def opts(precision=FP64, n_max=10, doppler=1, pn_terms=1, mode=FORWARD, knot_spacing=0, n_xi=2.0,

@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--cpu-walkers", type=int, default=0, help="oracle sample size (0: one per core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=6.0, help="serving measurement per precision (0: skip)")
     return ap.parse_args()
 
 
@@ -179,6 +180,68 @@ def time_steps(ctx, ds, theta_dev, o, lnl, steps, warmup, flush, barrier):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     return times
+
+
+def serve_bench(ctx, precision: int, rate: float, duration: float, n_max: int, seed: int = 5):
+    """Poisson-arriving requests (8-512 walkers, 2^16-2^22 samples, one
+    resident noise dataset per length) through the serving loop; latency is
+    completion minus arrival as stamped by the library."""
+    import threading
+    from paper_2311_17174_gb300 import emri, inputs as I
+    sched = I.config_c5(rate, duration, seed=seed)
+    dsets = {}
+    for logn in range(16, 23):
+        n = 1 << logn
+        psd = I.psd_bc04(n)
+        dsets[n] = ctx.dataset(emri.grid(n, I.DT), I.noise_spectrum(700 + logn, psd, n), psd, 1e-4, 1 / (2 * I.DT))
+    src = I.draw_sources(seed, 1, 1 << 22)[0]
+    pool = I.scatter_walkers(seed + 1, src, 512)
+    o = emri.opts(precision=precision, n_max=n_max)
+    ctx.serve_start(slots=4, queue_capacity=4096)
+    lat, walkers, lock = [], [0], threading.Lock()
+    tickets = []
+
+    def waiter():
+        k = 0
+        while True:
+            with lock:
+                if k >= len(tickets):
+                    if done_submitting[0]:
+                        return
+                    t = None
+                else:
+                    t = tickets[k]
+            if t is None:
+                time.sleep(0.001)
+                continue
+            tk, w = t
+            rc, _, _, st = ctx.serve_poll(tk, w, timeout_us=-1)
+            lat.append((st.done_ns - st.arrival_ns) / 1e6)
+            walkers[0] += w
+            k += 1
+
+    done_submitting = [False]
+    th = threading.Thread(target=waiter)
+    th.start()
+    t0 = time.perf_counter()
+    for (ta, dsi, w, n) in sched:
+        dt_ = t0 + ta - time.perf_counter()
+        if dt_ > 0:
+            time.sleep(dt_)
+        tk = ctx.serve_submit(dsets[n], pool[:w].T.copy(), o)
+        with lock:
+            tickets.append((tk, w))
+    with lock:
+        done_submitting[0] = True
+    th.join()
+    elapsed = time.perf_counter() - t0
+    ctx.serve_stop()
+    for d in dsets.values():
+        d.close()
+    lat = np.array(lat)
+    return {"precision": "fp64" if precision == 0 else "mixed", "rate_per_s": rate, "requests": int(len(lat)),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "lnl_per_s": walkers[0] / elapsed, "seconds": elapsed, "slots": 4}
 
 
 def flop_model(n_max: int) -> float:
@@ -332,6 +395,12 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_tot = float(t.item())
 
+    # ---- serving: p50/p99 latency under Poisson arrivals (rank 0)
+    serving = None
+    if rank == 0 and args.serve_seconds > 0:
+        serving = [serve_bench(ctx, emri.MIXED, 20.0, args.serve_seconds, wl.n_max),
+                   serve_bench(ctx, emri.FP64, 1.5, args.serve_seconds, wl.n_max)]
+
     # ---- roofline of the dominant kernel (FP64 step)
     per_step = {k: v[0] / args.steps for k, v in ktimes.items() if v[1]}
     dom = max(per_step, key=per_step.get)
@@ -371,6 +440,7 @@ def main():
             "mixed": mixed,
             "e2e": {"value": W * world * args.steps / (e2e_tot / 1e3), "unit": "lnL/s",
                     "h2d_bytes_per_step": int(th_host.numel() * 8), "d2h_bytes_per_step": int(out_host.numel() * 8)},
+            "serving": serving,
             "gpu_launches": int(launches),
             "kernels_ms_per_step": {k: round(v, 3) for k, v in per_step.items()},
             "roofline": roof,

@@ -127,7 +127,12 @@ const char* emri_version(void);
 /* Create a context on CUDA device `device`.  hbm_budget_bytes caps the
  * device memory the library holds for workspaces and resident datasets
  * (0 = 80% of the device's free memory at creation).  Builds the FFT twiddle
- * and quadrature tables.  *out receives the context (caller destroys). */
+ * and quadrature tables.  *out receives the context (caller destroys).
+ * Debug aid: with the environment variable EMRI_DEBUG_POISON set to a
+ * non-zero value at creation, the context's shared workspace is filled with
+ * 0xFF bytes (NaN as FP32/FP64) before every call, so that a kernel reading
+ * intermediate data that the same call did not write yields NaN instead of a
+ * stale value from an earlier call; it costs one memset per call. */
 int emri_ctx_create(int device, size_t hbm_budget_bytes, emri_ctx** out);
 
 /* Stop serving if running, free every workspace, table and the context. */

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -123,6 +124,49 @@ static void gauss_legendre32(double* x, double* w) {
   }
 }
 
+// Chebyshev-Picard integration tables for the orbit kernel: with the 32
+// Chebyshev-Gauss-Lobatto nodes x_j = -cos(pi j/31) on [-1, 1] and the
+// Lagrange basis l_j(x) = sum_k (2/(31 c_j c_k)) T_k(x_j) T_k(x)
+// (c_0 = c_31 = 2, else 1), the weights
+//   Q_j(x) = (1/2) int_{-1}^{x} l_j(s) ds   (unit segment, dtau = dx/2)
+// at the nodes (qn, stored transposed: qn[j*32 + i]) and at the 129 knot
+// positions x = -1 + 2q/128 (qk[q*32 + j]); long double, rounded once.
+static void mcpi_tables(double* qn, double* qk) {
+  typedef long double LD;
+  const int m = 32;
+  const LD pi = 3.141592653589793238462643383279502884L;
+  LD xn[32], cc[32];
+  for (int j = 0; j < m; ++j) {
+    xn[j] = -cosl(pi * j / (m - 1));
+    cc[j] = (j == 0 || j == m - 1) ? 2.0L : 1.0L;
+  }
+  auto cheb = [](int k, LD x) {
+    LD t0 = 1, t1 = x;
+    if (k == 0) return t0;
+    for (int i = 2; i <= k; ++i) {
+      LD t2 = 2 * x * t1 - t0;
+      t0 = t1;
+      t1 = t2;
+    }
+    return t1;
+  };
+  auto cint = [&](int k, LD x) {   // int_{-1}^{x} T_k
+    if (k == 0) return x + 1;
+    if (k == 1) return (x * x - 1) / 2;
+    auto prim = [&](LD y) { return cheb(k + 1, y) / (2 * (k + 1)) - cheb(k - 1, y) / (2 * (k - 1)); };
+    return prim(x) - prim(-1.0L);
+  };
+  auto weight = [&](int j, LD x) {
+    LD acc = 0;
+    for (int k = 0; k < m; ++k) acc += 2.0L / ((m - 1) * cc[j] * cc[k]) * cheb(k, xn[j]) * cint(k, x);
+    return acc / 2;
+  };
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) qn[j * 32 + i] = (double)weight(j, xn[i]);
+  for (int q = 0; q <= 128; ++q)
+    for (int j = 0; j < m; ++j) qk[q * 32 + j] = (double)weight(j, -1.0L + 2.0L * q / 128);
+}
+
 // ----------------------------------------------------------- workspace
 int Workspace::reserve(emri_ctx* ctx, size_t bytes, cudaStream_t s) {
   if (bytes <= cap) return EMRI_OK;
@@ -154,6 +198,8 @@ int Workspace::reserve(emri_ctx* ctx, size_t bytes, cudaStream_t s) {
 void Workspace::acquire(cudaStream_t s) {
   if (!ev) cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   if (has_ev && s != last_stream) cudaStreamWaitEvent(s, ev, 0);
+  // debug aid: a kernel that reads workspace it did not write this call sees NaN
+  if (poison && ptr) cudaMemsetAsync(ptr, 0xFF, cap, s);
 }
 
 void Workspace::release(cudaStream_t s) {
@@ -185,6 +231,7 @@ size_t loglike_layout(const FftPlan& p, const OptsN& o, int w, int wave, Carve* 
   t.ivs = cv.take<char>(o.precision ? (size_t)w * nk * kIvMBytes : 0);
   t.lisa = cv.take<double>((size_t)(p.n / 256) * 6);
   t.dtab = cv.take<char>((size_t)w * p.n1 * cs);
+  t.rtab = cv.take<char>((size_t)w * p.n2 * cs);
   t.partial = cv.take<double2>((size_t)w * p.n2);
   t.z = cv.take<char>((size_t)wave * p.n * cs);
   if (b) *b = t;
@@ -212,10 +259,10 @@ int run_loglike(emri_ctx* ctx, const emri_dataset* ds, const double* theta, int6
   int64_t nl = 0;
   Profiler* pf = &ctx->prof;
   { KTimer t(pf, EMRI_K_PROLOGUE, s); launch_prologue(theta, ld, w, p.n, ds->dt, o, ctx->gl, b.wc, s); }
-  { KTimer t(pf, EMRI_K_DELAY, s); launch_delay_table(b.wc, w, p.n1, p.n2, f32, b.dtab, s); }
-  { KTimer t(pf, EMRI_K_ORBIT, s); launch_orbit(b.wc, w, p.n, ds->dt, ds->t0, o, b.knots, s); }
+  { KTimer t(pf, EMRI_K_DELAY, s); launch_delay_table(b.wc, w, p.n1, p.n2, f32, b.dtab, b.rtab, s); }
+  { KTimer t(pf, EMRI_K_ORBIT, s); launch_orbit(b.wc, w, p.n, ds->dt, ds->t0, o, b.knots, ctx->mcpi, s); }
   launch_lisa_tiles(p.n, ds->t0, ds->dt, b.lisa, s);
-  nl += 4;
+  nl += 5;
   if (f32) {
     KTimer t(pf, EMRI_K_ORBIT, s);
     launch_intervals_mixed(b.knots, w, p.n, o.ks, ds->dt, b.ivs, s);
@@ -236,8 +283,8 @@ int run_loglike(emri_ctx* ctx, const emri_dataset* ds, const double* theta, int6
     { KTimer t(pf, EMRI_K_FFT1, s); launch_fft_pass1(b.z, ww, p, f32, -1, ctx->tw, s); }
     {
       KTimer t(pf, EMRI_K_FFT2_IP, s);
-      launch_fft_pass2_ip(b.z, ww, p, f32, ctx->tw, b.wc + i0, b.dtab + (size_t)i0 * p.n1 * cs, dperm, wperm,
-                          b.partial + (size_t)i0 * p.n2, s);
+      launch_fft_pass2_ip(b.z, ww, p, f32, ctx->tw, b.wc + i0, b.dtab + (size_t)i0 * p.n1 * cs,
+                          b.rtab + (size_t)i0 * p.n2 * cs, dperm, wperm, b.partial + (size_t)i0 * p.n2, s);
     }
     {
       KTimer t(pf, EMRI_K_FINALIZE, s);
@@ -336,6 +383,10 @@ extern "C" int emri_ctx_create(int device, size_t budget, emri_ctx** out) {
   size_t fr = 0, tot = 0;
   CK(cudaMemGetInfo(&fr, &tot));
   c->budget = budget ? budget : (size_t)(0.8 * (double)fr);
+  {
+    const char* pz = getenv("EMRI_DEBUG_POISON");
+    c->ws.poison = pz && pz[0] && pz[0] != '0';
+  }
   c->used = 0;
   cudaError_t e2 = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
   if (e2 != cudaSuccess) {
@@ -343,7 +394,7 @@ extern "C" int emri_ctx_create(int device, size_t budget, emri_ctx** out) {
     return cuda_err(e2, "cudaStreamCreate");
   }
   // twiddle and quadrature tables
-  size_t tb = 4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8 + 64 * 8 + 35 * 32 * 12 + 35 * 12 + 256;
+  size_t tb = 4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8 + 64 * 8 + 35 * 32 * 12 + 35 * 12 + 256 + (32 + 129) * 32 * 8;
   char* p = nullptr;
   e2 = cudaMalloc(&p, tb);
   if (e2 != cudaSuccess) {
@@ -364,9 +415,15 @@ extern "C" int emri_ctx_create(int device, size_t budget, emri_ctx** out) {
     c->bt.f64 = (double*)(q + 35 * 32 * 8);
     c->bt.r32 = (float*)(q + 35 * 32 * 8 + 35 * 8);
     c->bt.f32 = (float*)(q + 35 * 32 * 8 + 35 * 8 + 35 * 32 * 4);
+    c->mcpi = (double*)(q + 35 * 32 * 12 + 35 * 12 + 4);   // 8-byte aligned: q is, and 13860 + 4 = 13864
   }
   double glh[64];
   gauss_legendre32(glh, glh + 32);
+  {
+    std::vector<double> mt((32 + 129) * 32);
+    mcpi_tables(mt.data(), mt.data() + 32 * 32);
+    cudaMemcpy(c->mcpi, mt.data(), mt.size() * sizeof(double), cudaMemcpyHostToDevice);
+  }
   launch_twiddle_init(c->tw, c->stream);
   launch_bessel_tables(c->bt, c->stream);
   cudaMemcpyAsync(c->gl, glh, sizeof glh, cudaMemcpyHostToDevice, c->stream);
@@ -388,6 +445,7 @@ extern "C" int emri_ctx_destroy(emri_ctx* c) {
   if (!c) return EMRI_OK;
   cudaSetDevice(c->device);
   serve_shutdown(c);
+  multi_destroy(c);
   c->prof.on = false;
   c->prof.drain();
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
@@ -444,7 +502,10 @@ extern "C" int emri_dataset_create(emri_ctx* ctx, const emri_grid* grid, const v
   ds->t0 = grid->t0;
   ds->fmin = fmin;
   ds->fmax = fmax;
-  ds->plan = make_fft_plan(n);
+  {
+    auto it = ctx->fft_split.find(n);
+    ds->plan = make_fft_plan(n, it == ctx->fft_split.end() ? 0 : it->second);
+  }
   const size_t keep = (size_t)n * (16 + 8 + 8 + 4) + 1024;
   const size_t tmp = (size_t)n * (16 + 16 + 8) + (size_t)(n / 2 + 1) * 8 + 4096;
   if (ctx->used + keep + tmp > ctx->budget) {
@@ -596,7 +657,7 @@ extern "C" int emri_ak_waveform(emri_ctx* ctx, const emri_grid* grid, const doub
   double* lisa = cv.take<double>((size_t)(grid->n / 256) * 6);
   Profiler* pf = &ctx->prof;
   { KTimer t(pf, EMRI_K_PROLOGUE, s); launch_prologue(theta, w, w, grid->n, grid->dt, o, ctx->gl, wc, s); }
-  { KTimer t(pf, EMRI_K_ORBIT, s); launch_orbit(wc, w, grid->n, grid->dt, grid->t0, o, kn, s); }
+  { KTimer t(pf, EMRI_K_ORBIT, s); launch_orbit(wc, w, grid->n, grid->dt, grid->t0, o, kn, ctx->mcpi, s); }
   launch_lisa_tiles(grid->n, grid->t0, grid->dt, lisa, s);
   if (o.precision) launch_intervals_mixed(kn, w, grid->n, o.ks, grid->dt, ivs, s);
   { KTimer t(pf, EMRI_K_WAVE, s); launch_wave(kn, wc, w, grid->n, grid->dt, grid->t0, o, z_out, true, ctx->bt, lisa, ivs, s); }
@@ -658,6 +719,10 @@ extern "C" int emri_loglike_batch(emri_ctx* ctx, const emri_dataset* ds, const d
   int rc = normalize_opts(opts, ds->n, &o);
   if (rc) return rc;
   std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!(opts && opts->knot_spacing)) {
+    const int pk = ctx_plan_ks(ctx, ds->n, o);
+    if (pk) o.ks = pk;
+  }
   CK(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   const int wave = pick_wave(ctx, ds->plan, o, w);

@@ -13,6 +13,7 @@
 
 namespace emri {
 struct Server;
+struct MultiGraph;
 }
 
 struct emri_ctx;
@@ -27,6 +28,7 @@ struct Workspace {
   cudaEvent_t ev = nullptr;
   bool has_ev = false;
   cudaStream_t last_stream = nullptr;
+  bool poison = false;   // fill with 0xFF bytes (FP NaN) at every acquire
   int reserve(emri_ctx* ctx, size_t bytes, cudaStream_t s);
   void acquire(cudaStream_t s);
   void release(cudaStream_t s);
@@ -54,6 +56,7 @@ struct LoglikeBufs {
   char* ivs;       // mixed interval records [w][n/ks]
   double* lisa;    // per-tile LISA-phase table [n/256][6]
   char* dtab;
+  char* rtab;      // per-walker row delay factors [w][n2]
   double2* partial;
   char* z;
 };
@@ -106,11 +109,14 @@ struct emri_ctx {
   emri::Twiddles tw{};
   emri::BesselTab bt{};
   double* gl = nullptr;
+  double* mcpi = nullptr;     // orbit integration tables (qn, qk)
   emri::Workspace ws;
   std::atomic<int64_t> launches{0};
   emri::Server* server = nullptr;
+  emri::MultiGraph* multi = nullptr;
   emri::Profiler prof;
   std::map<std::tuple<int64_t, int, int>, emri::Plan> plans;   // (n, n_max, precision)
+  std::map<int64_t, int> fft_split;                             // n -> n2 for new datasets
 };
 
 struct emri_dataset {
@@ -139,5 +145,7 @@ int run_loglike(emri_ctx* ctx, const emri_dataset* ds, const double* theta, int6
                 int wave, const LoglikeBufs& b, double* lnl, double* dh, double* hh, uint32_t* status,
                 cudaStream_t s, int64_t* launches);
 int ctx_plan_wave(emri_ctx* ctx, int64_t n, const OptsN& o);
+int ctx_plan_ks(emri_ctx* ctx, int64_t n, const OptsN& o);
 void serve_shutdown(emri_ctx* ctx);
+void multi_destroy(emri_ctx* ctx);
 }  // namespace emri

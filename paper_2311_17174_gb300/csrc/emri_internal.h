@@ -26,7 +26,8 @@ struct FftPlan {
   int n1, n2;
   int log2n;
 };
-FftPlan make_fft_plan(int64_t n);
+// n2 = 0: default split n2 = 2^min(10, log2(n)/2)
+FftPlan make_fft_plan(int64_t n, int n2 = 0);
 
 // Twiddle tables: ta[i] = exp(-2 pi i i/4096), i < 4096; tb[i] = exp(-2 pi i i/2^22), i < 1024.
 struct Twiddles {
@@ -49,12 +50,14 @@ void launch_bessel_tables(BesselTab t, cudaStream_t s);
 
 void launch_prologue(const double* theta, int64_t ld, int w, int64_t n, double dt, const OptsN& o,
                      const double* gl, WalkerC* out, cudaStream_t s);
-void launch_delay_table(const WalkerC* wc, int w, int n1, int n2, bool fp32, void* tab, cudaStream_t s);
+// tab[w][n1] = exp(-2 pi i frac(n2 k1 r)), rtab[w][n2] = exp(-2 pi i frac(k2 r))
+void launch_delay_table(const WalkerC* wc, int w, int n1, int n2, bool fp32, void* tab, void* rtab, cudaStream_t s);
 void launch_prologue_export(const WalkerC* wc, int w, double* out, cudaStream_t s);
 
 // orbit: knots[w][nk+1], nk = n / ks
+// mcpi_tab: Chebyshev-Picard tables (qn then qk); NULL selects the serial RK4 integrator
 void launch_orbit(WalkerC* wc, int w, int64_t n, double dt, double t0, const OptsN& o, Knot* knots,
-                  cudaStream_t s);
+                  const double* mcpi_tab, cudaStream_t s);
 
 // waveform: z[w][n] (double2 or float2); unit_scale multiplies by mu_s c (cm units)
 // lisa: per-tile phibar table [n/256][6] (launch_lisa_tiles); ivs: mixed
@@ -74,7 +77,7 @@ void launch_fft_pass2_store(const void* y, void* out, int batch, const FftPlan& 
                             const Twiddles& t, cudaStream_t s);
 // FFT pass 2 fused with the weighted inner products; partial[w][n2] = (dh, hh)
 void launch_fft_pass2_ip(const void* y, int w, const FftPlan& p, bool fp32, const Twiddles& t,
-                         const WalkerC* wc, const void* delay_tab, const void* data_perm,
+                         const WalkerC* wc, const void* delay_tab, const void* row_tab, const void* data_perm,
                          const void* wt_perm, double2* partial, cudaStream_t s);
 // per-walker fixed-order reduction of the partials and lnL
 // dh_scale / hh_scale undo the dataset's FP32 scaling (1 for FP64)

@@ -232,6 +232,11 @@ void serve_shutdown(emri_ctx* ctx) {
   ctx->server = nullptr;
 }
 
+int ctx_plan_ks(emri_ctx* ctx, int64_t n, const OptsN& o) {
+  auto it = ctx->plans.find(std::make_tuple(n, o.n_max, o.precision));
+  return it == ctx->plans.end() ? 0 : it->second.ks;
+}
+
 int ctx_plan_wave(emri_ctx* ctx, int64_t n, const OptsN& o) {
   auto it = ctx->plans.find(std::make_tuple(n, o.n_max, o.precision));
   return it == ctx->plans.end() ? 0 : it->second.wave;
@@ -329,12 +334,302 @@ extern "C" int emri_serve_poll(emri_ctx* ctx, uint64_t ticket, double* lnl_host,
 }
 
 // ========================================================= uneven batching
+namespace emri {
+
+// A captured multi-chain launch: one branch per chain inside one CUDA graph.
+struct MultiGraph {
+  std::vector<uint64_t> key;
+  std::vector<Workspace> ws;
+  std::vector<cudaStream_t> branches;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;
+};
+
+void multi_destroy(emri_ctx* ctx) {
+  MultiGraph* m = ctx->multi;
+  if (!m) return;
+  if (m->exec) cudaGraphExecDestroy(m->exec);
+  if (m->graph) cudaGraphDestroy(m->graph);
+  for (Workspace& w : m->ws) w.destroy(ctx);
+  for (cudaStream_t b : m->branches) cudaStreamDestroy(b);
+  for (cudaEvent_t e : m->joins) cudaEventDestroy(e);
+  if (m->fork) cudaEventDestroy(m->fork);
+  if (m->cap) cudaStreamDestroy(m->cap);
+  delete m;
+  ctx->multi = nullptr;
+}
+
+static void key_push(std::vector<uint64_t>& k, const void* p) { k.push_back((uint64_t)(uintptr_t)p); }
+
+}  // namespace emri
+
 extern "C" int emri_loglike_multi(emri_ctx* ctx, const emri_work* items, int n_items, void* stream) {
-  return set_err(EMRI_EINVAL, "multi-chain launches are not available in this build");
+  if (!ctx) return set_err(EMRI_EINVAL, "NULL context");
+  if (n_items < 0 || (n_items > 0 && !items)) return set_err(EMRI_EINVAL, "bad item list");
+  if (n_items == 0) return EMRI_OK;
+  std::vector<OptsN> on(n_items);
+  std::vector<uint64_t> key;
+  for (int i = 0; i < n_items; ++i) {
+    const emri_work& it = items[i];
+    if (!it.ds || it.ds->ctx != ctx) return set_err(EMRI_EINVAL, "item %d: missing or foreign dataset", i);
+    if (it.w < 0) return set_err(EMRI_EINVAL, "item %d: w must be >= 0", i);
+    if (it.w > 0 && (!it.theta_dev || !it.lnl_dev)) return set_err(EMRI_EINVAL, "item %d: NULL pointer", i);
+    int rc = normalize_opts(&it.opts, it.ds->n, &on[i]);
+    if (rc) return rc;
+    key_push(key, it.ds);
+    key_push(key, it.theta_dev);
+    key.push_back((uint64_t)it.w);
+    key_push(key, it.lnl_dev);
+    key_push(key, it.dh_dev);
+    key_push(key, it.hh_dev);
+    key_push(key, it.status_dev);
+    key.push_back(((uint64_t)on[i].precision << 48) | ((uint64_t)on[i].n_max << 32) | ((uint64_t)on[i].ks << 8) |
+                  ((uint64_t)on[i].pn_terms << 1) | (uint64_t)on[i].doppler);
+    uint64_t f[3];
+    memcpy(&f[0], &on[i].n_xi, 8);
+    memcpy(&f[1], &on[i].omega_m, 8);
+    memcpy(&f[2], &on[i].h0, 8);
+    key.insert(key.end(), f, f + 3);
+  }
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(EMRI_ECUDA, "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  MultiGraph* m = ctx->multi;
+  if (!m || m->key != key) {
+    multi_destroy(ctx);
+    m = new MultiGraph();
+    ctx->multi = m;
+    m->key = key;
+    m->ws.resize(n_items);
+    const int nb = std::min(n_items, 64);
+    m->branches.resize(nb);
+    m->joins.resize(n_items);
+    cudaError_t e = cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming);
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) e = cudaStreamCreateWithFlags(&m->branches[b], cudaStreamNonBlocking);
+    for (int i = 0; i < n_items && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&m->joins[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      multi_destroy(ctx);
+      return cuda_err(e, "multi: streams/events");
+    }
+    // per-chain workspaces; the time series of a chain is bounded to ~512 MiB per wave
+    std::vector<int> wave(n_items, 0);
+    for (int i = 0; i < n_items; ++i) {
+      if (items[i].w == 0) continue;
+      const size_t cs = on[i].precision ? sizeof(float2) : sizeof(double2);
+      const size_t per = (size_t)items[i].ds->n * cs;
+      wave[i] = (int)std::max<size_t>(1, std::min<size_t>((size_t)items[i].w, ((size_t)512 << 20) / per));
+      int rc = m->ws[i].reserve(ctx, loglike_layout(items[i].ds->plan, on[i], items[i].w, wave[i], nullptr, nullptr),
+                                m->cap);
+      if (rc) {
+        multi_destroy(ctx);
+        return rc;
+      }
+    }
+    // capture: fork from the capture stream into one branch per chain, join back
+    const bool prof_was_on = ctx->prof.on;
+    ctx->prof.on = false;   // no timing events inside a capture
+    e = cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal);
+    int rc = EMRI_OK;
+    if (e == cudaSuccess) {
+      cudaEventRecord(m->fork, m->cap);
+      for (int i = 0; i < n_items && rc == EMRI_OK; ++i) {
+        cudaStream_t br = m->branches[i % nb];
+        cudaStreamWaitEvent(br, m->fork, 0);
+        if (items[i].w > 0) {
+          Carve cv(m->ws[i].ptr);
+          LoglikeBufs b;
+          loglike_layout(items[i].ds->plan, on[i], items[i].w, wave[i], &cv, &b);
+          int64_t nl = 0;
+          rc = run_loglike(ctx, items[i].ds, items[i].theta_dev, items[i].w, items[i].w, on[i], wave[i], b,
+                           items[i].lnl_dev, items[i].dh_dev, items[i].hh_dev, items[i].status_dev, br, &nl);
+          m->launches += nl;
+        }
+        cudaEventRecord(m->joins[i], br);
+        cudaStreamWaitEvent(m->cap, m->joins[i], 0);
+      }
+      cudaError_t e2 = cudaStreamEndCapture(m->cap, &m->graph);
+      if (e == cudaSuccess) e = e2;
+    }
+    ctx->prof.on = prof_was_on;
+    if (rc == EMRI_OK && e == cudaSuccess) e = cudaGraphInstantiate(&m->exec, m->graph, 0);
+    if (rc != EMRI_OK || e != cudaSuccess) {
+      multi_destroy(ctx);
+      return rc != EMRI_OK ? rc : cuda_err(e, "multi: graph capture");
+    }
+  }
+  cudaError_t e = cudaGraphLaunch(m->exec, s);
+  if (e != cudaSuccess) return cuda_err(e, "multi: graph launch");
+  ctx->launches += m->launches;
+  return EMRI_OK;
 }
 
 // ============================================================== autotuner
+// Candidates, timed on a synthetic batch of the requested shape:
+//  * knot spacing: FP64 keeps 128 (its accuracy budget); mixed tries 512, 1024;
+//  * walkers per wave (the time-series buffer): all, 64, 16, 4 -- small waves
+//    keep a wave's series resident in L2 between the waveform and FFT kernels;
+//  * FFT split n = n1 * n2: the default n2 and its neighbours within the
+//    shared-memory limits.  The split becomes part of a dataset when it is
+//    created, so tune before creating the datasets it should apply to.
+namespace emri {
+
+static void synth_walkers(int w, int64_t n, double dt, std::vector<double>& th) {
+  // representative sources (M ~ 1e6, mu ~ 10, e0 ~ 0.2) starting ~2 T before the LSO
+  th.assign((size_t)kNParam * w, 0.0);
+  const double tsun = kGMsun / (kC * kC * kC);
+  for (int i = 0; i < w; ++i) {
+    const double M = 6e5 + 1e5 * (i % 7), mu = 8.0 + (i % 5), e0 = 0.15 + 0.02 * (i % 6);
+    const double ms = M * tsun, mus = mu * tsun;
+    const double ul = pow((1 - e0 * e0) / (6 + 2 * e0), 1.5);
+    const double u0 = pow(pow(ul, -8.0 / 3.0) + 256.0 / 5.0 * (mus / (ms * ms)) * 2.0 * (double)n * dt, -3.0 / 8.0);
+    double v[kNParam] = {M, mu, 0.3 + 0.05 * (i % 9), e0, u0 / (2 * kPi * ms), 0.1 * i, 0.2 * i, 0.3 * i,
+                         0.4 + 0.1 * (i % 20), 0.5 * i, 0.9, 0.3 * i, 0.8, 0.4, 1.0, 0.0};
+    for (int p = 0; p < kNParam; ++p) th[(size_t)p * w + i] = v[p];
+  }
+}
+
+static bool read_cache(const char* path, int64_t n, int n_max, int prec, Plan* out, int* n2) {
+  if (!path) return false;
+  std::ifstream f(path);
+  std::string line;
+  bool found = false;
+  while (std::getline(f, line)) {
+    long long nn = 0, ks = 0, wave = 0, s2 = 0;
+    int nm = 0, pr = 0;
+    if (sscanf(line.c_str(), "{\"n\": %lld, \"n_max\": %d, \"precision\": %d, \"knot_spacing\": %lld, \"wave\": %lld, \"n2\": %lld",
+               &nn, &nm, &pr, &ks, &wave, &s2) == 6 &&
+        nn == n && nm == n_max && pr == prec) {
+      out->ks = (int)ks;
+      out->wave = (int)wave;
+      *n2 = (int)s2;
+      found = true;   // the last matching line wins
+    }
+  }
+  return found;
+}
+
+}  // namespace emri
+
 extern "C" int emri_autotune(emri_ctx* ctx, const emri_grid* grid, int n_max, int precision, const char* cache_path,
                              int64_t* choice_out) {
-  return set_err(EMRI_EINVAL, "autotuning is not available in this build");
+  if (!ctx) return set_err(EMRI_EINVAL, "NULL context");
+  int rc = check_grid(grid);
+  if (rc) return rc;
+  emri_opts oo;
+  emri_opts_default(&oo);
+  oo.precision = precision;
+  oo.n_max = n_max;
+  OptsN base;
+  if ((rc = normalize_opts(&oo, grid->n, &base))) return rc;
+  const int64_t n = grid->n;
+  Plan best;
+  int best_n2 = 0;
+  if (read_cache(cache_path, n, n_max, precision, &best, &best_n2)) {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->plans[std::make_tuple(n, n_max, precision)] = best;
+    if (best_n2) ctx->fft_split[n] = best_n2;
+    if (choice_out) {
+      choice_out[0] = best.ks;
+      choice_out[1] = best.wave;
+      choice_out[2] = best_n2 ? n / best_n2 : make_fft_plan(n).n1;
+    }
+    return EMRI_OK;
+  }
+  const size_t cs = precision ? sizeof(float2) : sizeof(double2);
+  const int w = (int)std::max<int64_t>(4, std::min<int64_t>(64, ((int64_t)4 << 30) / (n * (int64_t)cs)));
+  std::vector<double> th;
+  synth_walkers(w, n, grid->dt, th);
+  // device buffers for the synthetic batch
+  double* d = nullptr;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(EMRI_ECUDA, "cudaSetDevice");
+  if (cudaMalloc(&d, sizeof(double) * (kNParam + 3) * w) != cudaSuccess) return set_err(EMRI_ENOMEM, "autotune buffers");
+  cudaMemcpy(d, th.data(), sizeof(double) * kNParam * w, cudaMemcpyHostToDevice);
+  double* lnl = d + (size_t)kNParam * w;
+  std::vector<int> ks_c = precision ? std::vector<int>{512, 1024} : std::vector<int>{128};
+  std::vector<int> wave_c = {w, 64, 16, 4};
+  const FftPlan def = make_fft_plan(n);
+  std::vector<int> n2_c = {def.n2};
+  if (def.n2 / 2 >= 32 && n / (def.n2 / 2) <= 4096) n2_c.push_back(def.n2 / 2);
+  if (def.n2 * 2 <= 1024 && n / (def.n2 * 2) >= 32) n2_c.push_back(def.n2 * 2);
+  float best_ms = 1e30f;
+  std::vector<double> zeros((size_t)2 * n, 0.0), psd((size_t)n / 2 + 1);
+  for (int64_t k = 0; k <= n / 2; ++k) {
+    const double f = (double)(k ? k : 1) / ((double)n * grid->dt);
+    psd[k] = 9.18e-52 / (f * f * f * f) + 1.59e-41 + 9.18e-38 * f * f;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int n2 : n2_c) {
+    {
+      std::lock_guard<std::mutex> lk(ctx->mu);
+      ctx->fft_split[n] = n2;
+    }
+    emri_dataset* ds = nullptr;
+    rc = emri_dataset_create(ctx, grid, zeros.data(), 0, psd.data(), 1e-4, 0.5 / grid->dt, &ds);
+    if (rc) break;
+    for (int ks : ks_c) {
+      for (int wv : wave_c) {
+        if (wv > w) continue;
+        emri_opts o = oo;
+        o.knot_spacing = ks;
+        {
+          std::lock_guard<std::mutex> lk(ctx->mu);
+          ctx->plans[std::make_tuple(n, n_max, precision)] = Plan{ks, wv};
+        }
+        float ms = 0.f;
+        for (int rep = 0; rep < 3 && rc == EMRI_OK; ++rep) {
+          cudaEventRecord(e0, ctx->stream);
+          rc = emri_loglike_batch(ctx, ds, d, w, &o, lnl, nullptr, nullptr, nullptr, ctx->stream);
+          cudaEventRecord(e1, ctx->stream);
+          cudaEventSynchronize(e1);
+          float m = 0.f;
+          cudaEventElapsedTime(&m, e0, e1);
+          if (rep > 0) ms += m;   // first run warms up
+        }
+        if (rc) break;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = Plan{ks, wv};
+          best_n2 = n2;
+        }
+      }
+      if (rc) break;
+    }
+    emri_dataset_destroy(ds);
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d);
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (rc == EMRI_OK) {
+      ctx->plans[std::make_tuple(n, n_max, precision)] = best;
+      ctx->fft_split[n] = best_n2;
+    } else {
+      ctx->plans.erase(std::make_tuple(n, n_max, precision));
+      ctx->fft_split.erase(n);
+    }
+  }
+  if (rc) return rc;
+  if (cache_path) {
+    FILE* f = fopen(cache_path, "a");
+    if (f) {
+      fprintf(f, "{\"n\": %lld, \"n_max\": %d, \"precision\": %d, \"knot_spacing\": %d, \"wave\": %d, \"n2\": %d, \"ms\": %.4f}\n",
+              (long long)n, n_max, precision, best.ks, best.wave, best_n2, best_ms / 2.0f);
+      fclose(f);
+    }
+  }
+  if (choice_out) {
+    choice_out[0] = best.ks;
+    choice_out[1] = best.wave;
+    choice_out[2] = n / best_n2;
+  }
+  return EMRI_OK;
 }

@@ -25,13 +25,18 @@ namespace emri {
 constexpr int kFftThreads = 512;   // pass 1 (column groups)
 constexpr int kPass2Threads = 256; // pass 2 (rows)
 
-FftPlan make_fft_plan(int64_t n) {
+FftPlan make_fft_plan(int64_t n, int n2) {
   FftPlan p;
   p.n = n;
   int m = 0;
   while ((int64_t(1) << m) < n) ++m;
   p.log2n = m;
   int m2 = m / 2 < 10 ? m / 2 : 10;
+  if (n2 > 0) {
+    int q = 0;
+    while ((1 << q) < n2) ++q;
+    m2 = q;
+  }
   p.n2 = 1 << m2;
   p.n1 = (int)(n >> m2);
   return p;
@@ -97,91 +102,89 @@ __device__ __forceinline__ C2 twiddle22(const C2* __restrict__ ta, const C2* __r
 }
 
 // ------------------------------------------------- shared-memory Stockham
-// nb transforms of length L (power of two, <= 4096); element i of transform
-// c lives at buf[i*sj + c*sc].  Butterfly b works on transform b % nb, so
-// consecutive threads touch consecutive transforms when sc = 1 (row-major
-// tiles: conflict-free) or consecutive elements when nb = 1.  Each thread
-// stages its outputs in registers so a stage reads everything before
-// anything is overwritten.
-template <typename C2, int MAXB>
-__device__ void smem_fft(C2* buf, int L, int nb, int sj, int sc, int sign, const C2* __restrict__ ta) {
+// NB transforms of length L = 2^LG (compile-time), element i of transform c at
+// buf[i*NB + c] (row-major tile; NB = 1 for a single contiguous transform).
+// Butterfly b works on transform b % NB, element b / NB, so consecutive
+// threads touch consecutive addresses.  Each thread stages its outputs in
+// registers so a stage reads everything before anything is overwritten.
+template <typename C2, int LG, int NB, int NTH>
+__device__ __forceinline__ void smem_fft(C2* buf, int sign, const C2* __restrict__ ta) {
+  constexpr int L = 1 << LG;
+  constexpr int NR4 = LG / 2;
+  constexpr int NBF4 = NB * (L / 4);
+  constexpr int MB4 = (NBF4 + NTH - 1) / NTH;
   const int tid = threadIdx.x;
-  const int nth = blockDim.x;
-  int lg = 0;
-  while ((1 << lg) < L) ++lg;
-  const int nr4 = lg / 2;
-  int ns = 1;
-  for (int st = 0; st < nr4; ++st) {
-    const int q4 = L / 4;
-    const int nbf = nb * q4;
-    C2 y[MAXB][4];
-    int dst[MAXB];
 #pragma unroll
-    for (int r = 0; r < MAXB; ++r) {
-      const int b = tid + r * nth;
+  for (int st = 0; st < NR4; ++st) {
+    const int ns = 1 << (2 * st);
+    constexpr int Q4 = L / 4;
+    C2 y[MB4][4];
+    int dst[MB4];
+#pragma unroll
+    for (int r = 0; r < MB4; ++r) {
+      const int b = tid + r * NTH;
       dst[r] = -1;
-      if (b < nbf) {
-        const int c = b % nb, j = b / nb;
+      if (NBF4 % NTH == 0 || b < NBF4) {
+        const int c = b % NB, j = b / NB;
         const int k = j & (ns - 1);
-        C2* col = buf + c * sc;
-        C2 a0 = col[j * sj], a1 = col[(j + q4) * sj], a2 = col[(j + 2 * q4) * sj], a3 = col[(j + 3 * q4) * sj];
-        if (ns > 1) {
-          const int u = (k * 4096) / (ns * 4);   // twiddle step in 1/4096 cycles
+        C2* col = buf + c;
+        C2 a0 = col[j * NB], a1 = col[(j + Q4) * NB], a2 = col[(j + 2 * Q4) * NB], a3 = col[(j + 3 * Q4) * NB];
+        if (st > 0) {
+          const int u = (k * 4096) >> (2 * st + 2);   // twiddle step in 1/4096 cycles
           a1 = cmul(a1, conj_if(ta[u], sign));
-          a2 = cmul(a2, conj_if(ta[(2 * u) & 4095], sign));
-          a3 = cmul(a3, conj_if(ta[(3 * u) & 4095], sign));
+          a2 = cmul(a2, conj_if(ta[2 * u], sign));
+          a3 = cmul(a3, conj_if(ta[3 * u], sign));
         }
         const C2 b0 = cadd(a0, a2), b1 = csub(a0, a2), b2 = cadd(a1, a3);
-        C2 d = csub(a1, a3);
-        // times -i (forward) or +i (inverse)
-        const C2 b3 = sign < 0 ? CT<C2>::make(d.y, -d.x) : CT<C2>::make(-d.y, d.x);
+        const C2 d = csub(a1, a3);
+        const C2 b3 = sign < 0 ? CT<C2>::make(d.y, -d.x) : CT<C2>::make(-d.y, d.x);   // -i d or +i d
         y[r][0] = cadd(b0, b2);
         y[r][1] = cadd(b1, b3);
         y[r][2] = csub(b0, b2);
         y[r][3] = csub(b1, b3);
-        dst[r] = c * sc + ((j / ns) * ns * 4 + k) * sj;
+        dst[r] = c + (((j >> (2 * st)) << (2 * st + 2)) + k) * NB;
       }
     }
     __syncthreads();
-    const int step = ns * sj;
 #pragma unroll
-    for (int r = 0; r < MAXB; ++r) {
+    for (int r = 0; r < MB4; ++r) {
       if (dst[r] >= 0) {
         buf[dst[r]] = y[r][0];
-        buf[dst[r] + step] = y[r][1];
-        buf[dst[r] + 2 * step] = y[r][2];
-        buf[dst[r] + 3 * step] = y[r][3];
+        buf[dst[r] + ns * NB] = y[r][1];
+        buf[dst[r] + 2 * ns * NB] = y[r][2];
+        buf[dst[r] + 3 * ns * NB] = y[r][3];
       }
     }
     __syncthreads();
-    ns *= 4;
   }
-  if (lg & 1) {
-    const int h2 = L / 2;
-    const int nbf = nb * h2;
-    C2 y[2 * MAXB][2];
-    int dst[2 * MAXB];
+  if (LG & 1) {
+    constexpr int H2 = L / 2;
+    constexpr int NBF2 = NB * H2;
+    constexpr int MB2 = (NBF2 + NTH - 1) / NTH;
+    constexpr int NS = 1 << (2 * NR4);
+    C2 y[MB2][2];
+    int dst[MB2];
 #pragma unroll
-    for (int r = 0; r < 2 * MAXB; ++r) {
-      const int b = tid + r * nth;
+    for (int r = 0; r < MB2; ++r) {
+      const int b = tid + r * NTH;
       dst[r] = -1;
-      if (b < nbf) {
-        const int c = b % nb, j = b / nb;
-        const int k = j & (ns - 1);
-        C2* col = buf + c * sc;
-        C2 a0 = col[j * sj], a1 = col[(j + h2) * sj];
-        if (ns > 1) a1 = cmul(a1, conj_if(ta[(k * 4096) / (ns * 2)], sign));
+      if (NBF2 % NTH == 0 || b < NBF2) {
+        const int c = b % NB, j = b / NB;
+        const int k = j & (NS - 1);
+        C2* col = buf + c;
+        C2 a0 = col[j * NB], a1 = col[(j + H2) * NB];
+        if (NS > 1) a1 = cmul(a1, conj_if(ta[(k * 4096) / (NS * 2)], sign));
         y[r][0] = cadd(a0, a1);
         y[r][1] = csub(a0, a1);
-        dst[r] = c * sc + ((j / ns) * ns * 2 + k) * sj;
+        dst[r] = c + (((j / NS) * NS * 2) + k) * NB;
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < 2 * MAXB; ++r) {
+    for (int r = 0; r < MB2; ++r) {
       if (dst[r] >= 0) {
         buf[dst[r]] = y[r][0];
-        buf[dst[r] + ns * sj] = y[r][1];
+        buf[dst[r] + NS * NB] = y[r][1];
       }
     }
     __syncthreads();
@@ -229,41 +232,42 @@ struct FftCfg<float2> {
 };
 
 // ------------------------------------------------------------- pass 1
-// CTA = ncol adjacent columns j1, all n2 rows: the tile is staged row-major
-// (rows of ncol contiguous elements), transformed along the rows index, and
-// written back in place with the inter-pass twiddle.
-template <typename C2>
-__global__ void __launch_bounds__(kFftThreads) k3_pass1(C2* __restrict__ z, int64_t n, int n1, int n2, int ncol,
-                                                        int sign, int shift22, const C2* __restrict__ ta,
-                                                        const C2* __restrict__ tb) {
+// CTA = NB adjacent columns j1, all n2 = 2^LG rows: the tile is staged
+// row-major (rows of NB contiguous elements), transformed along the rows
+// index, and written back in place with the inter-pass twiddle.
+template <typename C2, int LG, int NB>
+__global__ void __launch_bounds__(kFftThreads) k3_pass1(C2* __restrict__ z, int64_t n, int n1, int sign, int shift22,
+                                                        const C2* __restrict__ ta, const C2* __restrict__ tb) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C2* buf = reinterpret_cast<C2*>(smraw);
+  constexpr int N2 = 1 << LG;
   C2* zw = z + (int64_t)blockIdx.y * n;
-  const int j10 = blockIdx.x * ncol;
-  tile_load<C2, 8>(buf, zw + j10, n1, ncol, n2);
+  const int j10 = blockIdx.x * NB;
+  tile_load<C2, 8>(buf, zw + j10, n1, NB, N2);
   __syncthreads();
-  smem_fft<C2, FftCfg<C2>::kMaxB>(buf, n2, ncol, ncol, 1, sign, ta);
-  for (int idx = threadIdx.x; idx < ncol * n2; idx += blockDim.x) {
-    const int c = idx % ncol, k2 = idx / ncol;
+  smem_fft<C2, LG, NB, kFftThreads>(buf, sign, ta);
+  for (int idx = threadIdx.x; idx < NB * N2; idx += kFftThreads) {
+    const int c = idx % NB, k2 = idx / NB;
     const uint32_t m = (uint32_t)((j10 + c) * k2) << shift22;
     zw[j10 + c + (int64_t)n1 * k2] = cmul(buf[idx], twiddle22(ta, tb, m, sign));
   }
 }
 
 // --------------------------------------------------- pass 2, natural order
-template <typename C2>
+template <typename C2, int LG>
 __global__ void __launch_bounds__(kPass2Threads, 2) k4_pass2_store(const C2* __restrict__ y, C2* __restrict__ out,
-                                                              int64_t n, int n1, int n2, int sign,
-                                                              const C2* __restrict__ ta) {
+                                                                   int64_t n, int n2, int sign,
+                                                                   const C2* __restrict__ ta) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C2* buf = reinterpret_cast<C2*>(smraw);
+  constexpr int N1 = 1 << LG;
   const int k2 = blockIdx.x;
-  const C2* row = y + (int64_t)blockIdx.y * n + (int64_t)n1 * k2;
-  tile_load<C2, 4>(buf, row, 0, n1, 1);
+  const C2* row = y + (int64_t)blockIdx.y * n + (int64_t)N1 * k2;
+  tile_load<C2, 4>(buf, row, 0, N1, 1);
   __syncthreads();
-  smem_fft<C2, FftCfg<C2>::kMaxB>(buf, n1, 1, 1, 1, sign, ta);
+  smem_fft<C2, LG, 1, kPass2Threads>(buf, sign, ta);
   C2* o = out + (int64_t)blockIdx.y * n;
-  for (int k1 = threadIdx.x; k1 < n1; k1 += blockDim.x) o[k2 + (int64_t)n2 * k1] = buf[k1];
+  for (int k1 = threadIdx.x; k1 < N1; k1 += kPass2Threads) o[k2 + (int64_t)n2 * k1] = buf[k1];
 }
 
 // -------------------------------------------- pass 2 fused with the IP
@@ -307,55 +311,49 @@ struct AccF {
   }
 };
 
-template <typename C2, typename WT, typename Acc>
-__global__ void __launch_bounds__(kPass2Threads, 2) k4_pass2_ip(const C2* __restrict__ y, int64_t n, int n1, int n2,
-                                                           const C2* __restrict__ ta, const WalkerC* __restrict__ wcs,
-                                                           const C2* __restrict__ dtab, const C2* __restrict__ dperm,
-                                                           const WT* __restrict__ wperm, double2* __restrict__ partial) {
+template <typename C2, typename WT, typename Acc, int LG>
+__global__ void __launch_bounds__(kPass2Threads, 2) k4_pass2_ip(const C2* __restrict__ y, int64_t n, int n2,
+                                                                const C2* __restrict__ ta, const WalkerC* __restrict__ wcs,
+                                                                const C2* __restrict__ dtab, const C2* __restrict__ rtab,
+                                                                const C2* __restrict__ dperm, const WT* __restrict__ wperm,
+                                                                double2* __restrict__ partial) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C2* buf = reinterpret_cast<C2*>(smraw);
-  __shared__ double2 afac;
-  __shared__ double2 red[kPass2Threads / 32];
+  __shared__ Acc red[kPass2Threads / 32];
   using T = typename CT<C2>::T;
+  constexpr int N1 = 1 << LG;
   const int k2 = blockIdx.x, wk = blockIdx.y;
-  const C2* row = y + (int64_t)wk * n + (int64_t)n1 * k2;
-  tile_load<C2, 4>(buf, row, 0, n1, 1);
-  if (threadIdx.x == 0) {
-    // exp(-2 pi i frac(k2 r))
-    const double rh = wcs[wk].r_hi, rl = wcs[wk].r_lo;
-    dd p = dd_add_d(two_prod((double)k2, rh), (double)k2 * rl);
-    dd f = dd_frac(p);
-    double s, c;
-    sincospi(2.0 * f.hi, &s, &c);
-    afac = make_double2(c, -s);
-  }
+  const C2* row = y + (int64_t)wk * n + (int64_t)N1 * k2;
+  tile_load<C2, 4>(buf, row, 0, N1, 1);
   __syncthreads();
-  smem_fft<C2, FftCfg<C2>::kMaxB>(buf, n1, 1, 1, 1, -1, ta);
-  const C2 a = CT<C2>::make((T)afac.x, (T)afac.y);
-  const C2 cn = CT<C2>::make((T)wcs[wk].cn_re, (T)wcs[wk].cn_im);
-  const C2* tabw = dtab + (int64_t)wk * n1;
-  const int64_t base = (int64_t)k2 * n1;
+  smem_fft<C2, LG, 1, kPass2Threads>(buf, -1, ta);
+  const C2 a = rtab[(int64_t)wk * n2 + k2];                 // exp(-2 pi i frac(k2 r))
+  const C2* tabw = dtab + (int64_t)wk * N1;
+  const C2 cnv = CT<C2>::make((T)wcs[wk].cn_re, (T)wcs[wk].cn_im);
+  const int64_t base = (int64_t)k2 * N1;
   Acc acc;
   acc.init();
-  for (int k1 = threadIdx.x; k1 < n1; k1 += blockDim.x) {
+  for (int k1 = threadIdx.x; k1 < N1; k1 += kPass2Threads) {
     const C2 H = buf[k1];
     const T wv = (T)wperm[base + k1];
     const C2 D = dperm[base + k1];
     C2 f = cmul(a, tabw[k1]);
-    if (2 * k1 > n1 || (2 * k1 == n1 && k2 > 0)) f = cmul(f, cn);   // signed index k - n
+    if (2 * k1 > N1 || (2 * k1 == N1 && k2 > 0)) f = cmul(f, cnv);   // signed index k - n
     const C2 Hd = cmul(H, f);
     acc.add(wv * (D.x * Hd.x + D.y * Hd.y), wv * (H.x * H.x + H.y * H.y));
   }
-  // fixed-shape reduction: warp xor tree, then warp 0 over the warp sums
+  // fixed-shape reduction in the accumulator's own arithmetic: warp xor tree,
+  // then warp 0 over the warp partials
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) acc.shfl_merge(off);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) red[wid] = acc.get();
+  if (lane == 0) red[wid] = acc;
   __syncthreads();
   if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-    double2 v = lane < nw ? red[lane] : make_double2(0.0, 0.0);
-    AccD r{v.x, v.y};
+    constexpr int NW = kPass2Threads / 32;
+    Acc r;
+    if (lane < NW) r = red[lane];
+    else r.init();
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) r.shfl_merge(off);
     if (lane == 0) partial[(int64_t)wk * n2 + k2] = r.get();
@@ -441,50 +439,95 @@ __global__ void k_inner_dd(const double2* __restrict__ d, const double* __restri
 }
 
 // ------------------------------------------------------------ launchers
-static size_t pass1_smem(const FftPlan& p, bool fp32, int& ncol) {
-  ncol = fp32 ? FftCfg<float2>::kCols : FftCfg<double2>::kCols;
-  if (ncol > p.n1) ncol = p.n1;
-  return (size_t)ncol * p.n2 * (fp32 ? sizeof(float2) : sizeof(double2));
+template <typename C2>
+static size_t csize() { return sizeof(C2); }
+
+template <typename C2, int NB, int LG>
+static void pass1_inst(C2* z, int batch, const FftPlan& p, int sign, int shift, const C2* ta, const C2* tb,
+                       cudaStream_t s) {
+  dim3 g(p.n1 / NB, batch);
+  k3_pass1<C2, LG, NB><<<g, kFftThreads, (size_t)NB * (1 << LG) * sizeof(C2), s>>>(z, p.n, p.n1, sign, shift, ta, tb);
+}
+
+template <typename C2, int NB>
+static void pass1_dispatch(C2* z, int batch, const FftPlan& p, int sign, const C2* ta, const C2* tb, cudaStream_t s) {
+  const int shift = 22 - p.log2n;
+  int lg = 0;
+  while ((1 << lg) < p.n2) ++lg;
+  switch (lg) {
+    case 5: pass1_inst<C2, NB, 5>(z, batch, p, sign, shift, ta, tb, s); break;
+    case 6: pass1_inst<C2, NB, 6>(z, batch, p, sign, shift, ta, tb, s); break;
+    case 7: pass1_inst<C2, NB, 7>(z, batch, p, sign, shift, ta, tb, s); break;
+    case 8: pass1_inst<C2, NB, 8>(z, batch, p, sign, shift, ta, tb, s); break;
+    case 9: pass1_inst<C2, NB, 9>(z, batch, p, sign, shift, ta, tb, s); break;
+    default: pass1_inst<C2, NB, 10>(z, batch, p, sign, shift, ta, tb, s); break;
+  }
 }
 
 void launch_fft_pass1(void* z, int batch, const FftPlan& p, bool fp32, int sign, const Twiddles& t,
                       cudaStream_t s) {
   if (batch <= 0) return;
-  int ncol;
-  const size_t sm = pass1_smem(p, fp32, ncol);
-  dim3 g(p.n1 / ncol, batch);
-  const int shift = 22 - p.log2n;
   if (fp32)
-    k3_pass1<float2><<<g, kFftThreads, sm, s>>>((float2*)z, p.n, p.n1, p.n2, ncol, sign, shift, t.ta32, t.tb32);
+    pass1_dispatch<float2, FftCfg<float2>::kCols>((float2*)z, batch, p, sign, t.ta32, t.tb32, s);
   else
-    k3_pass1<double2><<<g, kFftThreads, sm, s>>>((double2*)z, p.n, p.n1, p.n2, ncol, sign, shift, t.ta64, t.tb64);
+    pass1_dispatch<double2, FftCfg<double2>::kCols>((double2*)z, batch, p, sign, t.ta64, t.tb64, s);
+}
+
+#define EMRI_LG_SWITCH(lg, CALL)  \
+  switch (lg) {                   \
+    case 5: CALL(5); break;       \
+    case 6: CALL(6); break;       \
+    case 7: CALL(7); break;       \
+    case 8: CALL(8); break;       \
+    case 9: CALL(9); break;       \
+    case 10: CALL(10); break;     \
+    case 11: CALL(11); break;     \
+    default: CALL(12); break;     \
+  }
+
+static int log2i(int v) {
+  int lg = 0;
+  while ((1 << lg) < v) ++lg;
+  return lg;
 }
 
 void launch_fft_pass2_store(const void* y, void* out, int batch, const FftPlan& p, bool fp32, int sign,
                             const Twiddles& t, cudaStream_t s) {
   if (batch <= 0) return;
   dim3 g(p.n2, batch);
-  if (fp32)
-    k4_pass2_store<float2><<<g, kPass2Threads, p.n1 * sizeof(float2), s>>>((const float2*)y, (float2*)out, p.n, p.n1,
-                                                                          p.n2, sign, t.ta32);
-  else
-    k4_pass2_store<double2><<<g, kPass2Threads, p.n1 * sizeof(double2), s>>>((const double2*)y, (double2*)out, p.n,
-                                                                            p.n1, p.n2, sign, t.ta64);
+  const int lg = log2i(p.n1);
+  if (fp32) {
+#define CALL32(L) k4_pass2_store<float2, L><<<g, kPass2Threads, p.n1 * sizeof(float2), s>>>( \
+      (const float2*)y, (float2*)out, p.n, p.n2, sign, t.ta32)
+    EMRI_LG_SWITCH(lg, CALL32)
+#undef CALL32
+  } else {
+#define CALL64(L) k4_pass2_store<double2, L><<<g, kPass2Threads, p.n1 * sizeof(double2), s>>>( \
+      (const double2*)y, (double2*)out, p.n, p.n2, sign, t.ta64)
+    EMRI_LG_SWITCH(lg, CALL64)
+#undef CALL64
+  }
 }
 
 void launch_fft_pass2_ip(const void* y, int w, const FftPlan& p, bool fp32, const Twiddles& t, const WalkerC* wc,
-                         const void* delay_tab, const void* data_perm, const void* wt_perm, double2* partial,
-                         cudaStream_t s) {
+                         const void* delay_tab, const void* row_tab, const void* data_perm, const void* wt_perm,
+                         double2* partial, cudaStream_t s) {
   if (w <= 0) return;
   dim3 g(p.n2, w);
-  if (fp32)
-    k4_pass2_ip<float2, float, AccF><<<g, kPass2Threads, p.n1 * sizeof(float2), s>>>(
-        (const float2*)y, p.n, p.n1, p.n2, t.ta32, wc, (const float2*)delay_tab, (const float2*)data_perm,
-        (const float*)wt_perm, partial);
-  else
-    k4_pass2_ip<double2, double, AccD><<<g, kPass2Threads, p.n1 * sizeof(double2), s>>>(
-        (const double2*)y, p.n, p.n1, p.n2, t.ta64, wc, (const double2*)delay_tab, (const double2*)data_perm,
-        (const double*)wt_perm, partial);
+  const int lg = log2i(p.n1);
+  if (fp32) {
+#define CALLI32(L) k4_pass2_ip<float2, float, AccF, L><<<g, kPass2Threads, p.n1 * sizeof(float2), s>>>( \
+      (const float2*)y, p.n, p.n2, t.ta32, wc, (const float2*)delay_tab, (const float2*)row_tab,           \
+      (const float2*)data_perm, (const float*)wt_perm, partial)
+    EMRI_LG_SWITCH(lg, CALLI32)
+#undef CALLI32
+  } else {
+#define CALLI64(L) k4_pass2_ip<double2, double, AccD, L><<<g, kPass2Threads, p.n1 * sizeof(double2), s>>>( \
+      (const double2*)y, p.n, p.n2, t.ta64, wc, (const double2*)delay_tab, (const double2*)row_tab,            \
+      (const double2*)data_perm, (const double*)wt_perm, partial)
+    EMRI_LG_SWITCH(lg, CALLI64)
+#undef CALLI64
+  }
 }
 
 void launch_finalize(const double2* partial, int n2, const WalkerC* wc, int w, double dh_scale, double hh_scale,
@@ -513,14 +556,19 @@ void launch_inner_dd(const double2* d, const double* w, int64_t n, double* out, 
 }
 
 // Raise the dynamic shared-memory limit of the FFT kernels (once per device).
+template <typename F>
+static void raise(F f) {
+  cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
 void fft_set_smem_limits() {
-  const int lim = 200 * 1024;
-  cudaFuncSetAttribute(k3_pass1<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k3_pass1<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k4_pass2_store<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k4_pass2_store<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k4_pass2_ip<double2, double, AccD>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k4_pass2_ip<float2, float, AccF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+#define P1(L) raise(k3_pass1<double2, L, FftCfg<double2>::kCols>), raise(k3_pass1<float2, L, FftCfg<float2>::kCols>)
+  P1(5); P1(6); P1(7); P1(8); P1(9); P1(10);
+#undef P1
+#define P2(L) raise(k4_pass2_store<double2, L>), raise(k4_pass2_store<float2, L>), \
+              raise(k4_pass2_ip<double2, double, AccD, L>), raise(k4_pass2_ip<float2, float, AccF, L>)
+  P2(5); P2(6); P2(7); P2(8); P2(9); P2(10); P2(11); P2(12);
+#undef P2
 }
 
 }  // namespace emri

@@ -1,10 +1,19 @@
 // k_orbit.cu -- step S1: the AK orbit of Eq. (1), FP64.
 //
 // The paper integrates Y = {Phi, nu, e, gamma~, alpha} with a standard
-// Runge-Kutta solver on the time grid (Sec. 3, "Waveform computation"; the
-// right-hand side is the AK system of Barack & Cutler 2004 that the paper
-// cites).  Here each walker is one thread that integrates the same system
-// with classical RK4 at macro steps of K_s samples, in the variable
+// solver on the time grid (Sec. 3, "Waveform computation"; the right-hand
+// side is the AK system of Barack & Cutler 2004 that the paper cites).
+// A step-by-step integrator is a serial FP64 dependency chain per walker, and
+// on this GPU one FP64 warp instruction occupies its SM sub-partition for ~64
+// cycles; so the orbit is integrated in parallel in time instead: one warp
+// per walker, segments of S samples, the solution on each segment
+// represented by its values at the 32 Chebyshev-Gauss-Lobatto nodes (one per
+// lane) and found by Picard iteration y(t) = y(t_a) + int f(y) with the
+// spectral integration matrix (Chebyshev-Picard iteration; converges in 4-7
+// sweeps here since a segment is ~1e-3 of the radiation-reaction time).  The
+// knots every K_s samples are read off the segment's polynomial (integral
+// weights at the knot positions).  The same system is written in the
+// variable
 // v = x^(1/3) = (2 pi G M nu / c^3)^(1/3) instead of nu: then x^(2/3) = v^2,
 // x^(11/3) = v^11 and (1-e^2)^(-k/2) = s^k with one s = 1/sqrt(1-e^2), so the
 // right-hand side is polynomial apart from one reciprocal square root and the
@@ -119,6 +128,54 @@ __device__ __forceinline__ void write_knot(Knot* kn, const OrbState& y, const do
   *kn = k;
 }
 
+// Serial compensated RK4 at the knot step from knot k0 (state y, already
+// written) over knots k0+1..k1.  Returns true if the orbit stayed inside the
+// LSO; otherwise locates the plunge sample jp by re-integrating the crossing
+// interval at the sampling step, writes the first knot past the crossing
+// (the right end of the interval holding the last valid samples) and sets
+// last to it.
+__device__ bool rk4_span(const OrbSrc& s, const WalkerC& c, OrbState& y, int64_t k0, int64_t k1, int ks, double dt,
+                         double t0, int doppler, int64_t n, Knot* kn, int64_t& jp, uint32_t& st, int64_t& last) {
+  const double h = (double)ks * dt;
+  double r[5];
+  ak_rhs_v(s, y.v_hi, y.e_hi, r[0], r[1], r[2], r[3], r[4]);
+  for (int64_t k = k0; k < k1; ++k) {
+    OrbState y0 = y;
+    rk4_step(s, y, h, r);
+    if (!state_finite(y) || plunged(y.v_hi, y.e_hi)) {
+      OrbState f = y0;
+      int64_t j = (k + 1) * ks;
+      bool found = false;
+      for (int q = 1; q <= ks; ++q) {
+        double rr[5];
+        ak_rhs_v(s, f.v_hi, f.e_hi, rr[0], rr[1], rr[2], rr[3], rr[4]);
+        rk4_step(s, f, dt, rr);
+        if (!state_finite(f) || plunged(f.v_hi, f.e_hi)) {
+          j = k * ks + q;
+          found = true;
+          st |= state_finite(f) ? ST_PLUNGE : ST_NONFINITE;
+          break;
+        }
+      }
+      if (!found) st |= state_finite(y) ? ST_PLUNGE : ST_NONFINITE;
+      jp = j < n ? j : n;
+      if (jp == n) st &= ~(uint32_t)ST_PLUNGE;
+      if (state_finite(y)) {
+        ak_rhs_v(s, y.v_hi, y.e_hi, r[0], r[1], r[2], r[3], r[4]);
+        write_knot(kn + k + 1, y, r, c, t0 + (double)((k + 1) * ks) * dt, doppler);
+      } else {
+        kn[k + 1] = kn[k];
+      }
+      last = k + 1;
+      return false;
+    }
+    ak_rhs_v(s, y.v_hi, y.e_hi, r[0], r[1], r[2], r[3], r[4]);
+    write_knot(kn + k + 1, y, r, c, t0 + (double)((k + 1) * ks) * dt, doppler);
+    last = k + 1;
+  }
+  return true;
+}
+
 __global__ void k1_orbit(WalkerC* __restrict__ wcs, int w, int64_t n, double dt, double t0, int ks, int pn,
                          int doppler, Knot* __restrict__ knots) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -134,7 +191,6 @@ __global__ void k1_orbit(WalkerC* __restrict__ wcs, int w, int64_t n, double dt,
   }
   OrbSrc s{c.kv, c.ke, c.inv2pim, c.spin, c.coslam, pn};
   OrbState y{c.v0_hi, c.v0_lo, c.e0, 0.0, c.phi0c, 0.0, c.gam0c, 0.0, c.alp0c, 0.0};
-  const double h = (double)ks * dt;
   int64_t jp = n;
   uint32_t st = 0;
   double r[5];
@@ -145,42 +201,7 @@ __global__ void k1_orbit(WalkerC* __restrict__ wcs, int w, int64_t n, double dt,
     jp = 0;
     st |= ST_PLUNGE;
   } else {
-    for (int64_t k = 0; k < nk; ++k) {
-      OrbState y0 = y;
-      rk4_step(s, y, h, r);
-      if (!state_finite(y) || plunged(y.v_hi, y.e_hi)) {
-        // locate the first sample of (k ks, (k+1) ks] at or past the LSO by
-        // re-integrating the interval at the sampling step
-        OrbState f = y0;
-        int64_t j = (k + 1) * ks;
-        bool found = false;
-        for (int q = 1; q <= ks; ++q) {
-          double rr[5];
-          ak_rhs_v(s, f.v_hi, f.e_hi, rr[0], rr[1], rr[2], rr[3], rr[4]);
-          rk4_step(s, f, dt, rr);
-          if (!state_finite(f) || plunged(f.v_hi, f.e_hi)) {
-            j = k * ks + q;
-            found = true;
-            st |= state_finite(f) ? ST_PLUNGE : ST_NONFINITE;
-            break;
-          }
-        }
-        if (!found) st |= state_finite(y) ? ST_PLUNGE : ST_NONFINITE;
-        jp = j < n ? j : n;
-        if (jp == n) st &= ~(uint32_t)ST_PLUNGE;
-        if (state_finite(y)) {
-          ak_rhs_v(s, y.v_hi, y.e_hi, r[0], r[1], r[2], r[3], r[4]);
-          write_knot(kn + k + 1, y, r, c, t0 + (double)((k + 1) * ks) * dt, doppler);
-        } else {
-          kn[k + 1] = kn[k];
-        }
-        last = k + 1;
-        break;
-      }
-      ak_rhs_v(s, y.v_hi, y.e_hi, r[0], r[1], r[2], r[3], r[4]);
-      write_knot(kn + k + 1, y, r, c, t0 + (double)((k + 1) * ks) * dt, doppler);
-      last = k + 1;
-    }
+    rk4_span(s, c, y, 0, nk, ks, dt, t0, doppler, n, kn, jp, st, last);
   }
   // knots past a plunge repeat the last one written (their samples are zeroed)
   for (int64_t q = last + 1; q <= nk; ++q) kn[q] = kn[last];
@@ -188,10 +209,199 @@ __global__ void k1_orbit(WalkerC* __restrict__ wcs, int w, int64_t n, double dt,
   wcs[i].status = c.status | st;
 }
 
+// ------------------------------------------------------ Chebyshev-Picard
+// qn[j*32 + i] = int_0^{tau_i} l_j(tau) dtau (transposed, nodes tau_i =
+// (1 - cos(pi i/31))/2 on the unit segment); qk[q*32 + j] = int_0^{q/128} l_j,
+// q = 0..128 (knot positions of the finest knot grid).  Built on the host.
+constexpr int kSeg = 8192;         // samples per segment (n if smaller)
+constexpr int kOrbitWarps = 4;     // walkers per CTA
+
+__device__ __forceinline__ void ak_rate_ve(const OrbSrc& s, double v, double e, double& dv, double& de) {
+  double d0, d1, d2;
+  ak_rhs_v(s, v, e, dv, de, d0, d1, d2);
+}
+
+__global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi(WalkerC* __restrict__ wcs, int w, int64_t n, double dt,
+                                                                   double t0, int ks, int pn, int doppler,
+                                                                   const double* __restrict__ qn_g,
+                                                                   const double* __restrict__ qk_g,
+                                                                   Knot* __restrict__ knots) {
+  __shared__ double qn[32 * 32];
+  __shared__ double qk[129 * 32];
+  __shared__ double fs[kOrbitWarps][5][32];
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  const int seg = (int)(n < kSeg ? n : kSeg);
+  const int K = seg / ks;                   // knots per segment
+  const int qstride = 128 / K;
+  for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) qn[i] = qn_g[i];
+  for (int q = 0; q <= K; ++q)
+    for (int i = threadIdx.x; i < 32; i += blockDim.x) qk[q * 32 + i] = qk_g[(q * qstride) * 32 + i];
+  __syncthreads();
+  const int wk = blockIdx.x * kOrbitWarps + wq;
+  if (wk >= w) return;
+  const WalkerC c = wcs[wk];
+  const int64_t nk = n / ks;
+  Knot* kn = knots + (int64_t)wk * (nk + 1);
+  if (c.status & ST_BADPARAM) {
+    Knot zk = {};
+    for (int64_t k = lane; k <= nk; k += 32) kn[k] = zk;
+    if (lane == 0) wcs[wk].j_plunge = 0;
+    return;
+  }
+  const OrbSrc s{c.kv, c.ke, c.inv2pim, c.spin, c.coslam, pn};
+  // segment-start state (identical in every lane), compensated
+  OrbState y{c.v0_hi, c.v0_lo, c.e0, 0.0, c.phi0c, 0.0, c.gam0c, 0.0, c.alp0c, 0.0};
+  const double H = (double)seg * dt;
+  const double taui = 0.5 * (1.0 - cospi((double)lane / 31.0));
+  double* f = &fs[wq][0][0];
+  int64_t jp = n;
+  uint32_t st = 0;
+  int64_t last = -1;   // last knot written
+  if (plunged(y.v_hi, y.e_hi)) {
+    double r[5];
+    ak_rhs_v(s, y.v_hi, y.e_hi, r[0], r[1], r[2], r[3], r[4]);
+    if (lane == 0) write_knot(kn, y, r, c, t0, doppler);
+    jp = 0;
+    st |= ST_PLUNGE;
+    last = 0;
+  }
+  const int64_t nseg = n / seg;
+  for (int64_t g = 0; g < nseg && jp == n; ++g) {
+    const OrbState ys = y;   // segment start
+    const int64_t kbase = g * (int64_t)K;
+    // Euler start, then Picard sweeps on (v, e) at the nodes
+    double f0v, f0e;
+    ak_rate_ve(s, y.v_hi, y.e_hi, f0v, f0e);
+    double v = y.v_hi + (y.v_lo + H * taui * f0v);
+    double e = y.e_hi + (y.e_lo + H * taui * f0e);
+    bool convw = false;
+    for (int it = 0; it < 30; ++it) {
+      double fv, fe;
+      ak_rate_ve(s, v, e, fv, fe);
+      __syncwarp();
+      f[0 * 32 + lane] = fv;
+      f[1 * 32 + lane] = fe;
+      __syncwarp();
+      double sv = 0.0, se = 0.0;
+#pragma unroll 8
+      for (int j = 0; j < 32; ++j) {
+        const double q = qn[j * 32 + lane];
+        sv = fma(q, f[0 * 32 + j], sv);
+        se = fma(q, f[1 * 32 + j], se);
+      }
+      const double vn = y.v_hi + (y.v_lo + H * sv);
+      const double en = y.e_hi + (y.e_lo + H * se);
+      // settled to within about two ulps (iterates can cycle at rounding level)
+      const bool conv = fabs(vn - v) <= 4e-16 * fabs(y.v_hi) && fabs(en - e) <= 2e-16;
+      v = vn;
+      e = en;
+      const bool ok = isfinite(v) && isfinite(e);
+      if (__all_sync(0xffffffffu, conv || !ok)) {
+        convw = __all_sync(0xffffffffu, conv && ok);
+        break;
+      }
+    }
+    // a segment that reaches the LSO, or on which the iteration does not
+    // settle, is integrated serially instead (fallback below)
+    bool serial = !convw;
+    if (!serial) {
+      // all five rates at the nodes
+      double r[5];
+      ak_rhs_v(s, v, e, r[0], r[1], r[2], r[3], r[4]);
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < 5; ++q) f[q * 32 + lane] = r[q];
+      __syncwarp();
+      // knots q = 0..K-1 of this segment (q = 0 is the start), and the end
+      // state (q = K), which every lane takes as the next segment's start
+      bool anybad = false;
+      for (int q0 = 0; q0 <= K; q0 += 32) {
+        const int q = q0 + lane;
+        bool bad = false;
+        OrbState yk = y;
+        if (q <= K) {
+          double sm[5] = {0, 0, 0, 0, 0};
+#pragma unroll 4
+          for (int j = 0; j < 32; ++j) {
+            const double wq_ = qk[q * 32 + j];
+#pragma unroll
+            for (int cc = 0; cc < 5; ++cc) sm[cc] = fma(wq_, f[cc * 32 + j], sm[cc]);
+          }
+          comp_add_small(yk.v_hi, yk.v_lo, H * sm[0]);
+          comp_add(yk.e_hi, yk.e_lo, H * sm[1]);
+          comp_add(yk.p_hi, yk.p_lo, H * sm[2]);
+          comp_add(yk.g_hi, yk.g_lo, H * sm[3]);
+          comp_add(yk.a_hi, yk.a_lo, H * sm[4]);
+          bad = q > 0 && (!state_finite(yk) || plunged(yk.v_hi, yk.e_hi));
+          if (q < K && !bad) {
+            double rk[5];
+            ak_rhs_v(s, yk.v_hi, yk.e_hi, rk[0], rk[1], rk[2], rk[3], rk[4]);
+            write_knot(kn + kbase + q, yk, rk, c, t0 + (double)((kbase + q) * ks) * dt, doppler);
+          }
+        }
+        anybad |= __any_sync(0xffffffffu, bad);
+        const int src = K - q0;
+        if (src >= 0 && src < 32) {
+          y.v_hi = __shfl_sync(0xffffffffu, yk.v_hi, src); y.v_lo = __shfl_sync(0xffffffffu, yk.v_lo, src);
+          y.e_hi = __shfl_sync(0xffffffffu, yk.e_hi, src); y.e_lo = __shfl_sync(0xffffffffu, yk.e_lo, src);
+          y.p_hi = __shfl_sync(0xffffffffu, yk.p_hi, src); y.p_lo = __shfl_sync(0xffffffffu, yk.p_lo, src);
+          y.g_hi = __shfl_sync(0xffffffffu, yk.g_hi, src); y.g_lo = __shfl_sync(0xffffffffu, yk.g_lo, src);
+          y.a_hi = __shfl_sync(0xffffffffu, yk.a_hi, src); y.a_lo = __shfl_sync(0xffffffffu, yk.a_lo, src);
+        }
+      }
+      serial = anybad;
+    }
+    if (serial) {
+      // lane 0 redoes the segment with the knot-step RK4 of k1_orbit from
+      // the segment start; its knots replace any written above
+      __syncwarp();
+      int valid = 1;
+      if (lane == 0) {
+        OrbState yy = ys;
+        double r0[5];
+        ak_rhs_v(s, yy.v_hi, yy.e_hi, r0[0], r0[1], r0[2], r0[3], r0[4]);
+        write_knot(kn + kbase, yy, r0, c, t0 + (double)(kbase * ks) * dt, doppler);
+        valid = rk4_span(s, c, yy, kbase, kbase + K, ks, dt, t0, doppler, n, kn, jp, st, last) ? 1 : 0;
+        y = yy;
+      }
+      valid = __shfl_sync(0xffffffffu, valid, 0);
+      jp = __shfl_sync(0xffffffffu, jp, 0);
+      st = __shfl_sync(0xffffffffu, st, 0);
+      last = __shfl_sync(0xffffffffu, last, 0);
+      y.v_hi = __shfl_sync(0xffffffffu, y.v_hi, 0); y.v_lo = __shfl_sync(0xffffffffu, y.v_lo, 0);
+      y.e_hi = __shfl_sync(0xffffffffu, y.e_hi, 0); y.e_lo = __shfl_sync(0xffffffffu, y.e_lo, 0);
+      y.p_hi = __shfl_sync(0xffffffffu, y.p_hi, 0); y.p_lo = __shfl_sync(0xffffffffu, y.p_lo, 0);
+      y.g_hi = __shfl_sync(0xffffffffu, y.g_hi, 0); y.g_lo = __shfl_sync(0xffffffffu, y.g_lo, 0);
+      y.a_hi = __shfl_sync(0xffffffffu, y.a_hi, 0); y.a_lo = __shfl_sync(0xffffffffu, y.a_lo, 0);
+      if (!valid) break;
+    }
+    last = kbase + K - 1;
+  }
+  if (jp == n && last == nk - 1) {
+    // the end knot (sample n) from the final state
+    double r[5];
+    ak_rhs_v(s, y.v_hi, y.e_hi, r[0], r[1], r[2], r[3], r[4]);
+    if (lane == 0) write_knot(kn + nk, y, r, c, t0 + (double)(nk * ks) * dt, doppler);
+    last = nk;
+  }
+  __syncwarp();
+  // knots past a plunge repeat the last one written (their samples are zeroed)
+  for (int64_t q = last + 1 + lane; q <= nk; q += 32) kn[q] = kn[last];
+  if (lane == 0) {
+    wcs[wk].j_plunge = jp;
+    wcs[wk].status = c.status | st;
+  }
+}
+
 void launch_orbit(WalkerC* wc, int w, int64_t n, double dt, double t0, const OptsN& o, Knot* knots,
-                  cudaStream_t s) {
+                  const double* mcpi_tab, cudaStream_t s) {
   if (w <= 0) return;
-  k1_orbit<<<(w + 31) / 32, 32, 0, s>>>(wc, w, n, dt, t0, o.ks, o.pn_terms, o.doppler, knots);
+  if (mcpi_tab) {
+    k1_orbit_mcpi<<<(w + kOrbitWarps - 1) / kOrbitWarps, 32 * kOrbitWarps, 0, s>>>(
+        wc, w, n, dt, t0, o.ks, o.pn_terms, o.doppler, mcpi_tab, mcpi_tab + 32 * 32, knots);
+  } else {
+    k1_orbit<<<(w + 31) / 32, 32, 0, s>>>(wc, w, n, dt, t0, o.ks, o.pn_terms, o.doppler, knots);
+  }
 }
 
 }  // namespace emri

@@ -164,16 +164,17 @@ __global__ void k0_prologue(const double* __restrict__ theta, int64_t ld, int w,
   out[i] = c;
 }
 
-// Per-walker delay table b[k1] = exp(-2 pi i frac(n2 k1 r)), k1 < n1, for the
-// factorisation exp(-2 pi i k r) = exp(-2 pi i k2 r) exp(-2 pi i n2 k1 r) of
-// bin k = k2 + n2 k1.
+// Per-walker delay tables for the factorisation
+// exp(-2 pi i k r) = exp(-2 pi i k2 r) exp(-2 pi i n2 k1 r) of bin k = k2 + n2 k1:
+// tab[k] = exp(-2 pi i frac(mult k r)), k < count (mult = n2 over k1 < n1, and
+// mult = 1 over k2 < n2).
 template <typename C2>
-__global__ void k0_delay_table(const WalkerC* __restrict__ wc, int n1, int n2, C2* __restrict__ tab) {
+__global__ void k0_delay_table(const WalkerC* __restrict__ wc, int count, int mult, C2* __restrict__ tab) {
   const int k1 = blockIdx.x * blockDim.x + threadIdx.x;
   const int wk = blockIdx.y;
-  if (k1 >= n1) return;
+  if (k1 >= count) return;
   const double rh = wc[wk].r_hi, rl = wc[wk].r_lo;
-  double m = (double)n2 * (double)k1;
+  double m = (double)mult * (double)k1;
   dd p = dd_add_d(two_prod(m, rh), m * rl);
   dd f = dd_frac(p);
   double s, c;
@@ -181,7 +182,7 @@ __global__ void k0_delay_table(const WalkerC* __restrict__ wc, int n1, int n2, C
   C2 v;
   v.x = c;
   v.y = -s;
-  tab[(int64_t)wk * n1 + k1] = v;
+  tab[(int64_t)wk * count + k1] = v;
 }
 
 __global__ void k0_export(const WalkerC* __restrict__ wc, int w, double* __restrict__ out) {
@@ -202,13 +203,16 @@ void launch_prologue(const double* theta, int64_t ld, int w, int64_t n, double d
   k0_prologue<<<(w + 63) / 64, 64, 0, s>>>(theta, ld, w, n, dt, o.mode, o.n_xi, o.omega_m, o.h0, gl, out);
 }
 
-void launch_delay_table(const WalkerC* wc, int w, int n1, int n2, bool fp32, void* tab, cudaStream_t s) {
+void launch_delay_table(const WalkerC* wc, int w, int n1, int n2, bool fp32, void* tab, void* rtab, cudaStream_t s) {
   if (w <= 0) return;
-  dim3 g((n1 + 255) / 256, w);
-  if (fp32)
-    k0_delay_table<float2><<<g, 256, 0, s>>>(wc, n1, n2, (float2*)tab);
-  else
-    k0_delay_table<double2><<<g, 256, 0, s>>>(wc, n1, n2, (double2*)tab);
+  dim3 g1((n1 + 255) / 256, w), g2((n2 + 255) / 256, w);
+  if (fp32) {
+    k0_delay_table<float2><<<g1, 256, 0, s>>>(wc, n1, n2, (float2*)tab);
+    k0_delay_table<float2><<<g2, 256, 0, s>>>(wc, n2, 1, (float2*)rtab);
+  } else {
+    k0_delay_table<double2><<<g1, 256, 0, s>>>(wc, n1, n2, (double2*)tab);
+    k0_delay_table<double2><<<g2, 256, 0, s>>>(wc, n2, 1, (double2*)rtab);
+  }
 }
 
 void launch_prologue_export(const WalkerC* wc, int w, double* out, cudaStream_t s) {

@@ -252,6 +252,11 @@ __device__ __forceinline__ void load_geo(const WalkerC& c, Geo<T>& g) {
   g.amp_scale = T(c.amp_scale);
 }
 
+template <typename T>
+__device__ __forceinline__ T rcp_fast(T x) { return T(1) / x; }
+template <>
+__device__ __forceinline__ float rcp_fast<float>(float x) { return __fdividef(1.f, x); }
+
 // (x, y) -> (cos 2 atan2(y, x), sin 2 atan2(y, x)); (1, 0) when degenerate
 template <typename T>
 __device__ __forceinline__ void double_angle(T x, T y, T& c2, T& s2, bool degenerate) {
@@ -260,7 +265,7 @@ __device__ __forceinline__ void double_angle(T x, T y, T& c2, T& s2, bool degene
     c2 = T(1);
     s2 = T(0);
   } else {
-    const T inv = T(1) / r2;
+    const T inv = rcp_fast(r2);
     c2 = (x * x - y * y) * inv;
     s2 = T(2) * x * y * inv;
   }
@@ -287,6 +292,27 @@ template <>
 __device__ __forceinline__ void HarmStep<double>::next() {
   const double tc = 2.0 * c1 * cn - cp, ts = 2.0 * c1 * sn - sp;
   cp = cn; sp = sn; cn = tc; sn = ts;
+}
+
+// a_n, b_n, c_n of harmonic index n at fit time st
+template <typename T>
+__device__ __forceinline__ void amps_at(const T* __restrict__ bq, int n, T st, T& an, T& bn, T& rn);
+template <>
+__device__ __forceinline__ void amps_at<double>(const double* __restrict__ bq, int n, double st, double& an,
+                                                double& bn, double& rn) {
+  const double* b = bq + 9 * n;
+  an = (b[2] * st + b[1]) * st + b[0];
+  bn = (b[5] * st + b[4]) * st + b[3];
+  rn = (b[8] * st + b[7]) * st + b[6];
+}
+template <>
+__device__ __forceinline__ void amps_at<float>(const float* __restrict__ bq, int n, float st, float& an, float& bn,
+                                               float& rn) {
+  const float4* b = reinterpret_cast<const float4*>(bq + 12 * n);
+  const float4 x = b[0], y = b[1], z = b[2];
+  an = (x.z * st + x.y) * st + x.x;
+  bn = (y.y * st + y.x) * st + x.w;
+  rn = (z.x * st + y.w) * st + y.z;
 }
 
 // Channels at one sample.  cph/sph: cos/sin of the Doppler orbital phase;
@@ -344,10 +370,8 @@ __device__ __forceinline__ void channels(const Geo<T>& g, T cph, T sph, T c2gt, 
   hs.init(cph, sph);
   T Cs = T(0), Ss = T(0), Rs = T(0);
   for (int n = 0; n < n_max; ++n) {
-    const T* b = bq + 9 * n;
-    const T an = (b[2] * st + b[1]) * st + b[0];
-    const T bn = (b[5] * st + b[4]) * st + b[3];
-    const T rn = (b[8] * st + b[7]) * st + b[6];
+    T an, bn, rn;
+    amps_at<T>(bq, n, st, an, bn, rn);
     Cs += an * hs.cn;
     Ss += bn * hs.sn;
     Rs += rn * hs.cn;
@@ -358,6 +382,20 @@ __device__ __forceinline__ void channels(const Geo<T>& g, T cph, T sph, T c2gt, 
   hI = h3 * (fpI * hp + fxI * hx);
   hII = h3 * (fpII * hp + fxII * hx);
 }
+
+// Per-harmonic amplitude coefficients in shared memory: 9 values (a, b, c
+// quadratics) at stride AmpStride<T>; FP32 pads to 12 so one harmonic is
+// three 16-byte loads.
+template <typename T>
+struct AmpStride;
+template <>
+struct AmpStride<double> {
+  static constexpr int v = 9;
+};
+template <>
+struct AmpStride<float> {
+  static constexpr int v = 12;
+};
 
 // Bessel amplitude fit for the tile: nodes at tile-relative sample offsets
 // 0, L/2, L (L = 256, or the last valid offset when the orbit plunges inside
@@ -388,9 +426,10 @@ __device__ __forceinline__ void tile_harmonics(const IV* iv, int ni, int64_t j0,
   if (t < 3 * n_max) {
     const int n = t / 3, f = t % 3;
     const T f0 = bnode[(0 * 32 + n) * 3 + f], fh = bnode[(1 * 32 + n) * 3 + f], f1 = bnode[(2 * 32 + n) * 3 + f];
-    bq[9 * n + 3 * f + 0] = f0;
-    bq[9 * n + 3 * f + 1] = T(-3) * f0 + T(4) * fh - f1;
-    bq[9 * n + 3 * f + 2] = T(2) * f0 - T(4) * fh + T(2) * f1;
+    T* o = bq + AmpStride<T>::v * n + 3 * f;
+    o[0] = f0;
+    o[1] = T(-3) * f0 + T(4) * fh - f1;
+    o[2] = T(2) * f0 - T(4) * fh + T(2) * f1;
   }
 }
 
@@ -474,7 +513,7 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_mixed(const Knot* __restrict
                                                           const double* __restrict__ lisa, const IvM* __restrict__ ivs) {
   __shared__ IvM iv[kTile / 64];
   __shared__ float bnode[3 * 32 * 3];
-  __shared__ float bq[32 * 9];
+  __shared__ __align__(16) float bq[32 * 12];
   __shared__ float oq[2][3];
   __shared__ Geo<float> g;
   __shared__ int64_t jplunge;
@@ -511,10 +550,12 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_mixed(const Knot* __restrict
     const float so = (float)t * (1.f / kTile);
     const float cb = (oq[0][2] * so + oq[0][1]) * so + oq[0][0];
     const float sb = (oq[1][2] * so + oq[1][1]) * so + oq[1][0];
+    // hardware sin/cos of the reduced angles (|x| <= pi, absolute error ~5e-7)
+    constexpr float kTwoPiF = 6.283185307179586f;
     float sph, cph, s2g, c2g, sa, ca;
-    sincospif(2.f * fph, &sph, &cph);
-    sincospif(2.f * fgm, &s2g, &c2g);
-    sincospif(2.f * fal, &sa, &ca);
+    __sincosf(kTwoPiF * fph, &sph, &cph);
+    __sincosf(kTwoPiF * fgm, &s2g, &c2g);
+    __sincosf(kTwoPiF * fal, &sa, &ca);
     float hI, hII;
     channels<float>(g, cph, sph, c2g, s2g, ca, sa, cb, sb, A, (float)t / (float)span, bq, n_max, hI, hII);
     if (unit_scale) {

@@ -11,6 +11,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 import threading
+import weakref
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libemri.so")
@@ -158,9 +159,12 @@ class Context:
         _check(self.lib.emri_ctx_create(int(device), int(budget_bytes), C.byref(h)))
         self.h = h
         self.device = device
+        self._datasets = weakref.WeakSet()
 
     def close(self):
         if self.h:
+            for ds in list(self._datasets):   # datasets die with their context
+                ds.close()
             self.lib.emri_ctx_destroy(self.h)
             self.h = None
 
@@ -213,7 +217,9 @@ class Context:
         h = C.c_void_p()
         _check(self.lib.emri_dataset_create(self.h, C.byref(g), as_ptr(d), int(kind), as_ptr(p), float(fmin),
                                             float(fmax), C.byref(h)))
-        return Dataset(self, h, g)
+        ds = Dataset(self, h, g)
+        self._datasets.add(ds)
+        return ds
 
     # ------------------------------------------------------- batch calls
     def prologue(self, g: Grid, theta, o: Opts, out, stream=None):
@@ -285,9 +291,9 @@ class Dataset:
         return v.value
 
     def close(self):
-        if self.h:
+        if self.h and self.ctx.h:
             self.ctx.lib.emri_dataset_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:

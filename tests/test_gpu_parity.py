@@ -243,9 +243,42 @@ def test_c2_ensemble_step_sampled(ctx):
     assert np.all(np.abs(lnl[pick] - ref) <= tol), (lnl[pick], ref, tol)
     lnl_m = gpu_loglike(ctx, ds, th, wl.n_max, precision=1)[0]
     assert np.max(np.abs(lnl_m[pick] - ref)) <= 1e-2
+    # every walker: the two precisions each within 1e-2 of the exact value
+    assert np.max(np.abs(lnl_m - lnl)) <= 2e-2
     # waveform samples
     idx = np.unique(np.concatenate([[0, 1, wl.n - 1], np.random.default_rng(7).integers(0, wl.n, 2045)]))
     sI, sII, _ = O.waveform_sampled(th[pick], wl.n, wl.dt, idx, O.Opts(n_max=wl.n_max))
     z, _ = gpu_waveform(ctx, th[pick], wl.n, wl.dt, wl.n_max)
     for k in range(len(pick)):
         assert rel_l2(z[k, idx], sI[k] + 1j * sII[k]) <= 1e-9, k
+
+
+@pytest.mark.slow
+def test_poisoned_workspace_c2_subset(monkeypatch):
+    """With the workspace filled with NaN bytes before every call, no kernel
+    may read an intermediate value it did not write in the same call: 128
+    walkers of the 2^21 ensemble give finite lnL equal (bit for bit) to a
+    context without poisoning, in both precisions."""
+    E = emri_mod()
+    wl = I.config_c2()
+    th = wl.theta[::8].copy()
+    monkeypatch.setenv("EMRI_DEBUG_POISON", "1")
+    cp = E.Context(0)
+    monkeypatch.delenv("EMRI_DEBUG_POISON")
+    cq = E.Context(0)
+    try:
+        psd = I.psd_bc04(wl.n, wl.dt)
+        d, inj2, _, _ = O.injection_data(wl.injection, wl.n, wl.dt, psd, wl.noise_seed, O.Opts(n_max=wl.n_max),
+                                         snr=wl.snr)
+        th[:, I.I_Z] *= inj2[I.I_Z] / wl.injection[I.I_Z]
+        res = []
+        for c in (cp, cq):
+            ds = c.dataset(E.grid(wl.n, wl.dt), d, psd, 1e-4, 1.0 / (2 * wl.dt))
+            res.append([gpu_loglike(c, ds, th, wl.n_max, precision=p)[0] for p in (0, 1)])
+            ds.close()
+        for p in (0, 1):
+            assert np.all(np.isfinite(res[0][p]))
+            np.testing.assert_array_equal(res[0][p], res[1][p])
+    finally:
+        cp.close()
+        cq.close()

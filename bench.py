@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="serving measurement per precision (0: skip)")
+    ap.add_argument("--multi-chains", type=int, default=64, help="uneven-batching leg: chains (0: skip)")
     return ap.parse_args()
 
 
@@ -120,17 +121,24 @@ class ClockSampler:
 
 # ------------------------------------------------------------- workload
 def build_workload(ctx, args, seed_offset=0):
-    """Walkers, resident dataset and device buffers of the ensemble step.
+    """Walkers, resident dataset and device buffers of the ensemble step."""
+    from paper_2311_17174_gb300 import inputs as I
 
-    Data: the injection's unit-distance waveform and spectrum from the
-    library's own waveform and FFT calls, scaled to SNR 50 and added to the
-    seeded noise; the injection's redshift is set from the target distance
-    with the library's prologue (bisection)."""
+    wl = I.config_c2(walkers=args.walkers, n=1 << args.logn, n_max=args.n_max)
+    ds, theta, z_inj = injected_dataset(ctx, wl, wl.noise_seed + seed_offset)
+    return wl, ds, theta, z_inj
+
+
+def injected_dataset(ctx, wl, noise_seed):
+    """Resident dataset of one workload and its walkers at the injection's
+    distance.  Data: the injection's unit-distance waveform and spectrum from
+    the library's own waveform and FFT calls, scaled to the workload's SNR and
+    added to the seeded noise; the injection's redshift is set from the target
+    distance with the library's prologue (bisection)."""
     import torch
     from paper_2311_17174_gb300 import emri, inputs as I
 
-    n = 1 << args.logn
-    wl = I.config_c2(walkers=args.walkers, n=n, n_max=args.n_max)
+    n = wl.n
     g = emri.grid(n, wl.dt)
     psd = I.psd_bc04(n, wl.dt)
     dev = f"cuda:{torch.cuda.current_device()}"
@@ -141,6 +149,7 @@ def build_workload(ctx, args, seed_offset=0):
     ctx.fft_batch(z, n, 1, emri.FP64, -1)
     torch.cuda.synchronize()
     H = z[0].cpu().numpy()
+    del z
     probe = ctx.dataset(g, H, psd, wl.fmin, 1.0 / (2 * wl.dt))
     rho_u = float(np.sqrt(probe.dd()))
     probe.close()
@@ -155,11 +164,62 @@ def build_workload(ctx, args, seed_offset=0):
         return float(out[2, 0])
 
     z_inj = I.solve_distance(target, dgw)
-    data = H * (wl.snr / rho_u) + I.noise_spectrum(wl.noise_seed + seed_offset, psd, n, wl.dt)
+    data = H * (wl.snr / rho_u) + I.noise_spectrum(noise_seed, psd, n, wl.dt)
     ds = ctx.dataset(g, data, psd, wl.fmin, 1.0 / (2 * wl.dt))
     theta = wl.theta.copy()
     theta[:, I.I_Z] *= z_inj / wl.injection[I.I_Z]
-    return wl, ds, theta, z_inj
+    return ds, theta, z_inj
+
+
+def multi_bench(ctx, chains: int, steps: int, warmup: int, flush):
+    """Uneven batching: ``chains`` independent chains (32-512 walkers,
+    2^16-2^22 samples, n_max 5-30, own injection and noise each), mixed
+    precision, all chains in one emri_loglike_multi call (one captured CUDA
+    graph, one branch per chain), with schedules from the autotuner (one
+    tuning per length)."""
+    import torch
+    from paper_2311_17174_gb300 import emri, inputs as I
+
+    wls = I.config_c4(chains)
+    t_setup = time.perf_counter()
+    tuned = {}
+    for n in sorted({wl.n for wl in wls}):
+        tuned[n] = ctx.autotune(emri.grid(n, I.DT), 20, emri.MIXED)
+    items, dsets = [], []
+    for wl in wls:
+        ds, th, _ = injected_dataset(ctx, wl, wl.noise_seed)
+        dsets.append(ds)
+        w = th.shape[0]
+        theta = torch.tensor(th.T.copy(), dtype=torch.float64, device="cuda")
+        lnl = torch.zeros(w, dtype=torch.float64, device="cuda")
+        items.append((ds, theta, emri.opts(precision=emri.MIXED, n_max=wl.n_max), lnl, None, None, None))
+    t_setup = time.perf_counter() - t_setup
+    for _ in range(warmup):
+        ctx.loglike_multi(items)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.loglike_multi(items)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    walkers = sum(it[1].shape[1] for it in items)
+    finite = all(bool(torch.isfinite(it[3]).all()) for it in items)
+    for ds in dsets:
+        ds.close()
+    tot = float(sum(times))
+    return {"value": walkers * steps / (tot / 1e3), "unit": "lnL/s", "ms_per_step": tot / steps,
+            "chains": len(wls), "walkers": walkers,
+            "samples_x_walkers": int(sum(wl.n * wl.theta.shape[0] for wl in wls)),
+            "lengths": sorted({int(wl.n) for wl in wls}), "precision": "mixed",
+            "launch": "one CUDA graph per call, one branch per chain",
+            "autotuned": {str(k): v for k, v in tuned.items()}, "all_finite": finite,
+            "setup_s": t_setup}
 
 
 def time_steps(ctx, ds, theta_dev, o, lnl, steps, warmup, flush, barrier):
@@ -357,8 +417,11 @@ def main():
     # ---- mixed precision on the same walkers
     mixed = None
     if not args.no_mixed:
-        ctx.profile(True)
-        tm = time_steps(ctx, ds, theta_dev, omix, lnl, args.steps, 2, flush, barrier)
+        for _ in range(args.warmup):
+            ctx.loglike_batch(ds, theta_dev, omix, lnl)
+        torch.cuda.synchronize()
+        ctx.profile(True)   # timed steps only
+        tm = time_steps(ctx, ds, theta_dev, omix, lnl, args.steps, 0, flush, barrier)
         kt_mix = ctx.kernel_times()
         ctx.profile(False)
         mt = float(sum(tm))
@@ -401,6 +464,11 @@ def main():
         serving = [serve_bench(ctx, emri.MIXED, 20.0, args.serve_seconds, wl.n_max),
                    serve_bench(ctx, emri.FP64, 1.5, args.serve_seconds, wl.n_max)]
 
+    # ---- uneven batching: many chains in one captured launch (rank 0)
+    multi = None
+    if rank == 0 and args.multi_chains > 0:
+        multi = multi_bench(ctx, args.multi_chains, args.steps, 2, flush)
+
     # ---- roofline of the dominant kernel (FP64 step)
     per_step = {k: v[0] / args.steps for k, v in ktimes.items() if v[1]}
     dom = max(per_step, key=per_step.get)
@@ -441,6 +509,7 @@ def main():
             "e2e": {"value": W * world * args.steps / (e2e_tot / 1e3), "unit": "lnL/s",
                     "h2d_bytes_per_step": int(th_host.numel() * 8), "d2h_bytes_per_step": int(out_host.numel() * 8)},
             "serving": serving,
+            "multi_chain": multi,
             "gpu_launches": int(launches),
             "kernels_ms_per_step": {k: round(v, 3) for k, v in per_step.items()},
             "roofline": roof,

@@ -251,9 +251,16 @@ int emri_loglike_batch(emri_ctx* ctx, const emri_dataset* ds, const double* thet
 
 /* ------------------------------------------------------- uneven batching
  * Several independent chains, each with its own dataset (its own n), walker
- * count and options, evaluated in one multi-work launch sequence (the work
- * items of all chains share each kernel launch).  Pointers in emri_work are
- * device pointers owned by the caller; outputs as emri_loglike_batch. */
+ * count and options, evaluated by one launch of a captured CUDA graph with
+ * one branch per chain, so that the chains' kernels overlap on the device.
+ * The graph is captured on the first call with a given item list (pointers,
+ * counts and options) and replayed while the list stays the same; the values
+ * behind the pointers may change between calls.  Each chain has its own
+ * workspace (its time series bounded to ~512 MiB per wave).  Knot spacing and
+ * wave size follow the autotuner's plan for the chain's shape when one
+ * exists.  Pointers in emri_work are device pointers owned by the caller;
+ * outputs and determinism as emri_loglike_batch: each chain's results equal
+ * those of the chain evaluated alone. */
 typedef struct {
   const emri_dataset* ds;
   const double* theta_dev; /* [EMRI_NPARAM][w] */
@@ -266,6 +273,40 @@ typedef struct {
 } emri_work;
 
 int emri_loglike_multi(emri_ctx* ctx, const emri_work* items, int n_items, void* stream);
+
+/* ------------------------------------------------------- ensemble step
+ * One step of the affine-invariant ensemble sampler the paper uses for its
+ * posterior (Sec. 3, "Posterior sampling": emcee's stretch move, Goodman &
+ * Weare 2010, Commun. Appl. Math. Comput. Sci. 5, 65), on the device:
+ *   the W walkers form two halves S0 = [0, h), S1 = [h, W), h = W/2; S0 is
+ *   updated against the current S1, then S1 against the updated S0.  Walker
+ *   k of the active half takes the partner j = floor(u[0][k] * |other|) of
+ *   the other half and z = ((a - 1) u[1][k] + 1)^2 / a (density ~ z^-1/2 on
+ *   [1/a, a]); the proposal Y = X_j + z (X_k - X_j) in the free parameters
+ *   (others copied from X_k) is accepted iff
+ *   (d - 1) ln z + lnP(Y) - lnP(X_k) - ln u[2][k] > 0, d = number of free
+ *   parameters.  lnP = lnL of emri_loglike_batch plus a flat prior on the
+ *   box lo <= theta_p <= hi for the free p; a proposal outside the box, or
+ *   with status ST_BADPARAM / ST_NONFINITE, is rejected.
+ * theta_dev [EMRI_NPARAM][W] and lnp_dev [W] (device, caller-owned) hold the
+ * ensemble and its lnP on entry and are updated in place (lnp_dev of the
+ * starting ensemble comes from emri_loglike_batch).  u_dev [3][W] (device):
+ * uniforms in [0, 1) drawn by the caller, one triple per walker and step.
+ * accepted_dev [W] (nullable): 1 where the walker moved.  The proposal is
+ * formed with correctly rounded operations in the order written above.
+ * Errors: EMRI_EINVAL for W = 1, a <= 1, an empty free mask, bits above
+ * parameter 15, or an empty prior box; W = 0 is a no-op.  Asynchronous on
+ * `stream`; uses the context's workspace (sized for the larger half). */
+typedef struct {
+  double a;                 /* stretch scale, > 1 (2 is the usual choice)    */
+  uint32_t free_mask;       /* bit p set: parameter p (theta order) moves    */
+  double lo[EMRI_NPARAM];   /* flat prior box of the free parameters         */
+  double hi[EMRI_NPARAM];
+} emri_stretch_cfg;
+
+int emri_stretch_step(emri_ctx* ctx, const emri_dataset* ds, double* theta_dev, double* lnp_dev, int w,
+                      const emri_opts* opts, const emri_stretch_cfg* cfg, const double* u_dev,
+                      int32_t* accepted_dev, void* stream);
 
 /* ------------------------------------------------------------- serving
  * A continuous-batching request loop on the context's device: requests
@@ -306,6 +347,8 @@ int emri_serve_poll(emri_ctx* ctx, uint64_t ticket, double* lnl_host, uint32_t* 
  * split) for this grid, n_max and precision on the context's device and keep
  * the fastest as the context's plan for that shape; with cache_path
  * non-NULL the plans are also read from / appended to that JSON-lines file.
+ * A call whose (n, n_max, precision) has no plan uses the plan tuned for the
+ * same n and precision at the nearest n_max, if any.
  * choice_out (nullable, host) receives {knot_spacing, wave_walkers, fft_n1}. */
 int emri_autotune(emri_ctx* ctx, const emri_grid* grid, int n_max, int precision,
                   const char* cache_path, int64_t* choice_out);

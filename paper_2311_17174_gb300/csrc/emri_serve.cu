@@ -13,6 +13,7 @@
 #include <time.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -232,14 +233,34 @@ void serve_shutdown(emri_ctx* ctx) {
   ctx->server = nullptr;
 }
 
-int ctx_plan_ks(emri_ctx* ctx, int64_t n, const OptsN& o) {
+// The tuned plan for (n, n_max, precision); without one for this n_max, the
+// plan tuned for the same length and precision at the nearest n_max (the
+// choices depend on the length far more than on the harmonic count).
+static const Plan* find_plan(emri_ctx* ctx, int64_t n, const OptsN& o) {
   auto it = ctx->plans.find(std::make_tuple(n, o.n_max, o.precision));
-  return it == ctx->plans.end() ? 0 : it->second.ks;
+  if (it != ctx->plans.end()) return &it->second;
+  const Plan* best = nullptr;
+  int dist = 1 << 30;
+  for (auto lo = ctx->plans.lower_bound(std::make_tuple(n, 0, 0)); lo != ctx->plans.end(); ++lo) {
+    if (std::get<0>(lo->first) != n) break;
+    if (std::get<2>(lo->first) != o.precision) continue;
+    const int d = std::abs(std::get<1>(lo->first) - o.n_max);
+    if (d < dist) {
+      dist = d;
+      best = &lo->second;
+    }
+  }
+  return best;
+}
+
+int ctx_plan_ks(emri_ctx* ctx, int64_t n, const OptsN& o) {
+  const Plan* p = find_plan(ctx, n, o);
+  return p ? p->ks : 0;
 }
 
 int ctx_plan_wave(emri_ctx* ctx, int64_t n, const OptsN& o) {
-  auto it = ctx->plans.find(std::make_tuple(n, o.n_max, o.precision));
-  return it == ctx->plans.end() ? 0 : it->second.wave;
+  const Plan* p = find_plan(ctx, n, o);
+  return p ? p->wave : 0;
 }
 
 }  // namespace emri
@@ -371,6 +392,7 @@ extern "C" int emri_loglike_multi(emri_ctx* ctx, const emri_work* items, int n_i
   if (!ctx) return set_err(EMRI_EINVAL, "NULL context");
   if (n_items < 0 || (n_items > 0 && !items)) return set_err(EMRI_EINVAL, "bad item list");
   if (n_items == 0) return EMRI_OK;
+  std::lock_guard<std::mutex> lk(ctx->mu);
   std::vector<OptsN> on(n_items);
   std::vector<uint64_t> key;
   for (int i = 0; i < n_items; ++i) {
@@ -380,6 +402,10 @@ extern "C" int emri_loglike_multi(emri_ctx* ctx, const emri_work* items, int n_i
     if (it.w > 0 && (!it.theta_dev || !it.lnl_dev)) return set_err(EMRI_EINVAL, "item %d: NULL pointer", i);
     int rc = normalize_opts(&it.opts, it.ds->n, &on[i]);
     if (rc) return rc;
+    if (!it.opts.knot_spacing) {   // the autotuner's choice for this shape, if any
+      const int pk = ctx_plan_ks(ctx, it.ds->n, on[i]);
+      if (pk) on[i].ks = pk;
+    }
     key_push(key, it.ds);
     key_push(key, it.theta_dev);
     key.push_back((uint64_t)it.w);
@@ -395,7 +421,6 @@ extern "C" int emri_loglike_multi(emri_ctx* ctx, const emri_work* items, int n_i
     memcpy(&f[2], &on[i].h0, 8);
     key.insert(key.end(), f, f + 3);
   }
-  std::lock_guard<std::mutex> lk(ctx->mu);
   if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(EMRI_ECUDA, "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   MultiGraph* m = ctx->multi;
@@ -423,6 +448,8 @@ extern "C" int emri_loglike_multi(emri_ctx* ctx, const emri_work* items, int n_i
       const size_t cs = on[i].precision ? sizeof(float2) : sizeof(double2);
       const size_t per = (size_t)items[i].ds->n * cs;
       wave[i] = (int)std::max<size_t>(1, std::min<size_t>((size_t)items[i].w, ((size_t)512 << 20) / per));
+      const int pw = ctx_plan_wave(ctx, items[i].ds->n, on[i]);
+      if (pw > 0 && pw < wave[i]) wave[i] = pw;
       int rc = m->ws[i].reserve(ctx, loglike_layout(items[i].ds->plan, on[i], items[i].w, wave[i], nullptr, nullptr),
                                 m->cap);
       if (rc) {

@@ -191,6 +191,23 @@ __device__ __forceinline__ void smem_fft(C2* buf, int sign, const C2* __restrict
   }
 }
 
+// 16-byte asynchronous global -> shared copies (cp.async, L2 only) and their
+// group fences: the copies of a row are issued before the FFT and waited for
+// after it, so their latency overlaps the butterflies.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// bytes (a multiple of 16, both addresses 16-byte aligned) by all threads
+__device__ __forceinline__ void row_async(void* smem, const void* gmem, int bytes) {
+  for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x)
+    cp_async16((char*)smem + 16 * i, (const char*)gmem + 16 * (size_t)i);
+}
+
 // Copy nrow rows of rowlen contiguous complex values (global row stride gs)
 // to/from a row-major shared tile, with LPT independent 16-byte accesses per
 // thread in flight (rowlen * sizeof(C2) must be a multiple of 16).
@@ -227,8 +244,8 @@ struct FftCfg<double2> {
 };
 template <>
 struct FftCfg<float2> {
-  static constexpr int kCols = 16;   // 16 x 8 B = 128 B rows
-  static constexpr int kMaxB = 8;
+  static constexpr int kCols = 8;    // 8 x 8 B = 64 B rows; 64 KB tiles, two CTAs per SM
+  static constexpr int kMaxB = 4;
 };
 
 // ------------------------------------------------------------- pass 1
@@ -236,7 +253,7 @@ struct FftCfg<float2> {
 // row-major (rows of NB contiguous elements), transformed along the rows
 // index, and written back in place with the inter-pass twiddle.
 template <typename C2, int LG, int NB>
-__global__ void __launch_bounds__(kFftThreads) k3_pass1(C2* __restrict__ z, int64_t n, int n1, int sign, int shift22,
+__global__ void __launch_bounds__(kFftThreads, sizeof(C2) == 8 ? 2 : 1) k3_pass1(C2* __restrict__ z, int64_t n, int n1, int sign, int shift22,
                                                         const C2* __restrict__ ta, const C2* __restrict__ tb) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C2* buf = reinterpret_cast<C2*>(smraw);
@@ -311,33 +328,57 @@ struct AccF {
   }
 };
 
+// Shared memory of one pass-2 row: the row itself, then (when they fit in
+// 160 KB together) the row's data, delay factors and weights, prefetched.
+template <typename C2, typename WT, int LG>
+struct P2Smem {
+  static constexpr int N1 = 1 << LG;
+  static constexpr bool kPrefetch = (size_t)N1 * (3 * sizeof(C2) + sizeof(WT)) <= 160 * 1024;
+  static constexpr size_t bytes() {
+    return kPrefetch ? (size_t)N1 * (3 * sizeof(C2) + sizeof(WT)) : (size_t)N1 * sizeof(C2);
+  }
+};
+
 template <typename C2, typename WT, typename Acc, int LG>
-__global__ void __launch_bounds__(kPass2Threads, 2) k4_pass2_ip(const C2* __restrict__ y, int64_t n, int n2,
-                                                                const C2* __restrict__ ta, const WalkerC* __restrict__ wcs,
-                                                                const C2* __restrict__ dtab, const C2* __restrict__ rtab,
-                                                                const C2* __restrict__ dperm, const WT* __restrict__ wperm,
-                                                                double2* __restrict__ partial) {
+__global__ void __launch_bounds__(kPass2Threads, sizeof(C2) == 8 ? 4 : 2)
+    k4_pass2_ip(const C2* __restrict__ y, int64_t n, int n2, const C2* __restrict__ ta,
+                const WalkerC* __restrict__ wcs, const C2* __restrict__ dtab, const C2* __restrict__ rtab,
+                const C2* __restrict__ dperm, const WT* __restrict__ wperm, double2* __restrict__ partial) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  using SM = P2Smem<C2, WT, LG>;
   C2* buf = reinterpret_cast<C2*>(smraw);
+  C2* ds = buf + SM::N1;
+  C2* ts = ds + SM::N1;
+  WT* ws = reinterpret_cast<WT*>(ts + SM::N1);
   __shared__ Acc red[kPass2Threads / 32];
   using T = typename CT<C2>::T;
   constexpr int N1 = 1 << LG;
   const int k2 = blockIdx.x, wk = blockIdx.y;
   const C2* row = y + (int64_t)wk * n + (int64_t)N1 * k2;
-  tile_load<C2, 4>(buf, row, 0, N1, 1);
+  const int64_t base = (int64_t)k2 * N1;
+  const C2* tabw = dtab + (int64_t)wk * N1;
+  row_async(buf, row, N1 * (int)sizeof(C2));
+  cp_async_commit();
+  if (SM::kPrefetch) {
+    row_async(ds, dperm + base, N1 * (int)sizeof(C2));
+    row_async(ts, tabw, N1 * (int)sizeof(C2));
+    row_async(ws, wperm + base, N1 * (int)sizeof(WT));
+  }
+  cp_async_commit();
+  const C2 a = rtab[(int64_t)wk * n2 + k2];                 // exp(-2 pi i frac(k2 r))
+  const C2 cnv = CT<C2>::make((T)wcs[wk].cn_re, (T)wcs[wk].cn_im);
+  cp_async_wait<1>();
   __syncthreads();
   smem_fft<C2, LG, 1, kPass2Threads>(buf, -1, ta);
-  const C2 a = rtab[(int64_t)wk * n2 + k2];                 // exp(-2 pi i frac(k2 r))
-  const C2* tabw = dtab + (int64_t)wk * N1;
-  const C2 cnv = CT<C2>::make((T)wcs[wk].cn_re, (T)wcs[wk].cn_im);
-  const int64_t base = (int64_t)k2 * N1;
+  cp_async_wait<0>();
+  __syncthreads();
   Acc acc;
   acc.init();
   for (int k1 = threadIdx.x; k1 < N1; k1 += kPass2Threads) {
     const C2 H = buf[k1];
-    const T wv = (T)wperm[base + k1];
-    const C2 D = dperm[base + k1];
-    C2 f = cmul(a, tabw[k1]);
+    const T wv = SM::kPrefetch ? (T)ws[k1] : (T)wperm[base + k1];
+    const C2 D = SM::kPrefetch ? ds[k1] : dperm[base + k1];
+    C2 f = cmul(a, SM::kPrefetch ? ts[k1] : tabw[k1]);
     if (2 * k1 > N1 || (2 * k1 == N1 && k2 > 0)) f = cmul(f, cnv);   // signed index k - n
     const C2 Hd = cmul(H, f);
     acc.add(wv * (D.x * Hd.x + D.y * Hd.y), wv * (H.x * H.x + H.y * H.y));
@@ -516,13 +557,13 @@ void launch_fft_pass2_ip(const void* y, int w, const FftPlan& p, bool fp32, cons
   dim3 g(p.n2, w);
   const int lg = log2i(p.n1);
   if (fp32) {
-#define CALLI32(L) k4_pass2_ip<float2, float, AccF, L><<<g, kPass2Threads, p.n1 * sizeof(float2), s>>>( \
+#define CALLI32(L) k4_pass2_ip<float2, float, AccF, L><<<g, kPass2Threads, P2Smem<float2, float, L>::bytes(), s>>>( \
       (const float2*)y, p.n, p.n2, t.ta32, wc, (const float2*)delay_tab, (const float2*)row_tab,           \
       (const float2*)data_perm, (const float*)wt_perm, partial)
     EMRI_LG_SWITCH(lg, CALLI32)
 #undef CALLI32
   } else {
-#define CALLI64(L) k4_pass2_ip<double2, double, AccD, L><<<g, kPass2Threads, p.n1 * sizeof(double2), s>>>( \
+#define CALLI64(L) k4_pass2_ip<double2, double, AccD, L><<<g, kPass2Threads, P2Smem<double2, double, L>::bytes(), s>>>( \
       (const double2*)y, p.n, p.n2, t.ta64, wc, (const double2*)delay_tab, (const double2*)row_tab,            \
       (const double2*)data_perm, (const double*)wt_perm, partial)
     EMRI_LG_SWITCH(lg, CALLI64)

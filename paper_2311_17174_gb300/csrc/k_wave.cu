@@ -433,9 +433,10 @@ __device__ __forceinline__ void tile_harmonics(const IV* iv, int ni, int64_t j0,
   }
 }
 
-// span of the Bessel fit: the tile, or up to the last sample before a plunge
-__device__ __forceinline__ int tile_span(int64_t j0, int64_t jp) {
-  if (jp >= j0 + kTile) return kTile;
+// span of the Bessel fit: the L samples from j0, or up to the last sample
+// before a plunge
+__device__ __forceinline__ int tile_span(int64_t j0, int64_t jp, int L = kTile) {
+  if (jp >= j0 + L) return L;
   const int64_t l = jp - 1 - j0;
   return l < 1 ? 1 : (int)l;
 }
@@ -506,78 +507,95 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
   z[(int64_t)wk * n + j] = out;
 }
 
-__global__ void __launch_bounds__(kTile, 2) k2_wave_mixed(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
+// Mixed kernel: one CTA per segment of kSegM = 1024 samples (four tiles of
+// 256, one per pass of the sample loop), so the Bessel amplitude fit -- a
+// quadratic in time per harmonic, from three nodes -- is made once per 1024
+// samples; over that span its error is far below FP32 resolution.
+constexpr int kSegM = 1024;
+
+__global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
                                                           int64_t n, double dt, double t0, int ks, int n_max,
                                                           float2* __restrict__ z, int unit_scale,
                                                           const float* __restrict__ rk, const float* __restrict__ ifact,
                                                           const double* __restrict__ lisa, const IvM* __restrict__ ivs) {
-  __shared__ IvM iv[kTile / 64];
+  __shared__ IvM iv[kSegM / 64];
   __shared__ float bnode[3 * 32 * 3];
   __shared__ __align__(16) float bq[32 * 12];
-  __shared__ float oq[2][3];
+  __shared__ float oq[kSegM / kTile][2][3];
   __shared__ Geo<float> g;
   __shared__ int64_t jplunge;
   const int wk = blockIdx.y;
   const WalkerC& C = wcs[wk];
   const int64_t nk = n / ks;
-  const int64_t j0 = (int64_t)blockIdx.x * kTile;
+  const int64_t j0 = (int64_t)blockIdx.x * kSegM;
   const int64_t kfirst = j0 / ks;
-  const int ni = ks >= kTile ? 1 : kTile / ks;
+  const int ni = ks >= kSegM ? 1 : kSegM / ks;
   const int t = threadIdx.x;
   if (t < ni) iv[t] = ivs[(int64_t)wk * nk + kfirst + t];
-  if (t >= 128 && t < 134) oq[(t - 128) / 3][(t - 128) % 3] = (float)lisa[blockIdx.x * 6 + (t - 128)];
-  if (t == 160) {
+  constexpr int kTiles = kSegM / kTile;
+  if (t >= 128 && t < 128 + 6 * kTiles) {
+    const int q = t - 128;
+    oq[q / 6][(q % 6) / 3][q % 3] = (float)lisa[(blockIdx.x * kTiles + q / 6) * 6 + q % 6];
+  }
+  if (t == 224) {
     g = C.gf;
     jplunge = C.j_plunge;
   }
   __syncthreads();
-  const int span = tile_span(j0, jplunge);
+  const int span = tile_span(j0, jplunge, kSegM);
   tile_harmonics<float, IvM>(iv, ni, j0, kfirst, ks, n_max, span, bnode, bq, rk, ifact);
   __syncthreads();
-
-  const int64_t j = j0 + t;
-  float2 out = make_float2(0.f, 0.f);
-  if (j < jplunge) {
-    const int ki = ks >= kTile ? 0 : t / ks;
-    const int tau = (int)(j - (kfirst + ki) * ks);
-    const float s = (float)tau / (float)ks;
-    const IvM& v = iv[ki];
-    const float fph = phase_fx(v.ph_base, v.ph_inc, v.ph_c, tau, s);
-    float c2[2] = {2.f * v.gm_c[0], 2.f * v.gm_c[1]};
-    const float fgm = phase_fx(v.gm_base << 1, (long long)((unsigned long long)v.gm_inc << 1), c2, tau, s);
-    const float fal = phase_fx(v.al_base, v.al_inc, v.al_c, tau, s);
-    const float A = poly3<float>(v.am, s);
-    const float so = (float)t * (1.f / kTile);
-    const float cb = (oq[0][2] * so + oq[0][1]) * so + oq[0][0];
-    const float sb = (oq[1][2] * so + oq[1][1]) * so + oq[1][0];
-    // hardware sin/cos of the reduced angles (|x| <= pi, absolute error ~5e-7)
-    constexpr float kTwoPiF = 6.283185307179586f;
-    float sph, cph, s2g, c2g, sa, ca;
-    __sincosf(kTwoPiF * fph, &sph, &cph);
-    __sincosf(kTwoPiF * fgm, &s2g, &c2g);
-    __sincosf(kTwoPiF * fal, &sa, &ca);
-    float hI, hII;
-    channels<float>(g, cph, sph, c2g, s2g, ca, sa, cb, sb, A, (float)t / (float)span, bq, n_max, hI, hII);
-    if (unit_scale) {
-      hI *= g.amp_scale;
-      hII *= g.amp_scale;
+  const float inv_span = 1.f / (float)span;
+  const float inv_ks = 1.f / (float)ks;
+#pragma unroll 1
+  for (int tt = 0; tt < kTiles; ++tt) {
+    const int r = tt * kTile + t;   // offset in the segment
+    const int64_t j = j0 + r;
+    float2 out = make_float2(0.f, 0.f);
+    if (j < jplunge) {
+      const int ki = ks >= kSegM ? 0 : r / ks;
+      const int tau = r - ki * ks;
+      const float s = (float)tau * inv_ks;
+      const IvM& v = iv[ki];
+      const float fph = phase_fx(v.ph_base, v.ph_inc, v.ph_c, tau, s);
+      float c2[2] = {2.f * v.gm_c[0], 2.f * v.gm_c[1]};
+      const float fgm = phase_fx(v.gm_base << 1, (long long)((unsigned long long)v.gm_inc << 1), c2, tau, s);
+      const float fal = phase_fx(v.al_base, v.al_inc, v.al_c, tau, s);
+      const float A = poly3<float>(v.am, s);
+      const float so = (float)t * (1.f / kTile);
+      const float cb = (oq[tt][0][2] * so + oq[tt][0][1]) * so + oq[tt][0][0];
+      const float sb = (oq[tt][1][2] * so + oq[tt][1][1]) * so + oq[tt][1][0];
+      // hardware sin/cos of the reduced angles (|x| <= pi, absolute error ~5e-7)
+      constexpr float kTwoPiF = 6.283185307179586f;
+      float sph, cph, s2g, c2g, sa, ca;
+      __sincosf(kTwoPiF * fph, &sph, &cph);
+      __sincosf(kTwoPiF * fgm, &s2g, &c2g);
+      __sincosf(kTwoPiF * fal, &sa, &ca);
+      float hI, hII;
+      channels<float>(g, cph, sph, c2g, s2g, ca, sa, cb, sb, A, (float)r * inv_span, bq, n_max, hI, hII);
+      if (unit_scale) {
+        hI *= g.amp_scale;
+        hII *= g.amp_scale;
+      }
+      out = make_float2(hI, hII);
     }
-    out = make_float2(hI, hII);
+    z[(int64_t)wk * n + j] = out;
   }
-  z[(int64_t)wk * n + j] = out;
 }
 
 void launch_wave(const Knot* knots, const WalkerC* wc, int w, int64_t n, double dt, double t0,
                  const OptsN& o, void* z, bool unit_scale, const BesselTab& bt, const double* lisa, const void* ivs,
                  cudaStream_t s) {
   if (w <= 0) return;
-  dim3 grid((unsigned)(n / kTile), (unsigned)w);
-  if (o.precision == 0)
+  if (o.precision == 0) {
+    dim3 grid((unsigned)(n / kTile), (unsigned)w);
     k2_wave_f64<<<grid, kTile, 0, s>>>(knots, wc, n, dt, t0, o.ks, o.n_max, (double2*)z, unit_scale ? 1 : 0,
                                        bt.r64, bt.f64, lisa);
-  else
+  } else {
+    dim3 grid((unsigned)(n / kSegM), (unsigned)w);
     k2_wave_mixed<<<grid, kTile, 0, s>>>(knots, wc, n, dt, t0, o.ks, o.n_max, (float2*)z, unit_scale ? 1 : 0,
                                          bt.r32, bt.f32, lisa, (const IvM*)ivs);
+  }
 }
 
 }  // namespace emri

@@ -57,6 +57,10 @@ class ReqStats(C.Structure):
                 ("status", C.c_int32), ("slot", C.c_int32)]
 
 
+class StretchCfg(C.Structure):
+    _fields_ = [("a", C.c_double), ("free_mask", C.c_uint32), ("lo", C.c_double * 16), ("hi", C.c_double * 16)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -89,6 +93,8 @@ _SIGS = {
                                     C.POINTER(C.c_uint64)]),
     "emri_serve_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.POINTER(ReqStats),
                                   C.c_int64]),
+    "emri_stretch_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(Opts),
+                                    C.POINTER(StretchCfg), C.c_void_p, C.c_void_p, C.c_void_p]),
     "emri_autotune": (C.c_int, [C.c_void_p, C.POINTER(Grid), C.c_int, C.c_int, C.c_char_p,
                                 C.POINTER(C.c_int64)]),
 }
@@ -144,6 +150,16 @@ def fft_batch_noalloc(z, n: int, batch: int, precision: int, direction: int = -1
 def opts(precision=FP64, n_max=10, doppler=1, pn_terms=1, mode=FORWARD, knot_spacing=0, n_xi=2.0,
          omega_m=0.315, h0=67.4) -> Opts:
     return Opts(precision, n_max, doppler, pn_terms, mode, knot_spacing, n_xi, omega_m, h0)
+
+
+def stretch_cfg(free, lo, hi, a: float = 2.0) -> StretchCfg:
+    """Stretch-move configuration: ``free`` parameter indices (theta order),
+    prior box ``lo``/``hi`` (16 values each; only the free entries matter)."""
+    mask = 0
+    for p in free:
+        mask |= 1 << int(p)
+    return StretchCfg(float(a), mask, (C.c_double * 16)(*[float(x) for x in lo]),
+                      (C.c_double * 16)(*[float(x) for x in hi]))
 
 
 def grid(n: int, dt: float, t0: float = 0.0) -> Grid:
@@ -246,6 +262,14 @@ class Context:
             arr[i] = Work(ds.h.value, _ptr(theta), int(theta.shape[1]), o, _ptr(lnl), _ptr(dh), _ptr(hh),
                           _ptr(st))
         _check(self.lib.emri_loglike_multi(self.h, arr, len(items), _stream(stream)))
+
+    def stretch_step(self, ds: "Dataset", theta, lnp, o: Opts, cfg: StretchCfg, u, accepted=None, stream=None):
+        """emri_stretch_step: one affine-invariant ensemble step in place on
+        theta [16][W] and lnp [W] (device tensors), driven by the uniforms
+        u [3][W] (device)."""
+        w = int(theta.shape[1])
+        _check(self.lib.emri_stretch_step(self.h, ds.h, _ptr(theta), _ptr(lnp), w, C.byref(o), C.byref(cfg),
+                                          _ptr(u), _ptr(accepted), _stream(stream)))
 
     # ------------------------------------------------------------ serving
     def serve_start(self, slots: int = 4, queue_capacity: int = 1024, budget_bytes: int = 0):

@@ -35,7 +35,7 @@ def test_header_declares_the_path_calls():
     names = declared_functions()
     for must in ("emri_ak_waveform", "emri_fft_batch", "emri_loglike_batch", "emri_serve_submit",
                  "emri_serve_poll", "emri_dataset_create", "emri_ctx_create", "emri_autotune",
-                 "emri_loglike_multi", "emri_prologue"):
+                 "emri_loglike_multi", "emri_prologue", "emri_stretch_step"):
         assert must in names
 
 
@@ -85,6 +85,6 @@ def test_product_and_oracle_are_separate():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", text, flags=re.M), f
                 assert "liboracle" not in text and "emri_oracle" not in text, f
-    otext = open(os.path.join(ROOT, "oracle", "emri_oracle.c")).read() + \
-        open(os.path.join(ROOT, "oracle", "__init__.py")).read()
+    otext = "".join(open(os.path.join(ROOT, "oracle", f)).read()
+                    for f in sorted(os.listdir(os.path.join(ROOT, "oracle"))) if f.endswith((".c", ".py")))
     assert "paper_2311_17174_gb300.emri" not in otext and "libemri" not in otext and "emri_common" not in otext

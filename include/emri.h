@@ -49,9 +49,9 @@ enum emri_param {
   EMRI_P_SPIN = 2,   /* S/M^2 in [0, 1]                                  */
   EMRI_P_E0 = 3,     /* eccentricity at t0 (at the LSO in backward mode) */
   EMRI_P_NU0 = 4,    /* orbital frequency nu at t0 [Hz] (forward mode)   */
-  EMRI_P_PHI0 = 5,   /* orbital phase Phi at t0                          */
-  EMRI_P_GAMMA0 = 6, /* periastron angle gamma~ at t0                    */
-  EMRI_P_ALPHA0 = 7, /* Lense-Thirring angle alpha at t0                 */
+  EMRI_P_PHI0 = 5,   /* orbital phase Phi at t0 (backward: at the LSO)   */
+  EMRI_P_GAMMA0 = 6, /* periastron angle gamma~ at t0 (backward: LSO)    */
+  EMRI_P_ALPHA0 = 7, /* Lense-Thirring angle alpha at t0 (backward: LSO) */
   EMRI_P_THETA_S = 8, EMRI_P_PHI_S = 9,   /* source direction (ecliptic) */
   EMRI_P_THETA_K = 10, EMRI_P_PHI_K = 11, /* spin direction              */
   EMRI_P_LAMBDA = 12,/* angle between L and S                            */
@@ -79,8 +79,12 @@ enum emri_precision {
 
 enum emri_mode {
   EMRI_FORWARD = 0,          /* integrate forward from (nu0, e0) at t0     */
-  EMRI_BACKWARD_FROM_LSO = 1 /* last sample at the LSO with e = e0, integrate
-                                backwards (paper Sec. 3)                   */
+  EMRI_BACKWARD_FROM_LSO = 1 /* initial conditions at the LSO (paper
+                                Sec. 3): the last sample t0 + (n-1) dt has
+                                e = e0 and nu = nu_LSO(e0), and Phi0,
+                                gamma~0, alpha0 are the angles there; nu0 is
+                                ignored; the orbit is integrated backwards,
+                                so no plunge occurs in the window          */
 };
 
 /* per-walker status bits */

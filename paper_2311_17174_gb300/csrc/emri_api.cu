@@ -73,8 +73,6 @@ int normalize_opts(const emri_opts* in, int64_t n, OptsN* o) {
   if (a.n_max < 1 || a.n_max > 32) return set_err(EMRI_EINVAL, "opts.n_max must be in [1, 32]");
   if (a.mode != EMRI_FORWARD && a.mode != EMRI_BACKWARD_FROM_LSO)
     return set_err(EMRI_EINVAL, "opts.mode must be EMRI_FORWARD or EMRI_BACKWARD_FROM_LSO");
-  if (a.mode == EMRI_BACKWARD_FROM_LSO)
-    return set_err(EMRI_EINVAL, "backward-from-LSO integration is not available in this build");
   o->precision = a.precision;
   o->n_max = a.n_max;
   o->doppler = a.doppler ? 1 : 0;

@@ -393,10 +393,183 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi(WalkerC* __res
   }
 }
 
+// Backward mode (paper Sec. 3: initial conditions at the LSO, integrated back
+// in time): the LSO state (v_LSO(e0), e0, Phi0, gamma~0, alpha0) sits at the
+// last sample t0 + (n-1) dt.  One RK4 step of +dt carries it to the last knot
+// (sample n), from where the segments are integrated with negative step,
+// knots written from the end; the AK system is regular at the LSO, so the
+// short step past it is harmless.  A segment whose iteration does not settle
+// is redone serially (knot-step RK4 backwards).  No plunge check applies; an
+// orbit that becomes non-finite gives a zero waveform and ST_NONFINITE.
+__device__ bool rk4_span_back(const OrbSrc& s, const WalkerC& c, OrbState& y, int64_t k0, int64_t k1, int ks,
+                              double dt, double t0, int doppler, Knot* kn) {
+  const double h = -(double)ks * dt;
+  double r[5];
+  ak_rhs_v(s, y.v_hi, y.e_hi, r[0], r[1], r[2], r[3], r[4]);
+  for (int64_t k = k0; k > k1; --k) {
+    rk4_step(s, y, h, r);
+    if (!state_finite(y)) return false;
+    ak_rhs_v(s, y.v_hi, y.e_hi, r[0], r[1], r[2], r[3], r[4]);
+    write_knot(kn + k - 1, y, r, c, t0 + (double)((k - 1) * ks) * dt, doppler);
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi_back(WalkerC* __restrict__ wcs, int w, int64_t n,
+                                                                        double dt, double t0, int ks, int pn,
+                                                                        int doppler, const double* __restrict__ qn_g,
+                                                                        const double* __restrict__ qk_g,
+                                                                        Knot* __restrict__ knots) {
+  __shared__ double qn[32 * 32];
+  __shared__ double qk[129 * 32];
+  __shared__ double fs[kOrbitWarps][5][32];
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  const int seg = (int)(n < kSeg ? n : kSeg);
+  const int K = seg / ks;
+  const int qstride = 128 / K;
+  for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) qn[i] = qn_g[i];
+  for (int q = 0; q <= K; ++q)
+    for (int i = threadIdx.x; i < 32; i += blockDim.x) qk[q * 32 + i] = qk_g[(q * qstride) * 32 + i];
+  __syncthreads();
+  const int wk = blockIdx.x * kOrbitWarps + wq;
+  if (wk >= w) return;
+  const WalkerC c = wcs[wk];
+  const int64_t nk = n / ks;
+  Knot* kn = knots + (int64_t)wk * (nk + 1);
+  if (c.status & ST_BADPARAM) {
+    Knot zk = {};
+    for (int64_t k = lane; k <= nk; k += 32) kn[k] = zk;
+    if (lane == 0) wcs[wk].j_plunge = 0;
+    return;
+  }
+  const OrbSrc s{c.kv, c.ke, c.inv2pim, c.spin, c.coslam, pn};
+  OrbState y{c.v0_hi, c.v0_lo, c.e0, 0.0, c.phi0c, 0.0, c.gam0c, 0.0, c.alp0c, 0.0};
+  {
+    double r[5];
+    ak_rhs_v(s, y.v_hi, y.e_hi, r[0], r[1], r[2], r[3], r[4]);
+    rk4_step(s, y, dt, r);
+  }
+  const double H = -(double)seg * dt;
+  const double taui = 0.5 * (1.0 - cospi((double)lane / 31.0));
+  double* f = &fs[wq][0][0];
+  bool fail = !state_finite(y);
+  const int64_t nseg = n / seg;
+  for (int64_t g = nseg - 1; g >= 0 && !fail; --g) {
+    const OrbState ys = y;
+    const int64_t kend = (g + 1) * (int64_t)K;   // knot at the segment's start (its latest time)
+    double f0v, f0e;
+    ak_rate_ve(s, y.v_hi, y.e_hi, f0v, f0e);
+    double v = y.v_hi + (y.v_lo + H * taui * f0v);
+    double e = y.e_hi + (y.e_lo + H * taui * f0e);
+    bool convw = false;
+    for (int it = 0; it < 30; ++it) {
+      double fv, fe;
+      ak_rate_ve(s, v, e, fv, fe);
+      __syncwarp();
+      f[0 * 32 + lane] = fv;
+      f[1 * 32 + lane] = fe;
+      __syncwarp();
+      double sv = 0.0, se = 0.0;
+#pragma unroll 8
+      for (int j = 0; j < 32; ++j) {
+        const double q = qn[j * 32 + lane];
+        sv = fma(q, f[0 * 32 + j], sv);
+        se = fma(q, f[1 * 32 + j], se);
+      }
+      const double vn = y.v_hi + (y.v_lo + H * sv);
+      const double en = y.e_hi + (y.e_lo + H * se);
+      const bool conv = fabs(vn - v) <= 4e-16 * fabs(y.v_hi) && fabs(en - e) <= 2e-16;
+      v = vn;
+      e = en;
+      const bool ok = isfinite(v) && isfinite(e);
+      if (__all_sync(0xffffffffu, conv || !ok)) {
+        convw = __all_sync(0xffffffffu, conv && ok);
+        break;
+      }
+    }
+    bool serial = !convw;
+    if (!serial) {
+      double r[5];
+      ak_rhs_v(s, v, e, r[0], r[1], r[2], r[3], r[4]);
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < 5; ++q) f[q * 32 + lane] = r[q];
+      __syncwarp();
+      bool anybad = false;
+      for (int q0 = 0; q0 <= K; q0 += 32) {
+        const int q = q0 + lane;
+        bool bad = false;
+        OrbState yk = y;
+        if (q <= K) {
+          double sm[5] = {0, 0, 0, 0, 0};
+#pragma unroll 4
+          for (int j = 0; j < 32; ++j) {
+            const double wq_ = qk[q * 32 + j];
+#pragma unroll
+            for (int cc = 0; cc < 5; ++cc) sm[cc] = fma(wq_, f[cc * 32 + j], sm[cc]);
+          }
+          comp_add_small(yk.v_hi, yk.v_lo, H * sm[0]);
+          comp_add(yk.e_hi, yk.e_lo, H * sm[1]);
+          comp_add(yk.p_hi, yk.p_lo, H * sm[2]);
+          comp_add(yk.g_hi, yk.g_lo, H * sm[3]);
+          comp_add(yk.a_hi, yk.a_lo, H * sm[4]);
+          bad = q > 0 && !state_finite(yk);
+          if (q < K && !bad) {
+            double rk[5];
+            ak_rhs_v(s, yk.v_hi, yk.e_hi, rk[0], rk[1], rk[2], rk[3], rk[4]);
+            write_knot(kn + kend - q, yk, rk, c, t0 + (double)((kend - q) * ks) * dt, doppler);
+          }
+        }
+        anybad |= __any_sync(0xffffffffu, bad);
+        const int src = K - q0;
+        if (src >= 0 && src < 32) {
+          y.v_hi = __shfl_sync(0xffffffffu, yk.v_hi, src); y.v_lo = __shfl_sync(0xffffffffu, yk.v_lo, src);
+          y.e_hi = __shfl_sync(0xffffffffu, yk.e_hi, src); y.e_lo = __shfl_sync(0xffffffffu, yk.e_lo, src);
+          y.p_hi = __shfl_sync(0xffffffffu, yk.p_hi, src); y.p_lo = __shfl_sync(0xffffffffu, yk.p_lo, src);
+          y.g_hi = __shfl_sync(0xffffffffu, yk.g_hi, src); y.g_lo = __shfl_sync(0xffffffffu, yk.g_lo, src);
+          y.a_hi = __shfl_sync(0xffffffffu, yk.a_hi, src); y.a_lo = __shfl_sync(0xffffffffu, yk.a_lo, src);
+        }
+      }
+      serial = anybad;
+    }
+    if (serial) {
+      __syncwarp();
+      int valid = 1;
+      if (lane == 0) {
+        OrbState yy = ys;
+        double r0[5];
+        ak_rhs_v(s, yy.v_hi, yy.e_hi, r0[0], r0[1], r0[2], r0[3], r0[4]);
+        write_knot(kn + kend, yy, r0, c, t0 + (double)(kend * ks) * dt, doppler);
+        valid = rk4_span_back(s, c, yy, kend, kend - K, ks, dt, t0, doppler, kn) ? 1 : 0;
+        y = yy;
+      }
+      valid = __shfl_sync(0xffffffffu, valid, 0);
+      y.v_hi = __shfl_sync(0xffffffffu, y.v_hi, 0); y.v_lo = __shfl_sync(0xffffffffu, y.v_lo, 0);
+      y.e_hi = __shfl_sync(0xffffffffu, y.e_hi, 0); y.e_lo = __shfl_sync(0xffffffffu, y.e_lo, 0);
+      y.p_hi = __shfl_sync(0xffffffffu, y.p_hi, 0); y.p_lo = __shfl_sync(0xffffffffu, y.p_lo, 0);
+      y.g_hi = __shfl_sync(0xffffffffu, y.g_hi, 0); y.g_lo = __shfl_sync(0xffffffffu, y.g_lo, 0);
+      y.a_hi = __shfl_sync(0xffffffffu, y.a_hi, 0); y.a_lo = __shfl_sync(0xffffffffu, y.a_lo, 0);
+      fail = !valid;
+    }
+  }
+  if (!fail && lane == 0) {
+    double r[5];
+    ak_rhs_v(s, y.v_hi, y.e_hi, r[0], r[1], r[2], r[3], r[4]);
+    write_knot(kn, y, r, c, t0, doppler);   // knot 0 (sample 0)
+  }
+  if (lane == 0) {
+    wcs[wk].j_plunge = fail ? 0 : n;
+    wcs[wk].status = c.status | (fail ? (uint32_t)ST_NONFINITE : 0u);
+  }
+}
+
 void launch_orbit(WalkerC* wc, int w, int64_t n, double dt, double t0, const OptsN& o, Knot* knots,
                   const double* mcpi_tab, cudaStream_t s) {
   if (w <= 0) return;
-  if (mcpi_tab) {
+  if (o.mode == 1) {   // backward from the LSO (the integration tables are always present)
+    k1_orbit_mcpi_back<<<(w + kOrbitWarps - 1) / kOrbitWarps, 32 * kOrbitWarps, 0, s>>>(
+        wc, w, n, dt, t0, o.ks, o.pn_terms, o.doppler, mcpi_tab, mcpi_tab + 32 * 32, knots);
+  } else if (mcpi_tab) {
     k1_orbit_mcpi<<<(w + kOrbitWarps - 1) / kOrbitWarps, 32 * kOrbitWarps, 0, s>>>(
         wc, w, n, dt, t0, o.ks, o.pn_terms, o.doppler, mcpi_tab, mcpi_tab + 32 * 32, knots);
   } else {

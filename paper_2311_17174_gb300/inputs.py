@@ -189,6 +189,28 @@ def config_c3(walkers: int = 4096, n: int = 1 << 20, snr: float = 50.0) -> Workl
                     extra={"oracle_idx": idx})
 
 
+def config_paper(walkers: int = 8, n: int = 1 << 21, n_max: int = 10, seed: int = 6,
+                 rel: float = 1e-4) -> Workload:
+    """The paper's example run (Sec. 3 and its corner-plot example): initial
+    conditions at the LSO with e_LSO = 0.3 and Phi, gamma~, alpha = 0 there,
+    theta_S = pi/4, phi_S = 0, theta_K = pi/8, phi_K = 0, lambda = pi/6, fixed;
+    the four free parameters M = 1e6, mu = 10, S/M^2 = 0.1, Xi_0 = 1 scattered
+    by N(0, rel) relative; GW speed as in GR; a one-year window (n dt);
+    noise-free data (the paper's choice).  The source sits at 1 Gpc: z is a
+    placeholder that the caller sets from ``extra['d_gpc']`` with its own
+    distance function."""
+    inj = np.zeros(P)
+    inj[[I_M, I_MU, I_SPIN, I_E0, I_NU0]] = [1e6, 10.0, 0.1, 0.3, 0.0]
+    inj[[I_THS, I_PHS, I_THK, I_PHK, I_LAM]] = [np.pi / 4, 0.0, np.pi / 8, 0.0, np.pi / 6]
+    inj[[I_Z, I_XI0, I_ALPT]] = [0.2, 1.0, 0.0]
+    g = _rng(seed)
+    th = np.repeat(inj[None, :], walkers, axis=0)
+    for p_ in (I_M, I_MU, I_SPIN, I_XI0):
+        th[:, p_] *= 1.0 + rel * g.standard_normal(walkers)
+    return Workload(f"paper-lso-{walkers}w-2^{int(np.log2(n))}-n{n_max}", th, n, DT, n_max, inj, -1, None,
+                    extra={"d_gpc": 1.0, "free": (I_M, I_MU, I_SPIN, I_XI0), "mode": "backward_from_lso"})
+
+
 def config_c4(chains: int = 64):
     """Uneven batching: ``chains`` independent chains, W_c ~ U{32..512},
     N_c = 2^U{16..22}, n_max_c ~ U{5..30}; own injection, noise and PSD each."""

@@ -225,6 +225,43 @@ def test_loglike_zero_walkers_and_gr_limit(ctx):
     assert abs(lnl[0] - 0.5 * ds.dd()) <= 1e-9 * ds.dd()
 
 
+def test_backward_from_lso_paper_workload(ctx):
+    """Backward-from-LSO integration (the paper's own set-up: e_LSO = 0.3,
+    fixed geometry, M, mu, S/M^2, Xi_0 free), FP64 and mixed, waveform and
+    lnL against the oracle in backward mode; noise-free data at 1 Gpc."""
+    wl = I.config_paper(walkers=8, n=1 << 16, n_max=10)
+    n, dt, nm = wl.n, wl.dt, wl.n_max
+    ob = O.Opts(n_max=nm, backward=1)
+    # redshift of 1 Gpc from the oracle's distance (bisection)
+    mpc = 3.0856775814913673e24
+    z = I.solve_distance(1e3 * mpc, lambda zz: O.dl_cm(zz))
+    th = wl.theta.copy()
+    th[:, I.I_Z] = z
+    inj = wl.injection.copy()
+    inj[I.I_Z] = z
+    hI, hII, st_o = O.waveform(th, n, dt, ob)
+    z64, st = gpu_waveform(ctx, th, n, dt, nm, mode=1)
+    np.testing.assert_array_equal(st, st_o)
+    assert np.all(st == 0)
+    for k in range(len(th)):
+        assert rel_l2(z64[k], hI[k] + 1j * hII[k]) <= 1e-9, k
+    zm, _ = gpu_waveform(ctx, th, n, dt, nm, precision=1, mode=1)
+    assert max(rel_l2(zm[k], hI[k] + 1j * hII[k]) for k in range(len(th))) <= 1e-4
+    # the signal ends at the LSO: the last sample's orbit is at nu_LSO(e_LSO)
+    orb = O.orbit(th[0], n, dt, ob)
+    assert orb["nu"][-1] == pytest.approx(O.nu_lso(th[0, I.I_M], 0.3), rel=1e-15)
+    psd = I.psd_bc04(n, dt)
+    d, _, w, _ = O.injection_data(inj, n, dt, psd, None, ob)
+    ds = ctx.dataset(emri_mod().grid(n, dt), d, psd, 1e-4, 1.0 / (2 * dt))
+    ref, dh_o, hh_o, _ = O.loglike(th, n, dt, d, w, ob)
+    lnl, _, _, _ = gpu_loglike(ctx, ds, th, nm, mode=1)
+    dgw = np.array([O.prologue(t, n, dt)[2] for t in th])
+    assert np.all(np.abs(lnl - ref) <= lnl_tol(dh_o / dgw, hh_o / dgw ** 2))
+    lnl_m, _, _, _ = gpu_loglike(ctx, ds, th, nm, precision=1, mode=1)
+    assert np.max(np.abs(lnl_m - ref)) <= 1e-2
+    ds.close()
+
+
 @pytest.mark.slow
 def test_c2_ensemble_step_sampled(ctx):
     """1024 walkers, 2^21 samples, n <= 20, SNR 50, FP64 -- the benchmark's

@@ -190,6 +190,45 @@ def test_integrator_step_halving(oracle_mod):
     assert abs(a["gamma"][-1] - b["gamma"][-1]) < 1e-9
 
 
+def test_backward_newtonian_chirp_closed_form(oracle_mod):
+    # backward mode (paper Sec. 3: initial conditions at the LSO, integrated
+    # back in time): pn_terms = 0, e = 0, the last sample sits at nu_LSO and
+    # nu(t) = nu_L (1 + (T - t)/tau_L)^(-3/8), tau_L = (5/256) M (M/mu) (2 pi M nu_L)^(-8/3)
+    m, mu = 1e6, 10.0
+    th = theta_base(M=m, mu=mu, e0=0.0, nu0=0.0, spin=0.0, phi0=0.25)
+    n, dt = 20000, 15.0
+    orb = O.orbit(th, n, dt, O.Opts(pn_terms=0, backward=1))
+    nu_l = O.nu_lso(m, 0.0)
+    assert nu_l == pytest.approx(1 / (6 ** 1.5 * 2 * np.pi * m * TSUN), rel=1e-15)
+    m_s, mu_s = m * TSUN, mu * TSUN
+    tau = 5.0 / 256.0 * m_s * (m_s / mu_s) * (2 * np.pi * m_s * nu_l) ** (-8.0 / 3.0)
+    back = (n - 1 - np.arange(n)) * dt            # time before the LSO
+    nu_ref = nu_l * (1 + back / tau) ** (-3.0 / 8.0)
+    phi_ref = 0.25 - 2 * np.pi * nu_l * tau * 8.0 / 5.0 * ((1 + back / tau) ** (5.0 / 8.0) - 1)
+    assert orb["nu"][-1] == nu_l and orb["phi"][-1] == 0.25
+    assert np.max(np.abs(orb["nu"] / nu_ref - 1)) < 1e-13
+    assert np.max(np.abs(orb["phi"] - phi_ref)) < 1e-8
+    assert orb["n_valid"] == n
+
+
+def test_backward_then_forward_returns_to_the_lso(oracle_mod):
+    # full AK equations: integrating forward from the backward orbit's first
+    # sample reproduces the LSO state at the last sample (time reversibility)
+    th = theta_base(M=8e5, mu=15.0, e0=0.3, spin=0.6, lam=0.9, phi0=0.1, gam0=0.2, alp0=0.3)
+    n, dt = 1 << 14, 15.0
+    b = O.orbit(th, n, dt, O.Opts(backward=1))
+    f_th = th.copy()
+    f_th[[I.I_PHI0, I.I_NU0, I.I_E0, I.I_GAM0, I.I_ALP0]] = [b["phi"][0], b["nu"][0], b["e"][0], b["gamma"][0],
+                                                             b["alpha"][0]]
+    # forward mode stops at the LSO: shorten by one sample so the check stays inside it
+    f = O.orbit(f_th, n - 1, dt)
+    for k in ("phi", "gamma", "alpha"):
+        assert abs(f[k][-1] - b[k][-2]) < 1e-8, k
+    assert abs(f["nu"][-1] / b["nu"][-2] - 1) < 1e-13
+    assert abs(f["e"][-1] - b["e"][-2]) < 1e-14
+    assert b["e"][0] > 0.3 and b["nu"][0] < b["nu"][-1]
+
+
 def test_plunge_detected(oracle_mod):
     # start just below the LSO: the orbit plunges and the waveform is zero after it
     m, e0 = 1e6, 0.2

@@ -304,6 +304,14 @@ def serve_bench(ctx, precision: int, rate: float, duration: float, n_max: int, s
             "lnl_per_s": walkers[0] / elapsed, "seconds": elapsed, "slots": 4}
 
 
+# DRAM bytes per sample of k2_wave_f64 from one ncu capture of the kernel
+# (64 walkers x 2^20 samples, n_max 20: 72.16 MB read + 1013.64 MB written;
+# profiles/ncu_k2_wave_f64_64w_2p20.md), scaled to a launch by the samples it
+# processes (the kernel's traffic is its 16-byte output per sample plus the
+# per-tile orbit records, both proportional to walkers x samples).
+K2_F64_DRAM_BYTES_PER_SAMPLE = (72.156e6 + 1013.643e6) / (64 * 2 ** 20)
+
+
 def flop_model(n_max: int) -> float:
     """Algorithmic FP64 flops per sample of the factored harmonic sum and
     response (see the design notes): 24 per harmonic (rotation 6, three
@@ -479,8 +487,9 @@ def main():
         walkers_per_launch = W * args.steps / launches_wave
         flops = flop_model(wl.n_max) * wl.n * walkers_per_launch
         achieved = flops / (avg_ms / 1e3) / 1e12
+        traffic = K2_F64_DRAM_BYTES_PER_SAMPLE * wl.n * walkers_per_launch if wl.n_max == 20 else None
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k2_wave_f64",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": "k2_wave_f64",
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (FP64 vector unit)",
                 "flops_per_launch": flops, "avg_launch_ms": avg_ms}
     else:

@@ -95,6 +95,8 @@ def lib():
                 "orc_delay_apply": (None, [d, d, i64, C.c_double, C.c_double, d, d]),
                 "orc_loglike": (None, [d, i32, po, i64, C.c_double, C.c_double, d, d, d,
                                        d, d, d, u32, i32]),
+                "orc_loglike_fd": (None, [d, i32, po, i64, C.c_double, C.c_double, d, d, d, i32, i32,
+                                          C.c_double, d, d, d, d, u32, i32]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -336,6 +338,25 @@ def loglike(theta, n: int, dt: float, data_fd, w, opts: Opts | None = None, t0: 
     lib().orc_loglike(_dp(t), nw, C.byref(o), int(n), float(dt), float(t0), _dp(dr), _dp(di),
                       _dp(ww), _dp(lnl), _dp(dh), _dp(hh),
                       st.ctypes.data_as(C.POINTER(C.c_uint32)), _nthreads(nthreads))
+    return lnl, dh, hh, st
+
+
+def loglike_fd(theta, n: int, dt: float, data_fd, w, qm: int, qt: int, fstar: float, coef,
+               opts: Opts | None = None, t0: float = 0.0, nthreads=None):
+    """``loglike`` with frequency-dependent propagation: coef [W][qm+qt] holds
+    a_1..a_qm (alpha_M) and b_1..b_qt (extra alpha_T terms) per walker, in
+    powers of f/fstar."""
+    o = (opts or Opts()).c()
+    t = _theta_aos(theta)
+    nw = t.shape[0]
+    d = np.asarray(data_fd, dtype=np.complex128)
+    dr, di, ww = _f64(d.real), _f64(d.imag), _f64(w)
+    cf = _f64(np.asarray(coef, dtype=np.float64).reshape(nw, qm + qt))
+    lnl, dh, hh = np.zeros(nw), np.zeros(nw), np.zeros(nw)
+    st = np.zeros(nw, dtype=np.uint32)
+    lib().orc_loglike_fd(_dp(t), nw, C.byref(o), int(n), float(dt), float(t0), _dp(dr), _dp(di), _dp(ww),
+                         int(qm), int(qt), float(fstar), _dp(cf), _dp(lnl), _dp(dh), _dp(hh),
+                         st.ctypes.data_as(C.POINTER(C.c_uint32)), _nthreads(nthreads))
     return lnl, dh, hh, st
 
 

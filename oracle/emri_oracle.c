@@ -667,22 +667,40 @@ void orc_prologue(const double* th, const orc_opts* o, int64_t n, double dt, dou
   out[3] = d3[0]; out[4] = d3[1]; out[5] = d3[2];
 }
 
+/* Frequency-dependent propagation (paper Sec. 2: alpha_M = F(z, f),
+ * alpha_T = G(z, f), e.g. a power series in f/f_*, acting on the waveform in
+ * frequency space).  Reading: coefficients constant in z,
+ *   alpha_M(f) = sum_{m=1..qm} a_m (f/f_*)^m   (its constant part is Xi of Eq. (6)),
+ *   alpha_T(f) = alpha_T + sum_{m=1..qt} b_m (f/f_*)^m.
+ * With the z-independent alpha_M the damping integral of Sec. 2 is
+ * (1/2) alpha_M ln(1+z), so each bin is scaled by (1+z)^(-alpha_M(|f|)/2); the
+ * delay of G3 becomes dt_GW(f) = -(alpha_T(|f|)/2) t_LB(z), i.e. the extra
+ * phase in cycles -(t_LB/2) sum_m b_m f (|f|/f_*)^m at the signed f = k_s/T. */
+typedef struct {
+  int qm, qt;
+  double fstar;
+  const double* coef;   /* a_1..a_qm, b_1..b_qt of this walker */
+} fd_walker;
+
 /* Log-likelihood of W walkers against packed data spectrum D_k
  * (D = DFT(d_I + i d_II), natural order, N complex) and weights w (N):
- *   <d|h> = sum_k w_k Re(conj(D_k) H_k exp(-2 pi i k_s r)) / d_GW,
- *   <h|h> = sum_k w_k |H_k|^2 / d_GW^2,
+ *   <d|h> = sum_k w_k Re(conj(D_k) H_k F_k exp(-2 pi i k_s r)) / d_GW,
+ *   <h|h> = sum_k w_k |H_k F_k|^2 / d_GW^2,
  *   lnL   = <d|h> - <h|h>/2     (the constant -<d|d>/2 is left out),
- * H = DFT(h_I + i h_II) of the unit-distance channels.  Also returns the
- * unit-distance sums dh_u = sum w Re(conj D H e^{..}), hh_u = sum w |H|^2. */
-void orc_loglike(const double* theta, int w, const orc_opts* o, int64_t n, double dt, double t0,
-                 const double* d_re, const double* d_im, const double* wt,
-                 double* lnl, double* dh_u, double* hh_u, uint32_t* status, int nthreads) {
+ * H = DFT(h_I + i h_II) of the unit-distance channels, F_k = 1 or the
+ * frequency-dependent factor above.  Also returns the unit-distance sums
+ * dh_u = sum w Re(conj D H F e^{..}), hh_u = sum w |H F|^2. */
+static void loglike_impl(const double* theta, int w, const orc_opts* o, int64_t n, double dt, double t0,
+                         const double* d_re, const double* d_im, const double* wt, int qm, int qt,
+                         double fstar, const double* coef, double* lnl, double* dh_u, double* hh_u,
+                         uint32_t* status, int nthreads) {
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
   for (int k = 0; k < w; ++k) {
     const double* th = theta + (size_t)k * P_COUNT;
+    const fd_walker fd = {qm, qt, fstar, coef ? coef + (size_t)k * (qm + qt) : NULL};
     double* hI = (double*)malloc(sizeof(double) * (size_t)n);
     double* hII = (double*)malloc(sizeof(double) * (size_t)n);
     cplx* z = (cplx*)malloc(sizeof(cplx) * (size_t)n);
@@ -696,17 +714,37 @@ void orc_loglike(const double* theta, int w, const orc_opts* o, int64_t n, doubl
       double pro[6];
       orc_prologue(th, o, n, dt, pro);
       Q r = (Q)pro[4] + (Q)pro[5];
+      const int use_fd = fd.coef && (fd.qm > 0 || fd.qt > 0);
+      Q tlb = 0, df = 1 / ((Q)n * (Q)dt);
+      R l1z = 0;
+      if (use_fd) {
+        tlb = lookback_q(th[P_Z], o);
+        l1z = log1pl((R)th[P_Z]);
+      }
       R sdh = 0, shh = 0;
       for (int64_t j = 0; j < n; ++j) {
         if (wt[j] == 0) continue;
         int64_t ks = (2 * j <= n) ? j : j - n;   /* signed frequency index */
         Q ph = (Q)ks * r;
+        R amp = 1;
+        if (use_fd) {
+          Q f = (Q)ks * df;
+          Q x = (f < 0 ? -f : f) / (Q)fd.fstar;
+          Q xm = 1, am = 0, bt = 0;
+          for (int m = 1; m <= (fd.qm > fd.qt ? fd.qm : fd.qt); ++m) {
+            xm *= x;
+            if (m <= fd.qm) am += (Q)fd.coef[m - 1] * xm;
+            if (m <= fd.qt) bt += (Q)fd.coef[fd.qm + m - 1] * xm;
+          }
+          ph += -tlb / 2 * bt * f;                /* f * dt_GW extra, cycles */
+          amp = expl(-0.5L * l1z * (R)am);        /* (1+z)^(-alpha_M(|f|)/2) */
+        }
         ph -= floorf128(ph);
         R a = 2 * PI_R * (R)ph;
-        R fr = cosl(a), fi = -sinl(a);            /* exp(-2 pi i k_s r) */
+        R fr = amp * cosl(a), fi = -amp * sinl(a);  /* F_k exp(-2 pi i k_s r) */
         R hr = Z[j].re * fr - Z[j].im * fi, hi = Z[j].re * fi + Z[j].im * fr;
         sdh += (R)wt[j] * ((R)d_re[j] * hr + (R)d_im[j] * hi);
-        shh += (R)wt[j] * (Z[j].re * Z[j].re + Z[j].im * Z[j].im);
+        shh += (R)wt[j] * (Z[j].re * Z[j].re + Z[j].im * Z[j].im) * (amp * amp);
       }
       R dgw = (R)pro[2];
       dh = (double)sdh; hh = (double)shh;
@@ -718,4 +756,19 @@ void orc_loglike(const double* theta, int w, const orc_opts* o, int64_t n, doubl
     if (hh_u) hh_u[k] = hh;
     if (status) status[k] = st;
   }
+}
+
+void orc_loglike(const double* theta, int w, const orc_opts* o, int64_t n, double dt, double t0,
+                 const double* d_re, const double* d_im, const double* wt,
+                 double* lnl, double* dh_u, double* hh_u, uint32_t* status, int nthreads) {
+  loglike_impl(theta, w, o, n, dt, t0, d_re, d_im, wt, 0, 0, 1.0, NULL, lnl, dh_u, hh_u, status, nthreads);
+}
+
+/* exposed: the same with frequency-dependent propagation; coef [W][qm+qt]
+ * (a_1..a_qm, b_1..b_qt per walker), f_* = fstar [Hz] */
+void orc_loglike_fd(const double* theta, int w, const orc_opts* o, int64_t n, double dt, double t0,
+                    const double* d_re, const double* d_im, const double* wt, int qm, int qt, double fstar,
+                    const double* coef, double* lnl, double* dh_u, double* hh_u, uint32_t* status,
+                    int nthreads) {
+  loglike_impl(theta, w, o, n, dt, t0, d_re, d_im, wt, qm, qt, fstar, coef, lnl, dh_u, hh_u, status, nthreads);
 }

@@ -478,3 +478,69 @@ def test_lnl_gr_limit(oracle_mod):
         dl = O.dl_cm(th[k, I.I_Z], opts)
         ref = O.inner(data, H, w) / dl - 0.5 * O.inner(H, H, w) / dl ** 2
         assert lnl[k] == pytest.approx(ref, rel=1e-12, abs=1e-12 * abs(O.inner(H, H, w)) / dl ** 2)
+
+
+# ------------------------------------------- frequency-dependent propagation
+def test_fd_zero_coefficients_and_pure_phase(oracle_mod):
+    # all coefficients zero: the standard likelihood, bit for bit; a pure
+    # speed term (a_m = 0) is a phase: <h|h> unchanged bit for bit
+    n, dt = 1 << 12, 15.0
+    opts = O.Opts(n_max=4)
+    th = I.draw_sources(21, 3, n)
+    psd = I.psd_bc04(n, dt)
+    w = O.weights(psd, n, dt, 1e-4, 1.0)
+    data = I.noise_spectrum(9, psd, n, dt)
+    ref = O.loglike(th, n, dt, data, w, opts)
+    got = O.loglike_fd(th, n, dt, data, w, 2, 3, 1e-2, np.zeros((3, 5)), opts)
+    for a, b in zip(ref[:3], got[:3]):
+        np.testing.assert_array_equal(a, b)
+    coef = np.zeros((3, 5))
+    coef[:, 2:] = np.random.default_rng(3).normal(0, 0.05, (3, 3))
+    ph = O.loglike_fd(th, n, dt, data, w, 2, 3, 1e-2, coef, opts)
+    np.testing.assert_array_equal(ph[2], ref[2])
+    assert np.all(np.abs(ph[1] - ref[1]) > 0)
+
+
+def test_fd_factor_against_closed_form(oracle_mod):
+    # One bin of data at a time (D = delta_k0 and D = i delta_k0) reads the
+    # factor G_k0 = F_k0 exp(-2 pi i f dt_GW) applied to H_k0 off <d|h>.
+    # Independent closed form at 50 digits: G = (1+z)^(-alpha_M(|f|)/2)
+    # exp(-2 pi i f dt_GW(f)), dt_GW(f) = -(alpha_T + sum b_m (|f|/f*)^m)/2
+    # t_LB(z), with t_LB from mpmath quadrature; both signs of f.
+    mpmath.mp.dps = 50
+    n, dt = 1 << 12, 15.0
+    opts = O.Opts(n_max=3)
+    th = I.draw_sources(22, 1, n)
+    th[0, I.I_ALPT] = 0.037
+    z = th[0, I.I_Z]
+    fstar = 3e-3
+    a_m = [0.4, -0.25]
+    b_m = [0.05, -0.02, 0.011]
+    coef = np.array([a_m + b_m])
+    hI, hII, _ = O.waveform(th, n, dt, opts)
+    H = O.packed_spectrum(hI[0], hII[0])
+    psd = np.ones(n // 2 + 1)
+    w = O.weights(psd, n, dt, 0.0, 1.0)
+    om = mpmath.mpf(0.315)
+    E = lambda x: mpmath.sqrt(om * (1 + x) ** 3 + 1 - om)
+    hinv = mpmath.mpf(3.0856775814913673e24) / (mpmath.mpf(67.4) * 100000)
+    tlb = hinv * mpmath.quad(lambda x: 1 / ((1 + x) * E(x)), [0, mpmath.mpf(z)])
+    for k0 in (5, 301, 1777, n - 1777, n - 3):
+        ks = k0 if 2 * k0 <= n else k0 - n
+        f = mpmath.mpf(ks) / (mpmath.mpf(n) * mpmath.mpf(dt))
+        x = abs(f) / mpmath.mpf(fstar)
+        am = sum(mpmath.mpf(a) * x ** (m + 1) for m, a in enumerate(a_m))
+        at = mpmath.mpf(th[0, I.I_ALPT]) + sum(mpmath.mpf(b) * x ** (m + 1) for m, b in enumerate(b_m))
+        dtgw = -at / 2 * tlb
+        cyc = f * dtgw
+        cyc -= mpmath.floor(cyc)
+        g = (1 + mpmath.mpf(z)) ** (-am / 2) * mpmath.expjpi(-2 * cyc)
+        out = []
+        for dval in (1.0, 1j):
+            d = np.zeros(n, dtype=np.complex128)
+            d[k0] = dval
+            _, dh, _, _ = O.loglike_fd(th, n, dt, d, w, len(a_m), len(b_m), fstar, coef, opts)
+            out.append(dh[0] / w[k0])
+        hg = out[0] + 1j * out[1]
+        G = hg / H[k0]
+        assert abs(G - complex(g)) < 1e-12 * abs(complex(g)), (k0, G, complex(g))

@@ -253,6 +253,34 @@ int emri_loglike_batch(emri_ctx* ctx, const emri_dataset* ds, const double* thet
                        const emri_opts* opts, double* lnl_dev, double* dh_dev, double* hh_dev,
                        uint32_t* status_dev, void* stream);
 
+/* ------------------------------------- frequency-dependent propagation
+ * Paper Sec. 2 allows alpha_M and alpha_T to depend on the GW frequency
+ * (alpha_M = F(z, f), alpha_T = G(z, f), e.g. a power series in f/f_*),
+ * acting on the waveform in frequency space.  Model (coefficients constant
+ * in z, per walker):
+ *   alpha_M(f) = sum_{m=1..q_m} a_m (f/f_*)^m: every bin is scaled by
+ *                (1+z)^(-alpha_M(|f|)/2) (the z-independent case of the
+ *                damping integral; the constant part stays Xi of Eq. (6));
+ *   alpha_T(f) = alpha_T + sum_{m=1..q_t} b_m (f/f_*)^m: the GW-speed delay
+ *                becomes dt_GW(f) = -(alpha_T(|f|)/2) t_LB(z), i.e. the bin
+ *                factor exp(-2 pi i f dt_GW(f)) at the signed f_k.
+ * emri_loglike_batch_fd is emri_loglike_batch with these factors applied per
+ * bin inside the fused FFT pass (<h|h> includes the amplitude factor); the
+ * phase, up to ~1e18 cycles, is evaluated exactly mod 1 in 128-bit fixed
+ * point.  coef_dev (device, [q_m + q_t][W], caller-owned): a_1..a_qm then
+ * b_1..b_qt per walker.  q_m = q_t = 0 reproduces emri_loglike_batch.
+ * Errors: EMRI_EINVAL for q outside [0, 3], f_star <= 0, NULL coefficients. */
+typedef struct {
+  int q_m;                 /* alpha_M terms, 0..3                           */
+  int q_t;                 /* extra alpha_T terms, 0..3                     */
+  double f_star;           /* pivot frequency f_* [Hz], > 0                  */
+  const double* coef_dev;  /* [q_m + q_t][W] device doubles                 */
+} emri_fdprop;
+
+int emri_loglike_batch_fd(emri_ctx* ctx, const emri_dataset* ds, const double* theta_dev, int w,
+                          const emri_opts* opts, const emri_fdprop* fd, double* lnl_dev, double* dh_dev,
+                          double* hh_dev, uint32_t* status_dev, void* stream);
+
 /* ------------------------------------------------------- uneven batching
  * Several independent chains, each with its own dataset (its own n), walker
  * count and options, evaluated by one launch of a captured CUDA graph with

@@ -250,7 +250,7 @@ int pick_wave(emri_ctx* ctx, const FftPlan& p, const OptsN& o, int w) {
 // The launch sequence of steps S0-S7 for W walkers of one dataset.
 int run_loglike(emri_ctx* ctx, const emri_dataset* ds, const double* theta, int64_t ld, int w, const OptsN& o,
                 int wave, const LoglikeBufs& b, double* lnl, double* dh, double* hh, uint32_t* status,
-                cudaStream_t s, int64_t* launches) {
+                cudaStream_t s, int64_t* launches, const FdW* fd) {
   const FftPlan& p = ds->plan;
   const bool f32 = o.precision != 0;
   const size_t cs = f32 ? sizeof(float2) : sizeof(double2);
@@ -282,7 +282,8 @@ int run_loglike(emri_ctx* ctx, const emri_dataset* ds, const double* theta, int6
     {
       KTimer t(pf, EMRI_K_FFT2_IP, s);
       launch_fft_pass2_ip(b.z, ww, p, f32, ctx->tw, b.wc + i0, b.dtab + (size_t)i0 * p.n1 * cs,
-                          b.rtab + (size_t)i0 * p.n2 * cs, dperm, wperm, b.partial + (size_t)i0 * p.n2, s);
+                          b.rtab + (size_t)i0 * p.n2 * cs, dperm, wperm, b.partial + (size_t)i0 * p.n2, s,
+                          fd ? fd + i0 : nullptr);
     }
     {
       KTimer t(pf, EMRI_K_FINALIZE, s);
@@ -734,5 +735,46 @@ extern "C" int emri_loglike_batch(emri_ctx* ctx, const emri_dataset* ds, const d
   rc = run_loglike(ctx, ds, theta, w, w, o, wave, b, lnl, dh, hh, status, s, &nl);
   ctx->ws.release(s);
   ctx->launches += nl;
+  return rc;
+}
+
+extern "C" int emri_loglike_batch_fd(emri_ctx* ctx, const emri_dataset* ds, const double* theta, int w,
+                                     const emri_opts* opts, const emri_fdprop* fd, double* lnl, double* dh,
+                                     double* hh, uint32_t* status, void* stream) {
+  if (!ctx || !ds || !fd) return set_err(EMRI_EINVAL, "NULL context, dataset or propagation model");
+  if (ds->ctx != ctx) return set_err(EMRI_EINVAL, "dataset belongs to another context");
+  if (fd->q_m < 0 || fd->q_m > 3 || fd->q_t < 0 || fd->q_t > 3)
+    return set_err(EMRI_EINVAL, "q_m and q_t must be in [0, 3]");
+  if (!(fd->f_star > 0) || !isfinite(fd->f_star)) return set_err(EMRI_EINVAL, "f_star must be positive and finite");
+  if (w < 0) return set_err(EMRI_EINVAL, "w must be >= 0");
+  if (w == 0) return EMRI_OK;
+  if (!theta || !lnl || (fd->q_m + fd->q_t > 0 && !fd->coef_dev)) return set_err(EMRI_EINVAL, "NULL pointer");
+  OptsN o;
+  int rc = normalize_opts(opts, ds->n, &o);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!(opts && opts->knot_spacing)) {
+    const int pk = ctx_plan_ks(ctx, ds->n, o);
+    if (pk) o.ks = pk;
+  }
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int wave = pick_wave(ctx, ds->plan, o, w);
+  Carve probe(nullptr);
+  probe.take<FdW>(w);
+  probe.off = (probe.off + 255) & ~(size_t)255;
+  const size_t need = probe.off + loglike_layout(ds->plan, o, w, wave, nullptr, nullptr);
+  if ((rc = ctx->ws.reserve(ctx, need, s))) return rc;
+  ctx->ws.acquire(s);
+  Carve cv(ctx->ws.ptr);
+  FdW* fdw = cv.take<FdW>(w);
+  LoglikeBufs b;
+  loglike_layout(ds->plan, o, w, wave, &cv, &b);
+  launch_fdprop(theta, w, w, ds->n, ds->dt, o, fd->q_m, fd->q_t, fd->f_star, fd->coef_dev, fdw, s);
+  int64_t nl = 1;
+  int64_t nr = 0;
+  rc = run_loglike(ctx, ds, theta, w, w, o, wave, b, lnl, dh, hh, status, s, &nr, fdw);
+  ctx->ws.release(s);
+  ctx->launches += nl + nr;
   return rc;
 }

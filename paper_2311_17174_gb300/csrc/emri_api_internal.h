@@ -143,7 +143,7 @@ size_t loglike_layout(const FftPlan& p, const OptsN& o, int w, int wave, Carve* 
 int pick_wave(emri_ctx* ctx, const FftPlan& p, const OptsN& o, int w);
 int run_loglike(emri_ctx* ctx, const emri_dataset* ds, const double* theta, int64_t ld, int w, const OptsN& o,
                 int wave, const LoglikeBufs& b, double* lnl, double* dh, double* hh, uint32_t* status,
-                cudaStream_t s, int64_t* launches);
+                cudaStream_t s, int64_t* launches, const FdW* fd = nullptr);
 int ctx_plan_wave(emri_ctx* ctx, int64_t n, const OptsN& o);
 int ctx_plan_ks(emri_ctx* ctx, int64_t n, const OptsN& o);
 void serve_shutdown(emri_ctx* ctx);

@@ -76,6 +76,19 @@ struct __align__(16) WalkerC {
   uint32_t pad_u;
 };
 
+// Frequency-dependent propagation of one walker (Sec. 2, alpha_M(f),
+// alpha_T(f) as power series in f/f_*): bin k (|k_s| = a) gets the amplitude
+// exp(nlz_half * sum_m a_m (a xs)^m) and the extra phase (cycles, mod 1)
+// sgn(k_s) * sum_m beta_m a^(m+1), beta_m as 128-bit fixed-point fractions.
+struct FdW {
+  double nlz_half;                  // -ln(1+z)/2
+  double xs;                        // df / f_*
+  double a[3];                      // alpha_M coefficients a_1..a_3
+  unsigned long long bhi[3], blo[3];// beta_1..beta_3, value = (hi 2^64 + lo) / 2^128
+  int qm, qt;
+};
+
+
 // Mixed-precision interval record of one knot interval: the three phases
 // (Doppler orbital phase, gamma~, alpha; cycles) as 64-bit fixed point
 // base + inc * tau plus FP32 s^2, s^3 corrections (s = tau / K_s), and the

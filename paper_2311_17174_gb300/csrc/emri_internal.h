@@ -8,6 +8,7 @@ namespace emri {
 
 struct WalkerC;
 struct Knot;
+struct FdW;
 
 // Options after defaults and validation.
 struct OptsN {
@@ -53,6 +54,9 @@ void launch_prologue(const double* theta, int64_t ld, int w, int64_t n, double d
 // tab[w][n1] = exp(-2 pi i frac(n2 k1 r)), rtab[w][n2] = exp(-2 pi i frac(k2 r))
 void launch_delay_table(const WalkerC* wc, int w, int n1, int n2, bool fp32, void* tab, void* rtab, cudaStream_t s);
 void launch_prologue_export(const WalkerC* wc, int w, double* out, cudaStream_t s);
+// frequency-dependent propagation records fd[w] from theta and coef[qm+qt][w]
+void launch_fdprop(const double* theta, int64_t ld, int w, int64_t n, double dt, const OptsN& o, int qm, int qt,
+                   double fstar, const double* coef, FdW* fd, cudaStream_t s);
 
 // orbit: knots[w][nk+1], nk = n / ks
 // mcpi_tab: Chebyshev-Picard tables (qn then qk); NULL selects the serial RK4 integrator
@@ -78,7 +82,7 @@ void launch_fft_pass2_store(const void* y, void* out, int batch, const FftPlan& 
 // FFT pass 2 fused with the weighted inner products; partial[w][n2] = (dh, hh)
 void launch_fft_pass2_ip(const void* y, int w, const FftPlan& p, bool fp32, const Twiddles& t,
                          const WalkerC* wc, const void* delay_tab, const void* row_tab, const void* data_perm,
-                         const void* wt_perm, double2* partial, cudaStream_t s);
+                         const void* wt_perm, double2* partial, cudaStream_t s, const FdW* fd = nullptr);
 // per-walker fixed-order reduction of the partials and lnL
 // dh_scale / hh_scale undo the dataset's FP32 scaling (1 for FP64)
 void launch_finalize(const double2* partial, int n2, const WalkerC* wc, int w, double dh_scale, double hh_scale,

@@ -328,6 +328,74 @@ struct AccF {
   }
 };
 
+// 128-bit fixed-point fractions (mod 1) for the frequency-dependent phase:
+// value = (hi 2^64 + lo) / 2^128; products with a small integer and sums wrap
+// mod 2^128, which is exactly the reduction mod 1 cycle.
+struct U128 {
+  unsigned long long hi, lo;
+};
+__device__ __forceinline__ U128 mul128_small(U128 a, unsigned long long k) {
+  U128 r;
+  r.lo = a.lo * k;
+  r.hi = a.hi * k + __umul64hi(a.lo, k);
+  return r;
+}
+__device__ __forceinline__ U128 add128(U128 a, U128 b) {
+  U128 r;
+  r.lo = a.lo + b.lo;
+  r.hi = a.hi + b.hi + (r.lo < a.lo ? 1ull : 0ull);
+  return r;
+}
+__device__ __forceinline__ U128 neg128(U128 a) {
+  U128 r;
+  r.lo = ~a.lo + 1ull;
+  r.hi = ~a.hi + (r.lo == 0ull ? 1ull : 0ull);
+  return r;
+}
+
+// exp(-2 pi i phi) of a phase fraction given by the top 64 bits (signed,
+// [-1/2, 1/2) cycle)
+__device__ __forceinline__ void phase_factor(long long top, double& c, double& s) {
+  const double ph = (double)top * 5.421010862427522e-20;   // 2^-64
+  double sn, cs;
+  sincospi(2.0 * ph, &sn, &cs);
+  c = cs;
+  s = -sn;
+}
+__device__ __forceinline__ void phase_factor(long long top, float& c, float& s) {
+  const float ph = (float)(int)(top >> 32) * 2.3283064365386963e-10f;   // 2^-32
+  float sn, cs;
+  __sincosf(6.283185307179586f * ph, &sn, &cs);
+  c = cs;
+  s = -sn;
+}
+__device__ __forceinline__ double fd_exp(double x) { return exp(x); }
+__device__ __forceinline__ float fd_exp(float x) { return __expf(x); }
+
+// Frequency-dependent factor of bin |k_s| = a: amplitude A (returned) and
+// the phase factor (c, s) = exp(-2 pi i sgn(k_s) sum beta_m a^(m+1)).
+template <typename T>
+__device__ __forceinline__ T fd_factor(const FdW& f, unsigned long long a, bool neg, T& c, T& s) {
+  T A = T(1);
+  if (f.qm > 0) {
+    const T x = (T)a * (T)f.xs;
+    T am = (T)f.a[f.qm - 1];
+    for (int m = f.qm - 2; m >= 0; --m) am = am * x + (T)f.a[m];
+    A = fd_exp((T)f.nlz_half * am * x);
+  }
+  if (f.qt > 0) {
+    U128 acc{f.bhi[f.qt - 1], f.blo[f.qt - 1]};
+    for (int m = f.qt - 2; m >= 0; --m) acc = add128(mul128_small(acc, a), U128{f.bhi[m], f.blo[m]});
+    acc = mul128_small(mul128_small(acc, a), a);
+    if (neg) acc = neg128(acc);
+    phase_factor((long long)acc.hi, c, s);
+  } else {
+    c = T(1);
+    s = T(0);
+  }
+  return A;
+}
+
 // Shared memory of one pass-2 row: the row itself, then (when they fit in
 // 160 KB together) the row's data, delay factors and weights, prefetched.
 template <typename C2, typename WT, int LG>
@@ -339,11 +407,12 @@ struct P2Smem {
   }
 };
 
-template <typename C2, typename WT, typename Acc, int LG>
+template <typename C2, typename WT, typename Acc, int LG, bool FD>
 __global__ void __launch_bounds__(kPass2Threads, sizeof(C2) == 8 ? 4 : 2)
     k4_pass2_ip(const C2* __restrict__ y, int64_t n, int n2, const C2* __restrict__ ta,
                 const WalkerC* __restrict__ wcs, const C2* __restrict__ dtab, const C2* __restrict__ rtab,
-                const C2* __restrict__ dperm, const WT* __restrict__ wperm, double2* __restrict__ partial) {
+                const C2* __restrict__ dperm, const WT* __restrict__ wperm, double2* __restrict__ partial,
+                const FdW* __restrict__ fdw) {
   extern __shared__ __align__(16) unsigned char smraw[];
   using SM = P2Smem<C2, WT, LG>;
   C2* buf = reinterpret_cast<C2*>(smraw);
@@ -374,14 +443,26 @@ __global__ void __launch_bounds__(kPass2Threads, sizeof(C2) == 8 ? 4 : 2)
   __syncthreads();
   Acc acc;
   acc.init();
+  FdW fd;
+  if (FD) fd = fdw[wk];
   for (int k1 = threadIdx.x; k1 < N1; k1 += kPass2Threads) {
     const C2 H = buf[k1];
     const T wv = SM::kPrefetch ? (T)ws[k1] : (T)wperm[base + k1];
     const C2 D = SM::kPrefetch ? ds[k1] : dperm[base + k1];
     C2 f = cmul(a, SM::kPrefetch ? ts[k1] : tabw[k1]);
-    if (2 * k1 > N1 || (2 * k1 == N1 && k2 > 0)) f = cmul(f, cnv);   // signed index k - n
+    const bool neg = 2 * k1 > N1 || (2 * k1 == N1 && k2 > 0);
+    if (neg) f = cmul(f, cnv);   // signed index k - n
+    T A2 = T(1);
+    if (FD) {
+      const long long kk = (long long)k2 + (long long)n2 * k1;
+      const unsigned long long ak = (unsigned long long)(neg ? n - kk : kk);
+      T c, sn;
+      const T A = fd_factor<T>(fd, ak, neg, c, sn);
+      f = cmul(f, CT<C2>::make(A * c, A * sn));
+      A2 = A * A;
+    }
     const C2 Hd = cmul(H, f);
-    acc.add(wv * (D.x * Hd.x + D.y * Hd.y), wv * (H.x * H.x + H.y * H.y));
+    acc.add(wv * (D.x * Hd.x + D.y * Hd.y), wv * (H.x * H.x + H.y * H.y) * A2);
   }
   // fixed-shape reduction in the accumulator's own arithmetic: warp xor tree,
   // then warp 0 over the warp partials
@@ -550,25 +631,35 @@ void launch_fft_pass2_store(const void* y, void* out, int batch, const FftPlan& 
   }
 }
 
-void launch_fft_pass2_ip(const void* y, int w, const FftPlan& p, bool fp32, const Twiddles& t, const WalkerC* wc,
-                         const void* delay_tab, const void* row_tab, const void* data_perm, const void* wt_perm,
-                         double2* partial, cudaStream_t s) {
-  if (w <= 0) return;
+template <bool FD>
+static void pass2_ip_dispatch(const void* y, int w, const FftPlan& p, bool fp32, const Twiddles& t,
+                              const WalkerC* wc, const void* delay_tab, const void* row_tab, const void* data_perm,
+                              const void* wt_perm, double2* partial, const FdW* fd, cudaStream_t s) {
   dim3 g(p.n2, w);
   const int lg = log2i(p.n1);
   if (fp32) {
-#define CALLI32(L) k4_pass2_ip<float2, float, AccF, L><<<g, kPass2Threads, P2Smem<float2, float, L>::bytes(), s>>>( \
-      (const float2*)y, p.n, p.n2, t.ta32, wc, (const float2*)delay_tab, (const float2*)row_tab,           \
-      (const float2*)data_perm, (const float*)wt_perm, partial)
+#define CALLI32(L) k4_pass2_ip<float2, float, AccF, L, FD><<<g, kPass2Threads, P2Smem<float2, float, L>::bytes(), s>>>( \
+      (const float2*)y, p.n, p.n2, t.ta32, wc, (const float2*)delay_tab, (const float2*)row_tab,                \
+      (const float2*)data_perm, (const float*)wt_perm, partial, fd)
     EMRI_LG_SWITCH(lg, CALLI32)
 #undef CALLI32
   } else {
-#define CALLI64(L) k4_pass2_ip<double2, double, AccD, L><<<g, kPass2Threads, P2Smem<double2, double, L>::bytes(), s>>>( \
-      (const double2*)y, p.n, p.n2, t.ta64, wc, (const double2*)delay_tab, (const double2*)row_tab,            \
-      (const double2*)data_perm, (const double*)wt_perm, partial)
+#define CALLI64(L) k4_pass2_ip<double2, double, AccD, L, FD><<<g, kPass2Threads, P2Smem<double2, double, L>::bytes(), s>>>( \
+      (const double2*)y, p.n, p.n2, t.ta64, wc, (const double2*)delay_tab, (const double2*)row_tab,                 \
+      (const double2*)data_perm, (const double*)wt_perm, partial, fd)
     EMRI_LG_SWITCH(lg, CALLI64)
 #undef CALLI64
   }
+}
+
+void launch_fft_pass2_ip(const void* y, int w, const FftPlan& p, bool fp32, const Twiddles& t, const WalkerC* wc,
+                         const void* delay_tab, const void* row_tab, const void* data_perm, const void* wt_perm,
+                         double2* partial, cudaStream_t s, const FdW* fd) {
+  if (w <= 0) return;
+  if (fd)
+    pass2_ip_dispatch<true>(y, w, p, fp32, t, wc, delay_tab, row_tab, data_perm, wt_perm, partial, fd, s);
+  else
+    pass2_ip_dispatch<false>(y, w, p, fp32, t, wc, delay_tab, row_tab, data_perm, wt_perm, partial, nullptr, s);
 }
 
 void launch_finalize(const double2* partial, int n2, const WalkerC* wc, int w, double dh_scale, double hh_scale,
@@ -607,7 +698,8 @@ void fft_set_smem_limits() {
   P1(5); P1(6); P1(7); P1(8); P1(9); P1(10);
 #undef P1
 #define P2(L) raise(k4_pass2_store<double2, L>), raise(k4_pass2_store<float2, L>), \
-              raise(k4_pass2_ip<double2, double, AccD, L>), raise(k4_pass2_ip<float2, float, AccF, L>)
+              raise(k4_pass2_ip<double2, double, AccD, L, false>), raise(k4_pass2_ip<float2, float, AccF, L, false>), \
+              raise(k4_pass2_ip<double2, double, AccD, L, true>), raise(k4_pass2_ip<float2, float, AccF, L, true>)
   P2(5); P2(6); P2(7); P2(8); P2(9); P2(10); P2(11); P2(12);
 #undef P2
 }

@@ -25,6 +25,19 @@ __device__ __forceinline__ bool finite_all(const double* th, int64_t ld, int i) 
   return true;
 }
 
+// lookback time (flat Lambda-CDM, closed form) in dd:
+//   t_LB = (1/H0) (2/(3 sqrt(OL))) [asinh(s) - asinh(s (1+z)^(-3/2))], s = sqrt(OL/Om)
+__device__ dd lookback_dd(double zz, double omega_m, double h0) {
+  dd om = dd_make(omega_m);
+  dd ol = dd_add_d(dd_neg(om), 1.0);
+  dd s = dd_sqrt(dd_div(ol, om));
+  dd zp = two_sum(1.0, zz);
+  dd u = dd_div(dd_make(1.0), dd_mul(zp, dd_sqrt(zp)));
+  dd hinv_dd = dd_div(dd_make(kMpc), two_prod(h0, 1e5));
+  dd diff = dd_sub(dd_asinh(s), dd_asinh(dd_mul(s, u)));
+  return dd_mul(dd_div(dd_mul_d(hinv_dd, 2.0), dd_mul_d(dd_sqrt(ol), 3.0)), diff);
+}
+
 __global__ void k0_prologue(const double* __restrict__ theta, int64_t ld, int w, int64_t n, double dt,
                             int mode, double n_xi, double omega_m, double h0,
                             const double* __restrict__ gl, WalkerC* __restrict__ out) {
@@ -119,14 +132,7 @@ __global__ void k0_prologue(const double* __restrict__ theta, int64_t ld, int w,
   //   t_LB = (1/H0) (2/(3 sqrt(OL))) [asinh(s) - asinh(s (1+z)^(-3/2))], s = sqrt(OL/Om)
   const double alpt = st ? 0.0 : theta[P_ALPT * ld + i];
   if (alpt != 0.0 && zz > 0.0) {
-    dd om = dd_make(omega_m);
-    dd ol = dd_add_d(dd_neg(om), 1.0);
-    dd s = dd_sqrt(dd_div(ol, om));
-    dd zp = two_sum(1.0, zz);
-    dd u = dd_div(dd_make(1.0), dd_mul(zp, dd_sqrt(zp)));
-    dd hinv_dd = dd_div(dd_make(kMpc), two_prod(h0, 1e5));
-    dd diff = dd_sub(dd_asinh(s), dd_asinh(dd_mul(s, u)));
-    dd tlb = dd_mul(dd_div(dd_mul_d(hinv_dd, 2.0), dd_mul_d(dd_sqrt(ol), 3.0)), diff);
+    dd tlb = lookback_dd(zz, omega_m, h0);
     dd dtgw = dd_mul_d(tlb, -0.5 * alpt);
     dd tobs = two_prod((double)n, dt);
     dd r = dd_frac(dd_div(dtgw, tobs));
@@ -218,6 +224,58 @@ void launch_delay_table(const WalkerC* wc, int w, int n1, int n2, bool fp32, voi
 void launch_prologue_export(const WalkerC* wc, int w, double* out, cudaStream_t s) {
   if (w <= 0) return;
   k0_export<<<(w + 127) / 128, 128, 0, s>>>(wc, w, out);
+}
+
+// ----------------------------------------- frequency-dependent propagation
+// dd fraction x in [0, 1) -> 128-bit fixed point (hi, lo) = x 2^128, mod 2^128.
+// x.hi 2^64 is exact but carries only 53 bits; the low bits of the 64-bit
+// integer part come from x.lo 2^64, which can reach ~2^11 in magnitude, so
+// its integer part is carried into hi and only its fraction goes to lo.
+__device__ void dd_to_fx128(dd x, unsigned long long& hi, unsigned long long& lo) {
+  const double two64 = 18446744073709551616.0;
+  const double t = x.hi * two64;            // exact scaling, 0 <= t < 2^64
+  const double H = floor(t);                // exact
+  const double r = (t - H) + x.lo * two64;  // t - H and x.lo 2^64 exact; |r| < ~2^12
+  const double F = floor(r);                // exact integer
+  const double rem = r - F;                 // exact, [0, 1)
+  hi = (unsigned long long)H + (unsigned long long)(long long)F;   // mod 2^64
+  lo = (unsigned long long)(rem * two64);
+}
+
+// beta_m = -(t_LB/2) b_m df^(m+1) / f_*^m (cycles per |k|^(m+1)), reduced mod 1
+// in dd before the conversion to fixed point.
+__global__ void k0_fdprop(const double* __restrict__ theta, int64_t ld, int w, int64_t n, double dt, double omega_m,
+                          double h0, int qm, int qt, double fstar, const double* __restrict__ coef,
+                          FdW* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= w) return;
+  FdW f{};
+  f.qm = qm;
+  f.qt = qt;
+  double z = theta[P_Z * ld + i];
+  if (!(z >= 0.0) || !isfinite(z)) z = 0.0;   // such a walker is flagged by the prologue
+  f.nlz_half = -0.5 * log1p(z);
+  const dd tobs = two_prod((double)n, dt);
+  const dd df = dd_div(dd_make(1.0), tobs);
+  f.xs = dd_div(df, dd_make(fstar)).hi;
+  for (int m = 0; m < qm; ++m) f.a[m] = coef[(int64_t)m * w + i];
+  if (qt > 0) {
+    const dd tlb = z > 0.0 ? lookback_dd(z, omega_m, h0) : dd_make(0.0);
+    const dd q = dd_div(df, dd_make(fstar));
+    dd base = dd_mul(dd_mul_d(tlb, -0.5), df);   // -(t_LB/2) df
+    for (int m = 0; m < qt; ++m) {
+      base = dd_mul(base, q);                     // -(t_LB/2) df (df/f_*)^(m+1)
+      const dd beta = dd_frac(dd_mul_d(base, coef[(int64_t)(qm + m) * w + i]));
+      dd_to_fx128(beta, f.bhi[m], f.blo[m]);
+    }
+  }
+  out[i] = f;
+}
+
+void launch_fdprop(const double* theta, int64_t ld, int w, int64_t n, double dt, const OptsN& o, int qm, int qt,
+                   double fstar, const double* coef, FdW* fd, cudaStream_t s) {
+  if (w <= 0) return;
+  k0_fdprop<<<(w + 127) / 128, 128, 0, s>>>(theta, ld, w, n, dt, o.omega_m, o.h0, qm, qt, fstar, coef, fd);
 }
 
 }  // namespace emri

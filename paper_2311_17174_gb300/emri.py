@@ -57,6 +57,10 @@ class ReqStats(C.Structure):
                 ("status", C.c_int32), ("slot", C.c_int32)]
 
 
+class FdProp(C.Structure):
+    _fields_ = [("q_m", C.c_int), ("q_t", C.c_int), ("f_star", C.c_double), ("coef_dev", C.c_void_p)]
+
+
 class StretchCfg(C.Structure):
     _fields_ = [("a", C.c_double), ("free_mask", C.c_uint32), ("lo", C.c_double * 16), ("hi", C.c_double * 16)]
 
@@ -86,6 +90,9 @@ _SIGS = {
     "emri_fft_batch_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "emri_loglike_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(Opts),
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "emri_loglike_batch_fd": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(Opts),
+                                        C.POINTER(FdProp), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p]),
     "emri_loglike_multi": (C.c_int, [C.c_void_p, C.POINTER(Work), C.c_int, C.c_void_p]),
     "emri_serve_start": (C.c_int, [C.c_void_p, C.POINTER(ServeCfg)]),
     "emri_serve_stop": (C.c_int, [C.c_void_p]),
@@ -254,6 +261,14 @@ class Context:
         w = int(theta.shape[1]) if theta is not None and hasattr(theta, "shape") else 0
         _check(self.lib.emri_loglike_batch(self.h, ds.h, _ptr(theta), w, C.byref(o), _ptr(lnl), _ptr(dh),
                                            _ptr(hh), _ptr(status), _stream(stream)))
+
+    def loglike_batch_fd(self, ds: "Dataset", theta, o: Opts, q_m: int, q_t: int, f_star: float, coef, lnl,
+                         dh=None, hh=None, status=None, stream=None):
+        """emri_loglike_batch_fd: coef is a device tensor [q_m + q_t][W] (a_m then b_m)."""
+        w = int(theta.shape[1])
+        fd = FdProp(int(q_m), int(q_t), float(f_star), _ptr(coef) if coef is not None else None)
+        _check(self.lib.emri_loglike_batch_fd(self.h, ds.h, _ptr(theta), w, C.byref(o), C.byref(fd), _ptr(lnl),
+                                              _ptr(dh), _ptr(hh), _ptr(status), _stream(stream)))
 
     def loglike_multi(self, items, stream=None):
         arr = (Work * len(items))()

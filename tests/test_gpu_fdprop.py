@@ -1,0 +1,60 @@
+"""Frequency-dependent propagation (emri_loglike_batch_fd) against the
+oracle's orc_loglike_fd: FP64 lnL within 1e-9 (|<d|h>| + <h|h>/2), <h|h>
+within 2e-9 relative, mixed |dlnL| <= 1e-2, with coefficients that put the
+extra GW-speed phase at up to ~1e14 cycles (exact mod 1 on both sides), and
+zero coefficients reproducing emri_loglike_batch."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2311_17174_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def test_fdprop_matches_oracle():
+    from paper_2311_17174_gb300 import emri
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ctx = emri.Context(0)
+    n, dt, nm = 1 << 14, 15.0, 6
+    inj = I.draw_sources(91, 1, n)[0]
+    psd = I.psd_bc04(n, dt)
+    d, inj2, w, _ = O.injection_data(inj, n, dt, psd, 92, O.Opts(n_max=nm), snr=40.0)
+    th = I.scatter_walkers(93, inj2, 12)
+    ds = ctx.dataset(emri.grid(n, dt), d, psd, 1e-4, 1.0 / (2 * dt))
+    g = np.random.default_rng(94)
+    qm, qt, fstar = 2, 3, 3e-3
+    coef = np.concatenate([g.normal(0, 0.3, (12, qm)), g.normal(0, 0.05, (12, qt))], axis=1)
+    ref, dh_o, hh_o, st_o = O.loglike_fd(th, n, dt, d, w, qm, qt, fstar, coef, O.Opts(n_max=nm))
+    theta = torch.tensor(th.T.copy(), device="cuda:0")
+    cdev = torch.tensor(coef.T.copy(), device="cuda:0")
+    out = {}
+    for prec in (0, 1):
+        lnl, dh, hh = (torch.zeros(12, dtype=torch.float64, device="cuda:0") for _ in range(3))
+        ctx.loglike_batch_fd(ds, theta, emri.opts(precision=prec, n_max=nm), qm, qt, fstar, cdev, lnl, dh, hh)
+        torch.cuda.synchronize()
+        out[prec] = [x.cpu().numpy() for x in (lnl, dh, hh)]
+    dgw = np.array([O.prologue(t, n, dt)[2] for t in th])
+    tol = 1e-9 * (np.abs(dh_o / dgw) + 0.5 * hh_o / dgw ** 2)
+    assert np.all(np.abs(out[0][0] - ref) <= tol), (np.abs(out[0][0] - ref) / tol).max()
+    np.testing.assert_allclose(out[0][2], hh_o, rtol=2e-9)
+    assert np.max(np.abs(out[1][0] - ref)) <= 1e-2
+    # the model changes the answer (the test is not vacuous)
+    base = torch.zeros(12, dtype=torch.float64, device="cuda:0")
+    ctx.loglike_batch(ds, theta, emri.opts(n_max=nm), base)
+    torch.cuda.synchronize()
+    assert np.min(np.abs(base.cpu().numpy() - ref)) > 1e-3
+    # zero coefficients: the standard likelihood
+    zero = torch.zeros((qm + qt, 12), dtype=torch.float64, device="cuda:0")
+    lz = torch.zeros(12, dtype=torch.float64, device="cuda:0")
+    ctx.loglike_batch_fd(ds, theta, emri.opts(n_max=nm), qm, qt, fstar, zero, lz)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(lz.cpu().numpy(), base.cpu().numpy(), rtol=1e-14)
+    for bad in ((4, 0, fstar), (0, -1, fstar), (1, 1, 0.0)):
+        with pytest.raises(emri.EmriError) as ei:
+            ctx.loglike_batch_fd(ds, theta, emri.opts(n_max=nm), bad[0], bad[1], bad[2], cdev, lz)
+        assert ei.value.code == emri.EINVAL
+    ds.close()
+    ctx.close()

@@ -48,6 +48,8 @@ struct BesselTab {
   float* f32;
 };
 void launch_bessel_tables(BesselTab t, cudaStream_t s);
+// the FP64 waveform kernel's exp(2 pi i k/128) table on the current device; 0 on success
+int upload_exp128();
 
 void launch_prologue(const double* theta, int64_t ld, int w, int64_t n, double dt, const OptsN& o,
                      const double* gl, WalkerC* out, cudaStream_t s);

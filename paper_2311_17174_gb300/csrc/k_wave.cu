@@ -109,6 +109,38 @@ __global__ void k_bessel_tables(double* r64, float* r32, double* f64, float* f32
   }
 }
 
+// exp(2 pi i k / 128), k = -64..64, for the FP64 sin/cos of reduced phases;
+// filled from the host (long double) at context creation.
+__device__ double2 g_exp128[129];
+
+int upload_exp128() {
+  double2 h[129];
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int k = -64; k <= 64; ++k) {
+    const long double a = 2.0L * pi * (long double)k / 128.0L;
+    h[k + 64] = make_double2((double)cosl(a), (double)sinl(a));
+  }
+  return cudaMemcpyToSymbol(g_exp128, h, sizeof(h)) == cudaSuccess ? 0 : -1;
+}
+
+// cos(2 pi f), sin(2 pi f) for a phase |f| <= 1/2 cycle: f = k/128 + d with
+// |d| <= 1/256, exp(2 pi i k/128) from the table and the Taylor polynomials of
+// cos and sin at x = 2 pi d (|x| <= 0.0246: the first omitted terms, x^8/8!
+// and x^9/9!, are below 1e-18).  About 17 FP64 operations.
+__device__ __forceinline__ void sincos2pi_tab(double f, const double2* __restrict__ tab, double& s, double& c) {
+  const double kd = rint(f * 128.0);
+  const double d = fma(kd, -0.0078125, f);   // exact
+  const double x = d * 6.283185307179586;
+  const double x2 = x * x;
+  const double p = fma(x2, fma(x2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0);
+  const double sx = fma(x2 * x, p, x);
+  const double q = fma(x2, fma(x2, -1.0 / 720.0, 1.0 / 24.0), -0.5);
+  const double cx = fma(x2, q, 1.0);
+  const double2 t = tab[(int)kd + 64];
+  s = fma(t.y, cx, t.x * sx);
+  c = fma(t.x, cx, -t.y * sx);
+}
+
 void launch_bessel_tables(BesselTab t, cudaStream_t s) {
   k_bessel_tables<<<(35 * 32 + 255) / 256, 256, 0, s>>>(t.r64, t.r32, t.f64, t.f32);
 }
@@ -458,6 +490,7 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
   __shared__ double bnode[3 * 32 * 3];
   __shared__ double bq[32 * 9];
   __shared__ double oq[2][3];
+  __shared__ double2 ex[129];
   __shared__ Geo<double> g;
   const int wk = blockIdx.y;
   const WalkerC& C = wcs[wk];
@@ -471,16 +504,18 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
   if (t < ni) build_iv(kn[kfirst + t], kn[kfirst + t + 1], h, iv[t]);
   if (t >= 128 && t < 134) oq[(t - 128) / 3][(t - 128) % 3] = lisa[blockIdx.x * 6 + (t - 128)];
   if (t == 160) load_geo<double>(C, g);
+  if (t < 129) ex[t] = g_exp128[t];
   __syncthreads();
   const int span = tile_span(j0, C.j_plunge);
   tile_harmonics<double, IvD>(iv, ni, j0, kfirst, ks, n_max, span, bnode, bq, rk, ifact);
   __syncthreads();
+  const double inv_span = 1.0 / (double)span;
 
   const int64_t j = j0 + t;
   double2 out = make_double2(0.0, 0.0);
   if (j < C.j_plunge) {
     const int ki = ks >= kTile ? 0 : t / ks;
-    const double s = (double)(j - (kfirst + ki) * ks) / (double)ks;
+    const double s = (double)(j - (kfirst + ki) * ks) * (1.0 / (double)ks);   // ks: a power of two
     const IvD& v = iv[ki];
     double fph = poly3<double>(v.ph, s);
     fph -= rint(fph);
@@ -493,11 +528,11 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
     const double cb = (oq[0][2] * so + oq[0][1]) * so + oq[0][0];
     const double sb = (oq[1][2] * so + oq[1][1]) * so + oq[1][0];
     double sph, cph, s2g, c2g, sa, ca;
-    sincospi(2.0 * fph, &sph, &cph);
-    sincospi(2.0 * fgm, &s2g, &c2g);
-    sincospi(2.0 * fal, &sa, &ca);
+    sincos2pi_tab(fph, ex, sph, cph);
+    sincos2pi_tab(fgm, ex, s2g, c2g);
+    sincos2pi_tab(fal, ex, sa, ca);
     double hI, hII;
-    channels<double>(g, cph, sph, c2g, s2g, ca, sa, cb, sb, A, (double)t / span, bq, n_max, hI, hII);
+    channels<double>(g, cph, sph, c2g, s2g, ca, sa, cb, sb, A, (double)t * inv_span, bq, n_max, hI, hII);
     if (unit_scale) {
       hI *= g.amp_scale;
       hII *= g.amp_scale;

@@ -70,7 +70,7 @@ struct __align__(16) WalkerC {
   double dop;                // (R/c) sin(theta_S) [s]
   double pad[3];
   Geo<float> gf;             // the geometry rounded to FP32 (mixed kernels)
-  float padf[2];
+  float cnf[2];              // (cn_re, cn_im) rounded to FP32
   int64_t j_plunge;          // first zeroed sample (n if none); written by the orbit kernel
   uint32_t status;           // status bits (prologue | orbit)
   uint32_t pad_u;

@@ -191,6 +191,125 @@ __device__ __forceinline__ void smem_fft(C2* buf, int sign, const C2* __restrict
   }
 }
 
+// ------------------------------------------ radix-8 Stockham (FP32 path)
+// The same Stockham layout as smem_fft, with radix-8 stages (then one radix-4
+// or radix-2 stage for the remaining bits): a 2048-point transform takes four
+// shared-memory round trips instead of six.  Used for float2 only: in FP64
+// the radix-8 butterfly costs slightly more FP64 operations per point than
+// radix 4, and the FP64 passes are bound by the FP64 pipe.
+template <typename C2>
+__device__ __forceinline__ C2 mul_i(C2 d, int sign) {   // -i d (sign < 0) or +i d
+  return sign < 0 ? CT<C2>::make(d.y, -d.x) : CT<C2>::make(-d.y, d.x);
+}
+
+template <typename C2>
+__device__ __forceinline__ void dft4_inplace(C2& a0, C2& a1, C2& a2, C2& a3, int sign) {
+  const C2 s0 = cadd(a0, a2), s1 = csub(a0, a2), s2 = cadd(a1, a3), s3 = mul_i(csub(a1, a3), sign);
+  a0 = cadd(s0, s2);
+  a2 = csub(s0, s2);
+  a1 = cadd(s1, s3);
+  a3 = csub(s1, s3);
+}
+
+// X_q = sum_r a_r w^(q r), w = exp(sign 2 pi i / R), R = 2, 4, 8; in place
+template <typename C2, int R>
+__device__ __forceinline__ void dft_r(C2* a, int sign) {
+  using T = typename CT<C2>::T;
+  if constexpr (R == 2) {
+    const C2 t = a[0];
+    a[0] = cadd(t, a[1]);
+    a[1] = csub(t, a[1]);
+  } else if constexpr (R == 4) {
+    dft4_inplace(a[0], a[1], a[2], a[3], sign);
+  } else {
+    // even and odd halves, then the W8^q combination
+    C2 e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+    C2 o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+    dft4_inplace(e0, e1, e2, e3, sign);
+    dft4_inplace(o0, o1, o2, o3, sign);
+    const T h = T(0.70710678118654752440);
+    // W8 = h (1 - i) for sign < 0, h (1 + i) for sign > 0
+    o1 = sign < 0 ? CT<C2>::make(h * (o1.x + o1.y), h * (o1.y - o1.x))
+                  : CT<C2>::make(h * (o1.x - o1.y), h * (o1.x + o1.y));
+    o2 = mul_i(o2, sign);
+    o3 = sign < 0 ? CT<C2>::make(h * (o3.y - o3.x), -h * (o3.x + o3.y))
+                  : CT<C2>::make(-h * (o3.x + o3.y), h * (o3.x - o3.y));
+    a[0] = cadd(e0, o0); a[4] = csub(e0, o0);
+    a[1] = cadd(e1, o1); a[5] = csub(e1, o1);
+    a[2] = cadd(e2, o2); a[6] = csub(e2, o2);
+    a[3] = cadd(e3, o3); a[7] = csub(e3, o3);
+  }
+}
+
+// One radix-R stage on NB interleaved transforms of length L, sub-transform
+// length NS so far; twiddles W_{R NS}^{k r} from ta (4096 points per cycle).
+template <typename C2, int R, int NB, int NTH, int L, int NS>
+__device__ __forceinline__ void stage_r(C2* buf, int sign, const C2* __restrict__ ta) {
+  constexpr int Q = L / R;
+  constexpr int NBF = NB * Q;
+  constexpr int MB = (NBF + NTH - 1) / NTH;
+  constexpr int STEP = 4096 / (R * NS);
+  const int tid = threadIdx.x;
+  C2 y[MB][R];
+  int dst[MB];
+#pragma unroll
+  for (int m = 0; m < MB; ++m) {
+    const int b = tid + m * NTH;
+    dst[m] = -1;
+    if (NBF % NTH == 0 || b < NBF) {
+      const int c = b % NB, j = b / NB;
+      const int k = j & (NS - 1);
+#pragma unroll
+      for (int q = 0; q < R; ++q) y[m][q] = buf[(j + q * Q) * NB + c];
+      if (NS > 1) {
+        const int u = k * STEP;
+#pragma unroll
+        for (int q = 1; q < R; ++q) y[m][q] = cmul(y[m][q], conj_if(ta[u * q], sign));
+      }
+      dft_r<C2, R>(y[m], sign);
+      dst[m] = c + (((j / NS) * NS * R) + k) * NB;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < MB; ++m)
+    if (dst[m] >= 0) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) buf[dst[m] + q * NS * NB] = y[m][q];
+    }
+  __syncthreads();
+}
+
+template <typename C2, int LG, int NB, int NTH, int ST>
+__device__ __forceinline__ void r8_stages(C2* buf, int sign, const C2* __restrict__ ta) {
+  constexpr int L = 1 << LG;
+  constexpr int N8 = LG / 3;
+  if constexpr (ST < N8) {
+    stage_r<C2, 8, NB, NTH, L, (1 << (3 * ST))>(buf, sign, ta);
+    r8_stages<C2, LG, NB, NTH, ST + 1>(buf, sign, ta);
+  } else {
+    constexpr int NS = 1 << (3 * N8);
+    if constexpr (LG % 3 == 2) stage_r<C2, 4, NB, NTH, L, NS>(buf, sign, ta);
+    if constexpr (LG % 3 == 1) stage_r<C2, 2, NB, NTH, L, NS>(buf, sign, ta);
+  }
+}
+
+// The transform of a shared tile: radix-8 stages in FP32, radix-4 in FP64.
+template <typename C2, int LG, int NB, int NTH>
+__device__ __forceinline__ void tile_fft(C2* buf, int sign, const C2* __restrict__ ta) {
+  if constexpr (sizeof(C2) == 8)
+    r8_stages<C2, LG, NB, NTH, 0>(buf, sign, ta);
+  else
+    smem_fft<C2, LG, NB, NTH>(buf, sign, ta);
+}
+
+template <typename C2>
+__device__ __forceinline__ C2 cn_factor(const WalkerC& c);
+template <>
+__device__ __forceinline__ double2 cn_factor<double2>(const WalkerC& c) { return make_double2(c.cn_re, c.cn_im); }
+template <>
+__device__ __forceinline__ float2 cn_factor<float2>(const WalkerC& c) { return make_float2(c.cnf[0], c.cnf[1]); }
+
 // 16-byte asynchronous global -> shared copies (cp.async, L2 only) and their
 // group fences: the copies of a row are issued before the FFT and waited for
 // after it, so their latency overlaps the butterflies.
@@ -262,7 +381,7 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(C2) == 8 ? 2 : 1) k3_pass1
   const int j10 = blockIdx.x * NB;
   tile_load<C2, 8>(buf, zw + j10, n1, NB, N2);
   __syncthreads();
-  smem_fft<C2, LG, NB, kFftThreads>(buf, sign, ta);
+  tile_fft<C2, LG, NB, kFftThreads>(buf, sign, ta);
   for (int idx = threadIdx.x; idx < NB * N2; idx += kFftThreads) {
     const int c = idx % NB, k2 = idx / NB;
     const uint32_t m = (uint32_t)((j10 + c) * k2) << shift22;
@@ -282,7 +401,7 @@ __global__ void __launch_bounds__(kPass2Threads, 2) k4_pass2_store(const C2* __r
   const C2* row = y + (int64_t)blockIdx.y * n + (int64_t)N1 * k2;
   tile_load<C2, 4>(buf, row, 0, N1, 1);
   __syncthreads();
-  smem_fft<C2, LG, 1, kPass2Threads>(buf, sign, ta);
+  tile_fft<C2, LG, 1, kPass2Threads>(buf, sign, ta);
   C2* o = out + (int64_t)blockIdx.y * n;
   for (int k1 = threadIdx.x; k1 < N1; k1 += kPass2Threads) o[k2 + (int64_t)n2 * k1] = buf[k1];
 }
@@ -435,10 +554,10 @@ __global__ void __launch_bounds__(kPass2Threads, sizeof(C2) == 8 ? 4 : 2)
   }
   cp_async_commit();
   const C2 a = rtab[(int64_t)wk * n2 + k2];                 // exp(-2 pi i frac(k2 r))
-  const C2 cnv = CT<C2>::make((T)wcs[wk].cn_re, (T)wcs[wk].cn_im);
+  const C2 cnv = cn_factor<C2>(wcs[wk]);
   cp_async_wait<1>();
   __syncthreads();
-  smem_fft<C2, LG, 1, kPass2Threads>(buf, -1, ta);
+  tile_fft<C2, LG, 1, kPass2Threads>(buf, -1, ta);
   cp_async_wait<0>();
   __syncthreads();
   Acc acc;

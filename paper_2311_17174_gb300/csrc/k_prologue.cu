@@ -150,6 +150,8 @@ __global__ void k0_prologue(const double* __restrict__ theta, int64_t ld, int w,
     c.dt_gw = 0.0; c.r_hi = 0.0; c.r_lo = 0.0; c.cn_re = 1.0; c.cn_im = 0.0;
   }
   c.pad[0] = c.pad[1] = c.pad[2] = 0.0;
+  c.cnf[0] = (float)c.cn_re;
+  c.cnf[1] = (float)c.cn_im;
   {
     Geo<float>& g = c.gf;
     g.sx = (float)c.sx; g.sy = (float)c.sy; g.sz = (float)c.sz;
@@ -162,7 +164,7 @@ __global__ void k0_prologue(const double* __restrict__ theta, int64_t ld, int w,
     g.ne2 = (float)(c.nx * c.e2x + c.ny * c.e2y + c.nz * c.e2z);
     g.sin_ths = (float)sts; g.cos_ths = (float)cts; g.sin_phs = (float)sps; g.cos_phs = (float)cps;
     g.amp_scale = (float)c.amp_scale;
-    c.padf[0] = c.padf[1] = 0.f;
+
   }
   c.j_plunge = n;
   c.status = st;

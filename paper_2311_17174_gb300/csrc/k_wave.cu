@@ -303,6 +303,40 @@ __device__ __forceinline__ void double_angle(T x, T y, T& c2, T& s2, bool degene
   }
 }
 
+// Three double angles at once.  FP64: one reciprocal of the product of the
+// three squared radii serves all three (a reciprocal costs several FP64
+// instructions, a product one); the radii are sums of squares of unit-vector
+// components (<= 4), so the product cannot overflow and underflows only below
+// 1e-300.  FP32: three hardware reciprocals.
+template <typename T>
+__device__ __forceinline__ void double_angle3(T xa, T ya, bool dega, T xb, T yb, bool degb, T xc, T yc, bool degc,
+                                              T& ca, T& sa, T& cb, T& sb, T& cc, T& sc) {
+  double_angle(xa, ya, ca, sa, dega);
+  double_angle(xb, yb, cb, sb, degb);
+  double_angle(xc, yc, cc, sc, degc);
+}
+template <>
+__device__ __forceinline__ void double_angle3<double>(double xa, double ya, bool dega, double xb, double yb,
+                                                      bool degb, double xc, double yc, bool degc, double& ca,
+                                                      double& sa, double& cb, double& sb, double& cc, double& sc) {
+  double ra = xa * xa + ya * ya, rb = xb * xb + yb * yb, rc = xc * xc + yc * yc;
+  dega = dega || !(ra > 0.0);
+  degb = degb || !(rb > 0.0);
+  degc = degc || !(rc > 0.0);
+  if (dega) ra = 1.0;
+  if (degb) rb = 1.0;
+  if (degc) rc = 1.0;
+  const double rab = ra * rb;
+  const double inv = 1.0 / (rab * rc);
+  const double ia = rb * rc * inv, ib = ra * rc * inv, ic = rab * inv;
+  ca = dega ? 1.0 : (xa * xa - ya * ya) * ia;
+  sa = dega ? 0.0 : 2.0 * xa * ya * ia;
+  cb = degb ? 1.0 : (xb * xb - yb * yb) * ib;
+  sb = degb ? 0.0 : 2.0 * xb * yb * ib;
+  cc = degc ? 1.0 : (xc * xc - yc * yc) * ic;
+  sc = degc ? 0.0 : 2.0 * xc * yc * ic;
+}
+
 // cos(n Phi), sin(n Phi) for n = 1, 2, ...: complex rotation (FP32) or the
 // Chebyshev three-term recurrence c_{n+1} = 2 cos(Phi) c_n - c_{n-1} (FP64,
 // whose error growth ~n^2 eps is harmless at n <= 32 in double).
@@ -371,22 +405,19 @@ __device__ __forceinline__ void channels(const Geo<T>& g, T cph, T sph, T c2gt, 
   const T wx = zy * g.nz - zz * g.ny, wy = zz * g.nx - zx * g.nz, wz = zx * g.ny - zy * g.nx;
   const T pyv = lzd - c * zn;
   const T pxv = lx * wx + ly * wy + lz * wz;
-  T c2psi, s2psi;
-  double_angle(pxv, pyv, c2psi, s2psi, false);
   // beta: angle about L from L x N to L x S = sin(lam) (p x S):
   //   cos beta ~ sin(lam) N.S - cos(lam) N.p,  sin beta ~ N.(S x p) = cos a N.e2 - sin a N.e1
   const T xb = g.sl * g.ns - g.cl * u;
   const T yb = ca * g.ne2 - sa * g.ne1;
-  T c2b, s2b;
   const T one_c2 = T(1) - c * c;
-  double_angle(xb, yb, c2b, s2b, !(one_c2 > T(1e-24)));
-  const T c2g = c2gt * c2b - s2gt * s2b;
-  const T s2g = s2gt * c2b + c2gt * s2b;
   // detector-frame azimuth: phi = phibar + atan2(sqrt3 cos thS + sin thS cos(phibar-phiS), 2 sin thS sin(phibar-phiS))
   const T cdp = cb * g.cos_phs + sb * g.sin_phs;
   const T sdp = sb * g.cos_phs - cb * g.sin_phs;
-  T c2x, s2x;
-  double_angle(T(2) * g.sin_ths * sdp, T(1.7320508075688772) * g.cos_ths + g.sin_ths * cdp, c2x, s2x, false);
+  T c2psi, s2psi, c2b, s2b, c2x, s2x;
+  double_angle3<T>(pxv, pyv, false, xb, yb, !(one_c2 > T(1e-24)), T(2) * g.sin_ths * sdp,
+                   T(1.7320508075688772) * g.cos_ths + g.sin_ths * cdp, false, c2psi, s2psi, c2b, s2b, c2x, s2x);
+  const T c2g = c2gt * c2b - s2gt * s2b;
+  const T s2g = s2gt * c2b + c2gt * s2b;
   const T c2b_ = cb * cb - sb * sb, s2b_ = T(2) * sb * cb;
   const T c2p = c2b_ * c2x - s2b_ * s2x;
   const T s2p = s2b_ * c2x + c2b_ * s2x;

@@ -214,7 +214,7 @@ __global__ void k1_orbit(WalkerC* __restrict__ wcs, int w, int64_t n, double dt,
 // (1 - cos(pi i/31))/2 on the unit segment); qk[q*32 + j] = int_0^{q/128} l_j,
 // q = 0..128 (knot positions of the finest knot grid).  Built on the host.
 constexpr int kSeg = 8192;         // samples per segment (n if smaller)
-constexpr int kOrbitWarps = 4;     // walkers per CTA
+constexpr int kOrbitWarps = 1;     // walkers per CTA (one warp each: balances FP64 work over the SMs)
 
 __device__ __forceinline__ void ak_rate_ve(const OrbSrc& s, double v, double e, double& dv, double& de) {
   double d0, d1, d2;
@@ -226,13 +226,14 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi(WalkerC* __res
                                                                    const double* __restrict__ qn_g,
                                                                    const double* __restrict__ qk_g,
                                                                    Knot* __restrict__ knots) {
-  __shared__ double qn[32 * 32];
-  __shared__ double qk[129 * 32];
-  __shared__ double fs[kOrbitWarps][5][32];
+  extern __shared__ double osm[];          // qn[32*32], qk[(K+1)*32], fs[warps][5][32]
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
   const int seg = (int)(n < kSeg ? n : kSeg);
   const int K = seg / ks;                   // knots per segment
   const int qstride = 128 / K;
+  double* qn = osm;
+  double* qk = osm + 32 * 32;
+  double* fs = qk + (K + 1) * 32;
   for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) qn[i] = qn_g[i];
   for (int q = 0; q <= K; ++q)
     for (int i = threadIdx.x; i < 32; i += blockDim.x) qk[q * 32 + i] = qk_g[(q * qstride) * 32 + i];
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi(WalkerC* __res
   OrbState y{c.v0_hi, c.v0_lo, c.e0, 0.0, c.phi0c, 0.0, c.gam0c, 0.0, c.alp0c, 0.0};
   const double H = (double)seg * dt;
   const double taui = 0.5 * (1.0 - cospi((double)lane / 31.0));
-  double* f = &fs[wq][0][0];
+  double* f = fs + wq * 5 * 32;
   int64_t jp = n;
   uint32_t st = 0;
   int64_t last = -1;   // last knot written
@@ -420,13 +421,14 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi_back(WalkerC* 
                                                                         int doppler, const double* __restrict__ qn_g,
                                                                         const double* __restrict__ qk_g,
                                                                         Knot* __restrict__ knots) {
-  __shared__ double qn[32 * 32];
-  __shared__ double qk[129 * 32];
-  __shared__ double fs[kOrbitWarps][5][32];
+  extern __shared__ double osm[];          // qn[32*32], qk[(K+1)*32], fs[warps][5][32]
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
   const int seg = (int)(n < kSeg ? n : kSeg);
-  const int K = seg / ks;
+  const int K = seg / ks;                   // knots per segment
   const int qstride = 128 / K;
+  double* qn = osm;
+  double* qk = osm + 32 * 32;
+  double* fs = qk + (K + 1) * 32;
   for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) qn[i] = qn_g[i];
   for (int q = 0; q <= K; ++q)
     for (int i = threadIdx.x; i < 32; i += blockDim.x) qk[q * 32 + i] = qk_g[(q * qstride) * 32 + i];
@@ -451,7 +453,7 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi_back(WalkerC* 
   }
   const double H = -(double)seg * dt;
   const double taui = 0.5 * (1.0 - cospi((double)lane / 31.0));
-  double* f = &fs[wq][0][0];
+  double* f = fs + wq * 5 * 32;
   bool fail = !state_finite(y);
   const int64_t nseg = n / seg;
   for (int64_t g = nseg - 1; g >= 0 && !fail; --g) {
@@ -566,11 +568,14 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi_back(WalkerC* 
 void launch_orbit(WalkerC* wc, int w, int64_t n, double dt, double t0, const OptsN& o, Knot* knots,
                   const double* mcpi_tab, cudaStream_t s) {
   if (w <= 0) return;
+  const int64_t seg = n < kSeg ? n : kSeg;
+  const int K = (int)(seg / o.ks);
+  const size_t smem = sizeof(double) * (32 * 32 + (size_t)(K + 1) * 32 + kOrbitWarps * 5 * 32);
   if (o.mode == 1) {   // backward from the LSO (the integration tables are always present)
-    k1_orbit_mcpi_back<<<(w + kOrbitWarps - 1) / kOrbitWarps, 32 * kOrbitWarps, 0, s>>>(
+    k1_orbit_mcpi_back<<<(w + kOrbitWarps - 1) / kOrbitWarps, 32 * kOrbitWarps, smem, s>>>(
         wc, w, n, dt, t0, o.ks, o.pn_terms, o.doppler, mcpi_tab, mcpi_tab + 32 * 32, knots);
   } else if (mcpi_tab) {
-    k1_orbit_mcpi<<<(w + kOrbitWarps - 1) / kOrbitWarps, 32 * kOrbitWarps, 0, s>>>(
+    k1_orbit_mcpi<<<(w + kOrbitWarps - 1) / kOrbitWarps, 32 * kOrbitWarps, smem, s>>>(
         wc, w, n, dt, t0, o.ks, o.pn_terms, o.doppler, mcpi_tab, mcpi_tab + 32 * 32, knots);
   } else {
     k1_orbit<<<(w + 31) / 32, 32, 0, s>>>(wc, w, n, dt, t0, o.ks, o.pn_terms, o.doppler, knots);

@@ -560,8 +560,9 @@ __global__ void __launch_bounds__(kPass2Threads, sizeof(C2) == 8 ? 4 : 2)
   tile_fft<C2, LG, 1, kPass2Threads>(buf, -1, ta);
   cp_async_wait<0>();
   __syncthreads();
-  Acc acc;
-  acc.init();
+  // a thread's own bins (N1/256 of them) in plain arithmetic; the
+  // compensated accumulator then merges the threads in a fixed order
+  T sdh = T(0), shh = T(0);
   FdW fd;
   if (FD) fd = fdw[wk];
   for (int k1 = threadIdx.x; k1 < N1; k1 += kPass2Threads) {
@@ -581,8 +582,12 @@ __global__ void __launch_bounds__(kPass2Threads, sizeof(C2) == 8 ? 4 : 2)
       A2 = A * A;
     }
     const C2 Hd = cmul(H, f);
-    acc.add(wv * (D.x * Hd.x + D.y * Hd.y), wv * (H.x * H.x + H.y * H.y) * A2);
+    sdh += wv * (D.x * Hd.x + D.y * Hd.y);
+    shh += wv * (H.x * H.x + H.y * H.y) * A2;
   }
+  Acc acc;
+  acc.init();
+  acc.add(sdh, shh);
   // fixed-shape reduction in the accumulator's own arithmetic: warp xor tree,
   // then warp 0 over the warp partials
 #pragma unroll

@@ -221,6 +221,22 @@ __device__ __forceinline__ void ak_rate_ve(const OrbSrc& s, double v, double e, 
   ak_rhs_v(s, v, e, dv, de, d0, d1, d2);
 }
 
+// Start values of (v, e) at this lane's node for the Picard sweeps.  The first
+// segment (or one after a serial fallback) starts from the Euler step; later
+// ones repeat the previous segment's converged increment at the same node,
+// scaled by the ratio of the start rates -- the rates change by ~H/tau_rr
+// (~1e-3) per segment, so the start error drops from ~(H/tau)^2 to ~(H/tau)^3
+// of the increment and the iteration needs about two sweeps fewer.  The
+// fixed point reached is the same.
+__device__ __forceinline__ void warm_start(bool warm, const OrbState& y, double H, double taui, double f0v,
+                                           double f0e, double dv_prev, double de_prev, double f0v_prev,
+                                           double f0e_prev, double& v, double& e) {
+  const bool wv = warm && f0v_prev != 0.0;
+  const bool we = warm && f0e_prev != 0.0;
+  v = y.v_hi + (y.v_lo + (wv ? dv_prev * (f0v / f0v_prev) : H * taui * f0v));
+  e = y.e_hi + (y.e_lo + (we ? de_prev * (f0e / f0e_prev) : H * taui * f0e));
+}
+
 __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi(WalkerC* __restrict__ wcs, int w, int64_t n, double dt,
                                                                    double t0, int ks, int pn, int doppler,
                                                                    const double* __restrict__ qn_g,
@@ -267,14 +283,16 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi(WalkerC* __res
     last = 0;
   }
   const int64_t nseg = n / seg;
+  bool warm = false;
+  double dv_prev = 0.0, de_prev = 0.0, f0v_prev = 0.0, f0e_prev = 0.0;
   for (int64_t g = 0; g < nseg && jp == n; ++g) {
     const OrbState ys = y;   // segment start
     const int64_t kbase = g * (int64_t)K;
-    // Euler start, then Picard sweeps on (v, e) at the nodes
+    // start values at the nodes, then Picard sweeps on (v, e)
     double f0v, f0e;
     ak_rate_ve(s, y.v_hi, y.e_hi, f0v, f0e);
-    double v = y.v_hi + (y.v_lo + H * taui * f0v);
-    double e = y.e_hi + (y.e_lo + H * taui * f0e);
+    double v, e;
+    warm_start(warm, y, H, taui, f0v, f0e, dv_prev, de_prev, f0v_prev, f0e_prev, v, e);
     bool convw = false;
     for (int it = 0; it < 30; ++it) {
       double fv, fe;
@@ -305,6 +323,12 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi(WalkerC* __res
     // a segment that reaches the LSO, or on which the iteration does not
     // settle, is integrated serially instead (fallback below)
     bool serial = !convw;
+    // this segment's node increments seed the next segment's start values
+    warm = convw;
+    dv_prev = v - (ys.v_hi + ys.v_lo);
+    de_prev = e - (ys.e_hi + ys.e_lo);
+    f0v_prev = f0v;
+    f0e_prev = f0e;
     if (!serial) {
       // all five rates at the nodes
       double r[5];
@@ -355,6 +379,7 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi(WalkerC* __res
     if (serial) {
       // lane 0 redoes the segment with the knot-step RK4 of k1_orbit from
       // the segment start; its knots replace any written above
+      warm = false;
       __syncwarp();
       int valid = 1;
       if (lane == 0) {
@@ -456,13 +481,15 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi_back(WalkerC* 
   double* f = fs + wq * 5 * 32;
   bool fail = !state_finite(y);
   const int64_t nseg = n / seg;
+  bool warm = false;
+  double dv_prev = 0.0, de_prev = 0.0, f0v_prev = 0.0, f0e_prev = 0.0;
   for (int64_t g = nseg - 1; g >= 0 && !fail; --g) {
     const OrbState ys = y;
     const int64_t kend = (g + 1) * (int64_t)K;   // knot at the segment's start (its latest time)
     double f0v, f0e;
     ak_rate_ve(s, y.v_hi, y.e_hi, f0v, f0e);
-    double v = y.v_hi + (y.v_lo + H * taui * f0v);
-    double e = y.e_hi + (y.e_lo + H * taui * f0e);
+    double v, e;
+    warm_start(warm, y, H, taui, f0v, f0e, dv_prev, de_prev, f0v_prev, f0e_prev, v, e);
     bool convw = false;
     for (int it = 0; it < 30; ++it) {
       double fv, fe;
@@ -490,6 +517,12 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi_back(WalkerC* 
       }
     }
     bool serial = !convw;
+    // this segment's node increments seed the next segment's start values
+    warm = convw;
+    dv_prev = v - (ys.v_hi + ys.v_lo);
+    de_prev = e - (ys.e_hi + ys.e_lo);
+    f0v_prev = f0v;
+    f0e_prev = f0e;
     if (!serial) {
       double r[5];
       ak_rhs_v(s, v, e, r[0], r[1], r[2], r[3], r[4]);
@@ -535,6 +568,7 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi_back(WalkerC* 
       serial = anybad;
     }
     if (serial) {
+      warm = false;
       __syncwarp();
       int valid = 1;
       if (lane == 0) {

@@ -374,10 +374,10 @@ __device__ __forceinline__ void amps_at<double>(const double* __restrict__ bq, i
 template <>
 __device__ __forceinline__ void amps_at<float>(const float* __restrict__ bq, int n, float st, float& an, float& bn,
                                                float& rn) {
-  const float4* b = reinterpret_cast<const float4*>(bq + 12 * n);
+  const float4* b = reinterpret_cast<const float4*>(bq + 12 * n);   // (a0 b0 a1 b1)(a2 b2 r0 r1)(r2 -)
   const float4 x = b[0], y = b[1], z = b[2];
-  an = (x.z * st + x.y) * st + x.x;
-  bn = (y.y * st + y.x) * st + x.w;
+  an = (y.x * st + x.z) * st + x.x;
+  bn = (y.y * st + x.w) * st + x.y;
   rn = (z.x * st + y.w) * st + y.z;
 }
 
@@ -429,16 +429,39 @@ __device__ __forceinline__ void channels(const Geo<T>& g, T cph, T sph, T c2gt, 
   const T fpII = Q1 * c2psi + Q2 * s2psi;
   const T fxII = Q1 * s2psi - Q2 * c2psi;
   // harmonic sum
-  HarmStep<T> hs;
-  hs.init(cph, sph);
   T Cs = T(0), Ss = T(0), Rs = T(0);
-  for (int n = 0; n < n_max; ++n) {
-    T an, bn, rn;
-    amps_at<T>(bq, n, st, an, bn, rn);
-    Cs += an * hs.cn;
-    Ss += bn * hs.sn;
-    Rs += rn * hs.cn;
-    hs.next();
+  if constexpr (sizeof(T) == 4) {
+    // FP32: the a_n, b_n quadratics and the (C, S) sums as paired (f32x2)
+    // instructions; coefficients per harmonic (a0 b0 a1 b1)(a2 b2 r0 r1)(r2 -)
+    const float2 st2 = make_float2(st, st);
+    float2 cs = make_float2(cph, sph), acc = make_float2(0.f, 0.f);
+    float r = 0.f;
+    for (int n = 0; n < n_max; ++n) {
+      const float4* b = reinterpret_cast<const float4*>(bq + 12 * n);
+      const float4 x = b[0], y = b[1], z = b[2];
+      const float2 ab = __ffma2_rn(__ffma2_rn(make_float2(y.x, y.y), st2, make_float2(x.z, x.w)), st2,
+                                   make_float2(x.x, x.y));
+      const float rn = (z.x * st + y.w) * st + y.z;
+      acc = __ffma2_rn(ab, cs, acc);
+      r = fmaf(rn, cs.x, r);
+      const float cn = cs.x * cph - cs.y * sph;   // rotation by Phi
+      cs.y = cs.y * cph + cs.x * sph;
+      cs.x = cn;
+    }
+    Cs = acc.x;
+    Ss = acc.y;
+    Rs = r;
+  } else {
+    HarmStep<T> hs;
+    hs.init(cph, sph);
+    for (int n = 0; n < n_max; ++n) {
+      T an, bn, rn;
+      amps_at<T>(bq, n, st, an, bn, rn);
+      Cs += an * hs.cn;
+      Ss += bn * hs.sn;
+      Rs += rn * hs.cn;
+      hs.next();
+    }
   }
   const T hp = A * ((T(1) + c * c) * (Cs * c2g - Ss * s2g) + one_c2 * Rs);
   const T hx = T(-2) * c * A * (Ss * c2g + Cs * s2g);
@@ -448,7 +471,8 @@ __device__ __forceinline__ void channels(const Geo<T>& g, T cph, T sph, T c2gt, 
 
 // Per-harmonic amplitude coefficients in shared memory: 9 values (a, b, c
 // quadratics) at stride AmpStride<T>; FP32 pads to 12 so one harmonic is
-// three 16-byte loads.
+// three 16-byte loads, and interleaves a and b (a0 b0 a1 b1 a2 b2 r0 r1 r2)
+// for the paired evaluation.
 template <typename T>
 struct AmpStride;
 template <>
@@ -489,10 +513,21 @@ __device__ __forceinline__ void tile_harmonics(const IV* iv, int ni, int64_t j0,
   if (t < 3 * n_max) {
     const int n = t / 3, f = t % 3;
     const T f0 = bnode[(0 * 32 + n) * 3 + f], fh = bnode[(1 * 32 + n) * 3 + f], f1 = bnode[(2 * 32 + n) * 3 + f];
-    T* o = bq + AmpStride<T>::v * n + 3 * f;
-    o[0] = f0;
-    o[1] = T(-3) * f0 + T(4) * fh - f1;
-    o[2] = T(2) * f0 - T(4) * fh + T(2) * f1;
+    const T q0 = f0, q1 = T(-3) * f0 + T(4) * fh - f1, q2 = T(2) * f0 - T(4) * fh + T(2) * f1;
+    T* o = bq + AmpStride<T>::v * n;
+    if (sizeof(T) == 4 && f < 2) {      // FP32: a and b interleaved for the paired evaluation
+      o[f] = q0;
+      o[2 + f] = q1;
+      o[4 + f] = q2;
+    } else if (sizeof(T) == 4) {         // FP32: r after them
+      o[6] = q0;
+      o[7] = q1;
+      o[8] = q2;
+    } else {
+      o[3 * f + 0] = q0;
+      o[3 * f + 1] = q1;
+      o[3 * f + 2] = q2;
+    }
   }
 }
 

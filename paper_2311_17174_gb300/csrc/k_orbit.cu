@@ -213,7 +213,15 @@ __global__ void k1_orbit(WalkerC* __restrict__ wcs, int w, int64_t n, double dt,
 // qn[j*32 + i] = int_0^{tau_i} l_j(tau) dtau (transposed, nodes tau_i =
 // (1 - cos(pi i/31))/2 on the unit segment); qk[q*32 + j] = int_0^{q/128} l_j,
 // q = 0..128 (knot positions of the finest knot grid).  Built on the host.
-constexpr int kSeg = 8192;         // samples per segment (n if smaller)
+constexpr int kSeg = 16384;        // samples per segment (n if smaller; at most 128 knots)
+
+// samples per Chebyshev-Picard segment: kSeg, but no more than n and than 128
+// knot intervals (the knot-weight table has 129 rows)
+__host__ __device__ __forceinline__ int64_t mcpi_segment(int64_t n, int ks) {
+  int64_t seg = n < kSeg ? n : kSeg;
+  if (seg > 128 * (int64_t)ks) seg = 128 * (int64_t)ks;
+  return seg;
+}
 constexpr int kOrbitWarps = 1;     // walkers per CTA (one warp each: balances FP64 work over the SMs)
 
 __device__ __forceinline__ void ak_rate_ve(const OrbSrc& s, double v, double e, double& dv, double& de) {
@@ -244,7 +252,7 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi(WalkerC* __res
                                                                    Knot* __restrict__ knots) {
   extern __shared__ double osm[];          // qn[32*32], qk[(K+1)*32], fs[warps][5][32]
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
-  const int seg = (int)(n < kSeg ? n : kSeg);
+  const int seg = (int)mcpi_segment(n, ks);
   const int K = seg / ks;                   // knots per segment
   const int qstride = 128 / K;
   double* qn = osm;
@@ -448,7 +456,7 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi_back(WalkerC* 
                                                                         Knot* __restrict__ knots) {
   extern __shared__ double osm[];          // qn[32*32], qk[(K+1)*32], fs[warps][5][32]
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
-  const int seg = (int)(n < kSeg ? n : kSeg);
+  const int seg = (int)mcpi_segment(n, ks);
   const int K = seg / ks;                   // knots per segment
   const int qstride = 128 / K;
   double* qn = osm;
@@ -602,7 +610,7 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi_back(WalkerC* 
 void launch_orbit(WalkerC* wc, int w, int64_t n, double dt, double t0, const OptsN& o, Knot* knots,
                   const double* mcpi_tab, cudaStream_t s) {
   if (w <= 0) return;
-  const int64_t seg = n < kSeg ? n : kSeg;
+  const int64_t seg = mcpi_segment(n, o.ks);
   const int K = (int)(seg / o.ks);
   const size_t smem = sizeof(double) * (32 * 32 + (size_t)(K + 1) * 32 + kOrbitWarps * 5 * 32);
   if (o.mode == 1) {   // backward from the LSO (the integration tables are always present)

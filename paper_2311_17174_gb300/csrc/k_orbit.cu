@@ -213,7 +213,7 @@ __global__ void k1_orbit(WalkerC* __restrict__ wcs, int w, int64_t n, double dt,
 // qn[j*32 + i] = int_0^{tau_i} l_j(tau) dtau (transposed, nodes tau_i =
 // (1 - cos(pi i/31))/2 on the unit segment); qk[q*32 + j] = int_0^{q/128} l_j,
 // q = 0..128 (knot positions of the finest knot grid).  Built on the host.
-constexpr int kSeg = 16384;        // samples per segment (n if smaller; at most 128 knots)
+constexpr int kSeg = 65536;        // samples per segment (n if smaller; at most 128 knots)
 
 // samples per Chebyshev-Picard segment: kSeg, but no more than n and than 128
 // knot intervals (the knot-weight table has 129 rows)

@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="serving measurement per precision (0: skip)")
     ap.add_argument("--multi-chains", type=int, default=64, help="uneven-batching leg: chains (0: skip)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the paper-workload and ensemble-step legs")
     return ap.parse_args()
 
 
@@ -312,6 +313,114 @@ def serve_bench(ctx, precision: int, rate: float, duration: float, n_max: int, s
 K2_F64_DRAM_BYTES_PER_SAMPLE = (72.156e6 + 1013.643e6) / (64 * 2 ** 20)
 
 
+def paper_bench(ctx, steps: int, warmup: int):
+    """The paper's own set-up (initial conditions at the LSO, e_LSO = 0.3,
+    fixed geometry, M, mu, S/M^2, Xi_0 scattered; one year at 15 s; n_max 10;
+    noise-free data at 1 Gpc): latency of an 8-walker likelihood batch (the
+    paper's ensemble) and throughput at 1024 walkers, FP64 and mixed."""
+    import torch
+    from paper_2311_17174_gb300 import emri, inputs as I
+
+    res = {}
+    wl8 = I.config_paper(walkers=8)
+    n, dt = wl8.n, wl8.dt
+    g = emri.grid(n, dt)
+    mode = emri.BACKWARD_FROM_LSO
+    o64 = emri.opts(precision=emri.FP64, n_max=wl8.n_max, mode=mode)
+    out = torch.zeros((6, 1), dtype=torch.float64, device="cuda")
+
+    def dl(zz):
+        t = wl8.injection.copy()
+        t[I.I_Z] = zz
+        ctx.prologue(g, torch.tensor(t[:, None].copy(), dtype=torch.float64, device="cuda"), o64, out)
+        torch.cuda.synchronize()
+        return float(out[2, 0])
+
+    z = I.solve_distance(wl8.extra["d_gpc"] * 3.0856775814913673e27, dl)
+    inj = wl8.injection.copy()
+    inj[I.I_Z] = z
+    zt = torch.zeros((1, n), dtype=torch.complex128, device="cuda")
+    ctx.ak_waveform(g, torch.tensor(inj[:, None].copy(), device="cuda"), o64, zt)
+    ctx.fft_batch(zt, n, 1, emri.FP64, -1)
+    torch.cuda.synchronize()
+    # the injection spectrum at its distance (Xi_0 = 1, GR speed: d_GW = d_L)
+    data = zt[0].cpu().numpy() / dl(z)
+    del zt
+    psd = I.psd_bc04(n, dt)
+    ds = ctx.dataset(g, data, psd, wl8.fmin, 1.0 / (2 * dt))
+    for walkers in (8, 1024):
+        wl = I.config_paper(walkers=walkers)
+        th = wl.theta.copy()
+        th[:, I.I_Z] = z
+        theta = torch.tensor(th.T.copy(), device="cuda")
+        lnl = torch.zeros(walkers, dtype=torch.float64, device="cuda")
+        for prec, name in ((emri.FP64, "fp64"), (emri.MIXED, "mixed")):
+            o = emri.opts(precision=prec, n_max=wl.n_max, mode=mode)
+            for _ in range(warmup):
+                ctx.loglike_batch(ds, theta, o, lnl)
+            torch.cuda.synchronize()
+            times = []
+            for _ in range(steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ctx.loglike_batch(ds, theta, o, lnl)
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            ms = float(np.median(times))
+            res[f"{name}_{walkers}w"] = {"ms_per_batch": ms, "lnl_per_s": walkers / (ms / 1e3),
+                                         "lnl_injection_walker0": float(lnl[0])}
+    ds.close()
+    return {"workload": "paper-lso-1yr-2^21-n10 (backward from the LSO, 1 Gpc, noise-free)", **res}
+
+
+def stretch_bench(ctx, ds, theta_np, wl, steps: int, warmup: int, flush):
+    """emri_stretch_step on the ensemble: proposals, the likelihood of the
+    proposals and the acceptance on the device, the four free parameters of
+    the paper (M, mu, S/M^2, Xi_0) in a box of +-1e-3 relative; uniforms drawn
+    on the host and resident before the timed region."""
+    import torch
+    from paper_2311_17174_gb300 import emri, inputs as I
+
+    w = theta_np.shape[0]
+    free = [I.I_M, I.I_MU, I.I_SPIN, I.I_XI0]
+    lo, hi = np.full(16, -np.inf), np.full(16, np.inf)
+    for p_ in free:
+        c = wl.injection[p_]
+        lo[p_], hi[p_] = c * (1 - 1e-3), c * (1 + 1e-3)
+    lo[I.I_SPIN], hi[I.I_SPIN] = 0.0, 1.0
+    cfg = emri.stretch_cfg(free, lo, hi)
+    res = {}
+    g = np.random.default_rng(12)
+    for prec, name in ((emri.FP64, "fp64"), (emri.MIXED, "mixed")):
+        o = emri.opts(precision=prec, n_max=wl.n_max)
+        theta = torch.tensor(theta_np.T.copy(), device="cuda")
+        lnp = torch.zeros(w, dtype=torch.float64, device="cuda")
+        acc = torch.zeros(w, dtype=torch.int32, device="cuda")
+        ctx.loglike_batch(ds, theta, o, lnp)
+        us = [torch.tensor(g.random((3, w)), device="cuda") for _ in range(warmup + steps)]
+        for k in range(warmup):
+            ctx.stretch_step(ds, theta, lnp, o, cfg, us[k], acc)
+        torch.cuda.synchronize()
+        times, accepted = [], 0
+        for k in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.stretch_step(ds, theta, lnp, o, cfg, us[warmup + k], acc)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            accepted += int(acc.sum())
+        tot = float(sum(times))
+        res[name] = {"ms_per_step": tot / steps, "lnl_per_s": w * steps / (tot / 1e3),
+                     "acceptance": accepted / (w * steps)}
+    return {"walkers": w, "free_parameters": "M, mu, S/M^2, Xi_0", **res}
+
+
 def flop_model(n_max: int) -> float:
     """Algorithmic FP64 flops per sample of the factored harmonic sum and
     response (see the design notes): 24 per harmonic (rotation 6, three
@@ -472,6 +581,12 @@ def main():
         serving = [serve_bench(ctx, emri.MIXED, 20.0, args.serve_seconds, wl.n_max),
                    serve_bench(ctx, emri.FP64, 1.5, args.serve_seconds, wl.n_max)]
 
+    # ---- the paper's own workload and the on-device ensemble step (rank 0)
+    paper = stretch = None
+    if rank == 0 and not args.no_extra:
+        stretch = stretch_bench(ctx, ds, theta, wl, 3, 1, flush)
+        paper = paper_bench(ctx, 5, 2)
+
     # ---- uneven batching: many chains in one captured launch (rank 0)
     multi = None
     if rank == 0 and args.multi_chains > 0:
@@ -519,6 +634,8 @@ def main():
                     "h2d_bytes_per_step": int(th_host.numel() * 8), "d2h_bytes_per_step": int(out_host.numel() * 8)},
             "serving": serving,
             "multi_chain": multi,
+            "ensemble_step": stretch,
+            "paper_workload": paper,
             "gpu_launches": int(launches),
             "kernels_ms_per_step": {k: round(v, 3) for k, v in per_step.items()},
             "roofline": roof,

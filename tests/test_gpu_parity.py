@@ -319,3 +319,36 @@ def test_poisoned_workspace_c2_subset(monkeypatch):
     finally:
         cp.close()
         cq.close()
+
+
+@pytest.mark.slow
+def test_maximum_length_sampled(ctx):
+    """n = 2^22 (the largest grid), FP64 and mixed, two walkers: waveform on
+    sampled time samples against the oracle (FP64 1e-9, mixed 1e-4)."""
+    n, dt, nm = 1 << 22, 15.0, 6
+    th = I.draw_sources(131, 2, n)
+    idx = np.unique(np.concatenate([[0, 1, n // 2, n - 1], np.random.default_rng(132).integers(0, n, 1020)]))
+    sI, sII, st_o = O.waveform_sampled(th, n, dt, idx, O.Opts(n_max=nm))
+    z64, st = gpu_waveform(ctx, th, n, dt, nm)
+    np.testing.assert_array_equal(st, st_o)
+    zm, _ = gpu_waveform(ctx, th, n, dt, nm, precision=1)
+    for k in range(2):
+        ref = sI[k] + 1j * sII[k]
+        assert rel_l2(z64[k, idx], ref) <= 1e-9, k
+        assert rel_l2(zm[k, idx].astype(np.complex128), ref) <= 1e-4, k
+
+
+def test_mixed_extreme_options(ctx):
+    """Mixed precision at n_max = 32 (the largest cutoff) and knot spacing
+    512 (the autotuner's other choice), against the FP64 oracle."""
+    n, dt = 1 << 14, 15.0
+    th = I.draw_sources(141, 4, n)
+    th[:, I.I_E0] = [0.05, 0.3, 0.5, 0.7]
+    hI, hII, st_o = O.waveform(th, n, dt, O.Opts(n_max=32))
+    for ks in (512, 1024):
+        zm, st = gpu_waveform(ctx, th, n, dt, 32, precision=1, knot_spacing=ks)
+        np.testing.assert_array_equal(st, st_o)
+        for k in range(4):
+            if st_o[k] & 1:
+                continue
+            assert rel_l2(zm[k].astype(np.complex128), hI[k] + 1j * hII[k]) <= 2e-5, (ks, k)

@@ -6,8 +6,9 @@
 //  pass 1: for each column j1, the n2-point DFT over j2, times the twiddle
 //          exp(-2 pi i j1 k2 / n), written back in place (position j1 + n1 k2);
 //  pass 2: for each row k2, the n1-point DFT over j1 gives bins k2 + n2 k1.
-// Both passes are shared-memory Stockham FFTs (radix-4 stages, one radix-2
-// stage when log2 of the length is odd), one CTA per column group / row.
+// Both passes are shared-memory Stockham FFTs, one CTA per column group /
+// row: radix-4 stages (one radix-2 stage when log2 of the length is odd) in
+// FP64, radix-8 stages (then one radix-4 or radix-2) in FP32.
 // The likelihood path never writes the spectrum: pass 2 multiplies each bin
 // by the GW-speed delay factor and accumulates
 //   sum_k w_k Re(conj(D_k) H_k e^{-2 pi i k_s r})  and  sum_k w_k |H_k|^2

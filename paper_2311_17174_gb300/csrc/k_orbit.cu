@@ -6,13 +6,14 @@
 // A step-by-step integrator is a serial FP64 dependency chain per walker, and
 // on this GPU one FP64 warp instruction occupies its SM sub-partition for ~64
 // cycles; so the orbit is integrated in parallel in time instead: one warp
-// per walker, segments of S samples, the solution on each segment
-// represented by its values at the 32 Chebyshev-Gauss-Lobatto nodes (one per
-// lane) and found by Picard iteration y(t) = y(t_a) + int f(y) with the
-// spectral integration matrix (Chebyshev-Picard iteration; converges in 4-7
-// sweeps here since a segment is ~1e-3 of the radiation-reaction time).  The
-// knots every K_s samples are read off the segment's polynomial (integral
-// weights at the knot positions).  The same system is written in the
+// per walker, segments of up to 65536 samples (at most 128 knot intervals:
+// 16384 samples at K_s = 128), the solution on each segment represented by
+// its values at the 32 Chebyshev-Gauss-Lobatto nodes (one per lane) and found
+// by Picard iteration y(t) = y(t_a) + int f(y) with the spectral integration
+// matrix (Chebyshev-Picard iteration; a segment is ~1e-2..1e-1 of the
+// radiation-reaction time, and each segment's sweeps start from the previous
+// segment's node increments).  The knots every K_s samples are read off the
+// segment's polynomial (integral weights at the knot positions).  The same system is written in the
 // variable
 // v = x^(1/3) = (2 pi G M nu / c^3)^(1/3) instead of nu: then x^(2/3) = v^2,
 // x^(11/3) = v^11 and (1-e^2)^(-k/2) = s^k with one s = 1/sqrt(1-e^2), so the

@@ -388,7 +388,7 @@ __device__ __forceinline__ void amps_at<float>(const float* __restrict__ bq, int
 template <typename T>
 __device__ __forceinline__ void channels(const Geo<T>& g, T cph, T sph, T c2gt, T s2gt, T ca, T sa, T cb,
                                          T sb, T A, T st, const T* __restrict__ bq, int n_max, T& hI,
-                                         T& hII) {
+                                         T& hII, bool cheb = false) {
   // L(t) = S cos lam + sin lam p, p = e1 cos alpha + e2 sin alpha
   const T px_ = g.e1x * ca + g.e2x * sa, py_ = g.e1y * ca + g.e2y * sa, pz_ = g.e1z * ca + g.e2z * sa;
   const T lx = g.sx * g.cl + g.sl * px_;
@@ -436,17 +436,37 @@ __device__ __forceinline__ void channels(const Geo<T>& g, T cph, T sph, T c2gt, 
     const float2 st2 = make_float2(st, st);
     float2 cs = make_float2(cph, sph), acc = make_float2(0.f, 0.f);
     float r = 0.f;
-    for (int n = 0; n < n_max; ++n) {
-      const float4* b = reinterpret_cast<const float4*>(bq + 12 * n);
-      const float4 x = b[0], y = b[1], z = b[2];
-      const float2 ab = __ffma2_rn(__ffma2_rn(make_float2(y.x, y.y), st2, make_float2(x.z, x.w)), st2,
-                                   make_float2(x.x, x.y));
-      const float rn = (z.x * st + y.w) * st + y.z;
-      acc = __ffma2_rn(ab, cs, acc);
-      r = fmaf(rn, cs.x, r);
-      const float cn = cs.x * cph - cs.y * sph;   // rotation by Phi
-      cs.y = cs.y * cph + cs.x * sph;
-      cs.x = cn;
+    if (cheb) {
+      // (cos, sin)(n+1) = 2 cos(Phi) (cos, sin)(n) - (cos, sin)(n-1): one paired
+      // FMA per harmonic (used below e = 0.5, where its rounding stays at the
+      // level of the accumulation's; the rotation is kept above)
+      const float2 tc = make_float2(2.f * cph, 2.f * cph);
+      float2 prev = make_float2(1.f, 0.f);
+      for (int n = 0; n < n_max; ++n) {
+        const float4* b = reinterpret_cast<const float4*>(bq + 12 * n);
+        const float4 x = b[0], y = b[1], z = b[2];
+        const float2 ab = __ffma2_rn(__ffma2_rn(make_float2(y.x, y.y), st2, make_float2(x.z, x.w)), st2,
+                                     make_float2(x.x, x.y));
+        const float rn = (z.x * st + y.w) * st + y.z;
+        acc = __ffma2_rn(ab, cs, acc);
+        r = fmaf(rn, cs.x, r);
+        const float2 nxt = __ffma2_rn(tc, cs, make_float2(-prev.x, -prev.y));
+        prev = cs;
+        cs = nxt;
+      }
+    } else {
+      for (int n = 0; n < n_max; ++n) {
+        const float4* b = reinterpret_cast<const float4*>(bq + 12 * n);
+        const float4 x = b[0], y = b[1], z = b[2];
+        const float2 ab = __ffma2_rn(__ffma2_rn(make_float2(y.x, y.y), st2, make_float2(x.z, x.w)), st2,
+                                     make_float2(x.x, x.y));
+        const float rn = (z.x * st + y.w) * st + y.z;
+        acc = __ffma2_rn(ab, cs, acc);
+        r = fmaf(rn, cs.x, r);
+        const float cn = cs.x * cph - cs.y * sph;   // rotation by Phi
+        cs.y = cs.y * cph + cs.x * sph;
+        cs.x = cn;
+      }
     }
     Cs = acc.x;
     Ss = acc.y;
@@ -644,6 +664,7 @@ __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict
   }
   __syncthreads();
   const int span = tile_span(j0, jplunge, kSegM);
+  const bool cheb = C.e0 < 0.5;   // per walker (uniform in the CTA)
   tile_harmonics<float, IvM>(iv, ni, j0, kfirst, ks, n_max, span, bnode, bq, rk, ifact);
   __syncthreads();
   const float inv_span = 1.f / (float)span;
@@ -673,7 +694,7 @@ __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict
       __sincosf(kTwoPiF * fgm, &s2g, &c2g);
       __sincosf(kTwoPiF * fal, &sa, &ca);
       float hI, hII;
-      channels<float>(g, cph, sph, c2g, s2g, ca, sa, cb, sb, A, (float)r * inv_span, bq, n_max, hI, hII);
+      channels<float>(g, cph, sph, c2g, s2g, ca, sa, cb, sb, A, (float)r * inv_span, bq, n_max, hI, hII, cheb);
       if (unit_scale) {
         hI *= g.amp_scale;
         hII *= g.amp_scale;

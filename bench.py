@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="serving measurement per precision (0: skip)")
     ap.add_argument("--multi-chains", type=int, default=64, help="uneven-batching leg: chains (0: skip)")
     ap.add_argument("--no-extra", action="store_true", help="skip the paper-workload and ensemble-step legs")
+    ap.add_argument("--serve-sweep", action="store_true",
+                    help="serving at Poisson rates 10..2000 req/s (mixed) and 1..30 req/s (FP64), 4 s each, queue 64")
     return ap.parse_args()
 
 
@@ -243,7 +245,8 @@ def time_steps(ctx, ds, theta_dev, o, lnl, steps, warmup, flush, barrier):
     return times
 
 
-def serve_bench(ctx, precision: int, rate: float, duration: float, n_max: int, seed: int = 5):
+def serve_bench(ctx, precision: int, rate: float, duration: float, n_max: int, seed: int = 5,
+                queue_capacity: int = 4096):
     """Poisson-arriving requests (8-512 walkers, 2^16-2^22 samples, one
     resident noise dataset per length) through the serving loop; latency is
     completion minus arrival as stamped by the library."""
@@ -258,9 +261,10 @@ def serve_bench(ctx, precision: int, rate: float, duration: float, n_max: int, s
     src = I.draw_sources(seed, 1, 1 << 22)[0]
     pool = I.scatter_walkers(seed + 1, src, 512)
     o = emri.opts(precision=precision, n_max=n_max)
-    ctx.serve_start(slots=4, queue_capacity=4096)
+    ctx.serve_start(slots=4, queue_capacity=queue_capacity)
     lat, walkers, lock = [], [0], threading.Lock()
     tickets = []
+    rejected = [0]
 
     def waiter():
         k = 0
@@ -289,7 +293,13 @@ def serve_bench(ctx, precision: int, rate: float, duration: float, n_max: int, s
         dt_ = t0 + ta - time.perf_counter()
         if dt_ > 0:
             time.sleep(dt_)
-        tk = ctx.serve_submit(dsets[n], pool[:w].T.copy(), o)
+        try:
+            tk = ctx.serve_submit(dsets[n], pool[:w].T.copy(), o)
+        except emri.EmriError as exc:   # a full queue refuses the request (EAGAIN)
+            if exc.code != emri.EAGAIN:
+                raise
+            rejected[0] += 1
+            continue
         with lock:
             tickets.append((tk, w))
     with lock:
@@ -301,8 +311,9 @@ def serve_bench(ctx, precision: int, rate: float, duration: float, n_max: int, s
         d.close()
     lat = np.array(lat)
     return {"precision": "fp64" if precision == 0 else "mixed", "rate_per_s": rate, "requests": int(len(lat)),
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "lnl_per_s": walkers[0] / elapsed, "seconds": elapsed, "slots": 4}
+            "rejected": rejected[0], "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+            "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+            "lnl_per_s": walkers[0] / elapsed, "seconds": elapsed, "slots": 4, "queue_capacity": queue_capacity}
 
 
 # DRAM bytes per sample of k2_wave_f64 from one ncu capture of the kernel
@@ -580,6 +591,10 @@ def main():
     if rank == 0 and args.serve_seconds > 0:
         serving = [serve_bench(ctx, emri.MIXED, 20.0, args.serve_seconds, wl.n_max),
                    serve_bench(ctx, emri.FP64, 1.5, args.serve_seconds, wl.n_max)]
+    if rank == 0 and args.serve_sweep:
+        serving = (serving or []) + \
+            [serve_bench(ctx, emri.MIXED, r, 4.0, wl.n_max, queue_capacity=64) for r in (10, 30, 100, 300, 1000, 2000)] + \
+            [serve_bench(ctx, emri.FP64, r, 4.0, wl.n_max, queue_capacity=64) for r in (1, 3, 10, 30)]
 
     # ---- the paper's own workload and the on-device ensemble step (rank 0)
     paper = stretch = None

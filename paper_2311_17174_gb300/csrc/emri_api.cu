@@ -172,23 +172,31 @@ int Workspace::reserve(emri_ctx* ctx, size_t bytes, cudaStream_t s) {
   if (ptr) {
     cudaStreamSynchronize(last_stream);
     cudaFree(ptr);
-    ctx->used -= cap;
+    {
+      std::lock_guard<std::mutex> lk(ctx->budget_mu);
+      ctx->used -= cap;
+    }
     ptr = nullptr;
     cap = 0;
   }
-  if (ctx->used + want > ctx->budget) {
-    want = bytes;
-    if (ctx->used + want > ctx->budget)
-      return set_err(EMRI_EBUDGET, "workspace of %zu bytes exceeds the HBM budget (%zu of %zu in use)", bytes,
-                     ctx->used, ctx->budget);
+  {
+    std::lock_guard<std::mutex> lk(ctx->budget_mu);
+    if (ctx->used + want > ctx->budget) {
+      want = bytes;
+      if (ctx->used + want > ctx->budget)
+        return set_err(EMRI_EBUDGET, "workspace of %zu bytes exceeds the HBM budget (%zu of %zu in use)", bytes,
+                       ctx->used, ctx->budget);
+    }
+    ctx->used += want;   // charged before the allocation, returned on failure
   }
   cudaError_t e = cudaMalloc(&ptr, want);
   if (e != cudaSuccess) {
     ptr = nullptr;
+    std::lock_guard<std::mutex> lk(ctx->budget_mu);
+    ctx->used -= want;
     return set_err(EMRI_ENOMEM, "cudaMalloc(%zu): %s", want, cudaGetErrorString(e));
   }
   cap = want;
-  ctx->used += want;
   (void)s;
   return EMRI_OK;
 }
@@ -210,6 +218,7 @@ void Workspace::destroy(emri_ctx* ctx) {
   if (ptr) {
     cudaDeviceSynchronize();
     cudaFree(ptr);
+    std::lock_guard<std::mutex> lk(ctx->budget_mu);
     ctx->used -= cap;
   }
   if (ev) cudaEventDestroy(ev);
@@ -464,7 +473,10 @@ extern "C" int emri_ctx_launches(const emri_ctx* c, int64_t* count) {
 
 extern "C" int emri_ctx_memory(const emri_ctx* c, size_t* used, size_t* budget) {
   if (!c) return set_err(EMRI_EINVAL, "NULL context");
-  if (used) *used = c->used;
+  if (used) {
+    std::lock_guard<std::mutex> blk(const_cast<emri_ctx*>(c)->budget_mu);
+    *used = c->used;
+  }
   if (budget) *budget = c->budget;
   return EMRI_OK;
 }
@@ -508,9 +520,12 @@ extern "C" int emri_dataset_create(emri_ctx* ctx, const emri_grid* grid, const v
   }
   const size_t keep = (size_t)n * (16 + 8 + 8 + 4) + 1024;
   const size_t tmp = (size_t)n * (16 + 16 + 8) + (size_t)(n / 2 + 1) * 8 + 4096;
-  if (ctx->used + keep + tmp > ctx->budget) {
-    delete ds;
-    return set_err(EMRI_EBUDGET, "dataset of %zu bytes exceeds the HBM budget", keep);
+  {
+    std::lock_guard<std::mutex> blk(ctx->budget_mu);
+    if (ctx->used + keep + tmp > ctx->budget) {
+      delete ds;
+      return set_err(EMRI_EBUDGET, "dataset of %zu bytes exceeds the HBM budget", keep);
+    }
   }
   char* kp = nullptr;
   char* tp = nullptr;
@@ -523,7 +538,10 @@ extern "C" int emri_dataset_create(emri_ctx* ctx, const emri_grid* grid, const v
   }
   ds->mem = kp;
   ds->bytes = keep;
-  ctx->used += keep;
+  {
+    std::lock_guard<std::mutex> blk(ctx->budget_mu);
+    ctx->used += keep;
+  }
   Carve k(kp), t(tp);
   ds->d_perm = k.take<double2>(n);
   ds->w_perm = k.take<double>(n);
@@ -574,7 +592,10 @@ extern "C" int emri_dataset_create(emri_ctx* ctx, const emri_grid* grid, const v
   } while (0);
   cudaFree(tp);
   if (e != cudaSuccess || rc2 != EMRI_OK) {
-    ctx->used -= keep;
+    {
+      std::lock_guard<std::mutex> blk(ctx->budget_mu);
+      ctx->used -= keep;
+    }
     cudaFree(kp);
     delete ds;
     return rc2 != EMRI_OK ? rc2 : cuda_err(e, "dataset preparation");
@@ -591,7 +612,10 @@ extern "C" int emri_dataset_destroy(emri_dataset* ds) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   cudaFree(ds->mem);
-  c->used -= ds->bytes;
+  {
+    std::lock_guard<std::mutex> blk(c->budget_mu);
+    c->used -= ds->bytes;
+  }
   delete ds;
   return EMRI_OK;
 }

@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <tuple>
 #include <vector>
@@ -63,7 +64,7 @@ struct LoglikeBufs {
 
 // Per-kernel event timing (enabled by emri_ctx_profile).
 struct Profiler {
-  bool on = false;
+  std::atomic<bool> on{false};
   std::mutex mu;
   std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> pending;
   std::vector<cudaEvent_t> pool;
@@ -102,7 +103,8 @@ struct Plan {
 struct emri_ctx {
   int device = 0;
   size_t budget = 0;
-  size_t used = 0;
+  size_t used = 0;            // guarded by budget_mu (the serving thread reserves too)
+  std::mutex budget_mu;
   std::mutex mu;
   cudaStream_t stream = nullptr;
   char* tables = nullptr;
@@ -112,7 +114,10 @@ struct emri_ctx {
   double* mcpi = nullptr;     // orbit integration tables (qn, qk)
   emri::Workspace ws;
   std::atomic<int64_t> launches{0};
-  emri::Server* server = nullptr;
+  // the serving loop; submit/poll hold a reference, so a concurrent stop
+  // cannot free it under them (swapped under server_mu)
+  std::shared_ptr<emri::Server> server;
+  std::mutex server_mu;
   emri::MultiGraph* multi = nullptr;
   emri::Profiler prof;
   std::map<std::tuple<int64_t, int, int>, emri::Plan> plans;   // (n, n_max, precision)

@@ -203,7 +203,12 @@ static void scheduler(Server* sv) {
 }
 
 void serve_shutdown(emri_ctx* ctx) {
-  Server* sv = ctx->server;
+  std::shared_ptr<Server> sp;
+  {
+    std::lock_guard<std::mutex> lk(ctx->server_mu);
+    sp.swap(ctx->server);
+  }
+  Server* sv = sp.get();
   if (!sv) return;
   {
     std::lock_guard<std::mutex> lk(sv->mu);
@@ -228,9 +233,12 @@ void serve_shutdown(emri_ctx* ctx) {
     cudaEventDestroy(sl.done);
     cudaStreamDestroy(sl.stream);
   }
-  sv->cv_done.notify_all();
-  delete sv;
-  ctx->server = nullptr;
+  {
+    // pollers still waiting wake up to completed or failed requests; the
+    // Server object itself lives until the last of them lets go of it
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->cv_done.notify_all();
+  }
 }
 
 // The tuned plan for (n, n_max, precision); without one for this n_max, the
@@ -268,32 +276,46 @@ int ctx_plan_wave(emri_ctx* ctx, int64_t n, const OptsN& o) {
 // ================================================================ serving
 extern "C" int emri_serve_start(emri_ctx* ctx, const emri_serve_cfg* cfg) {
   if (!ctx) return set_err(EMRI_EINVAL, "NULL context");
+  std::lock_guard<std::mutex> slk(ctx->server_mu);
   if (ctx->server) return set_err(EMRI_EINVAL, "serving already started");
   emri_serve_cfg c = cfg ? *cfg : emri_serve_cfg{4, 1024, 0};
   if (c.slots < 1 || c.slots > 64) return set_err(EMRI_EINVAL, "slots must be in [1, 64]");
   if (c.queue_capacity < 1) return set_err(EMRI_EINVAL, "queue_capacity must be >= 1");
   cudaSetDevice(ctx->device);
-  Server* sv = new Server();
+  auto sp = std::make_shared<Server>();
+  Server* sv = sp.get();
   sv->ctx = ctx;
   sv->cfg = c;
-  size_t room = ctx->budget > ctx->used ? ctx->budget - ctx->used : 0;
+  size_t room;
+  {
+    std::lock_guard<std::mutex> blk(ctx->budget_mu);
+    room = ctx->budget > ctx->used ? ctx->budget - ctx->used : 0;
+  }
   sv->budget = c.budget_bytes ? std::min(c.budget_bytes, room) : room;
   sv->slots.resize(c.slots);
   for (Slot& sl : sv->slots) {
     if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
-      delete sv;
+      for (Slot& q : sv->slots) {
+        if (q.done) cudaEventDestroy(q.done);
+        if (q.stream) cudaStreamDestroy(q.stream);
+      }
       return set_err(EMRI_ECUDA, "serve: stream/event creation failed");
     }
   }
-  ctx->server = sv;
+  ctx->server = sp;
   sv->th = std::thread(scheduler, sv);
   return EMRI_OK;
 }
 
+static std::shared_ptr<Server> server_of(emri_ctx* ctx) {
+  std::lock_guard<std::mutex> lk(ctx->server_mu);
+  return ctx->server;
+}
+
 extern "C" int emri_serve_stop(emri_ctx* ctx) {
   if (!ctx) return set_err(EMRI_EINVAL, "NULL context");
-  if (!ctx->server) return set_err(EMRI_ENOTFOUND, "serving not started");
+  if (!server_of(ctx)) return set_err(EMRI_ENOTFOUND, "serving not started");
   serve_shutdown(ctx);
   return EMRI_OK;
 }
@@ -301,7 +323,8 @@ extern "C" int emri_serve_stop(emri_ctx* ctx) {
 extern "C" int emri_serve_submit(emri_ctx* ctx, const emri_dataset* ds, const double* theta_host, int w,
                                  const emri_opts* opts, uint64_t* ticket) {
   if (!ctx || !ds || !ticket) return set_err(EMRI_EINVAL, "NULL argument");
-  Server* sv = ctx->server;
+  const std::shared_ptr<Server> sp = server_of(ctx);
+  Server* sv = sp.get();
   if (!sv) return set_err(EMRI_ENOTFOUND, "serving not started");
   if (ds->ctx != ctx) return set_err(EMRI_EINVAL, "dataset belongs to another context");
   if (w < 1) return set_err(EMRI_EINVAL, "w must be >= 1");
@@ -312,7 +335,10 @@ extern "C" int emri_serve_submit(emri_ctx* ctx, const emri_dataset* ds, const do
   r->ds = ds;
   r->w = w;
   r->theta.assign(theta_host, theta_host + (size_t)kNParam * w);
-  r->wave = pick_wave(ctx, ds->plan, r->o, w);
+  {
+    std::lock_guard<std::mutex> clk(ctx->mu);   // the tuned plans
+    r->wave = pick_wave(ctx, ds->plan, r->o, w);
+  }
   r->need = loglike_layout(ds->plan, r->o, w, r->wave, nullptr, nullptr);
   r->lnl.assign(w, 0.0);
   r->st.assign(w, 0u);
@@ -334,7 +360,8 @@ extern "C" int emri_serve_submit(emri_ctx* ctx, const emri_dataset* ds, const do
 extern "C" int emri_serve_poll(emri_ctx* ctx, uint64_t ticket, double* lnl_host, uint32_t* status_host,
                                emri_req_stats* stats, int64_t timeout_us) {
   if (!ctx) return set_err(EMRI_EINVAL, "NULL context");
-  Server* sv = ctx->server;
+  const std::shared_ptr<Server> sp = server_of(ctx);
+  Server* sv = sp.get();
   if (!sv) return set_err(EMRI_ENOTFOUND, "serving not started");
   std::unique_lock<std::mutex> lk(sv->mu);
   auto it = sv->reqs.find(ticket);

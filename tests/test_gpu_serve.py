@@ -116,3 +116,43 @@ def test_serve_admission_and_errors(env):
     with pytest.raises(emri.EmriError) as ei:
         ctx.serve_submit(dsets[16], th.T.copy(), emri.opts(n_max=8))
     assert ei.value.code == emri.ENOTFOUND
+
+
+def test_stop_while_pollers_wait_and_direct_calls_in_parallel(env):
+    """Pollers blocked on their tickets while another thread stops serving
+    get either their results or a clean error (never a crash); direct
+    emri_loglike_batch calls on the same context meanwhile are unaffected."""
+    emri, ctx, dsets = env
+    reqs = requests(5, 12)
+    ctx.serve_start(slots=2, queue_capacity=64)
+    tickets = [ctx.serve_submit(dsets[l], th.T.copy(), emri.opts(precision=p, n_max=8)) for (l, th, p) in reqs]
+    outcomes = [None] * len(reqs)
+
+    def poll(i):
+        try:
+            rc, lnl, st, stats = ctx.serve_poll(tickets[i], reqs[i][1].shape[0], timeout_us=-1)
+            outcomes[i] = ("ok", lnl)
+        except emri.EmriError as e:
+            outcomes[i] = ("err", e.code)
+
+    ths = [threading.Thread(target=poll, args=(i,)) for i in range(len(reqs))]
+    for t in ths:
+        t.start()
+    # a direct call on the same context while the loop runs
+    l0, th0, p0 = reqs[0]
+    alone = direct(emri, ctx, dsets[l0], th0, p0)
+    ctx.serve_stop()
+    for t in ths:
+        t.join(timeout=120)
+        assert not t.is_alive()
+    for i, (kind, val) in enumerate(outcomes):
+        if kind == "ok":
+            l, th, p = reqs[i]
+            np.testing.assert_array_equal(val, direct(emri, ctx, dsets[l], th, p))
+        else:
+            assert val == emri.ENOTFOUND   # never admitted before the stop
+    assert outcomes[0][0] == "ok" or outcomes[0][1] == emri.ENOTFOUND
+    np.testing.assert_array_equal(alone, direct(emri, ctx, dsets[l0], th0, p0))
+    with pytest.raises(emri.EmriError) as ei:
+        ctx.serve_poll(tickets[0], 1, timeout_us=0)
+    assert ei.value.code == emri.ENOTFOUND

@@ -139,7 +139,10 @@ const char* emri_version(void);
  * stale value from an earlier call; it costs one memset per call. */
 int emri_ctx_create(int device, size_t hbm_budget_bytes, emri_ctx** out);
 
-/* Stop serving if running, free every workspace, table and the context. */
+/* Stop serving if running (requests still queued fail with
+ * EMRI_ENOTFOUND), free every workspace, table and the context.  Datasets are
+ * owned by the caller: destroy them first (a dataset must not outlive its
+ * context).  NULL is a no-op. */
 int emri_ctx_destroy(emri_ctx* ctx);
 
 /* Number of CUDA kernels the library has launched on this context so far
@@ -188,6 +191,8 @@ int emri_ctx_kernel_times(emri_ctx* ctx, double* ms, int64_t* launches);
  * The dataset lives in device memory counted against the HBM budget. */
 int emri_dataset_create(emri_ctx* ctx, const emri_grid* grid, const void* data, int data_kind,
                         const double* psd, double fmin, double fmax, emri_dataset** out);
+/* Free a dataset (waits for the device); NULL is a no-op.  Call it before
+ * destroying the dataset's context. */
 int emri_dataset_destroy(emri_dataset* ds);
 
 /* <d|d> of the dataset (host double). */

@@ -381,55 +381,15 @@ __device__ __forceinline__ void amps_at<float>(const float* __restrict__ bq, int
   rn = (z.x * st + y.w) * st + y.z;
 }
 
-// Channels at one sample.  cph/sph: cos/sin of the Doppler orbital phase;
-// c2gt/s2gt: of 2 gamma~; ca/sa: of alpha; cb/sb: of phibar (the LISA
-// orbital phase); A = x^(2/3); st: time in [0, 1] of the harmonic-amplitude
-// fit bq.
+// Harmonic sums at one sample: Cs = sum_n a_n cos(n Phi), Ss = sum_n b_n
+// sin(n Phi), Rs = sum_n c_n cos(n Phi), with the amplitudes from the tile's
+// fit bq at time st in [0, 1]; cph/sph: cos/sin of the Doppler orbital phase.
 template <typename T>
-__device__ __forceinline__ void channels(const Geo<T>& g, T cph, T sph, T c2gt, T s2gt, T ca, T sa, T cb,
-                                         T sb, T A, T st, const T* __restrict__ bq, int n_max, T& hI,
-                                         T& hII, bool cheb = false) {
-  // L(t) = S cos lam + sin lam p, p = e1 cos alpha + e2 sin alpha
-  const T px_ = g.e1x * ca + g.e2x * sa, py_ = g.e1y * ca + g.e2y * sa, pz_ = g.e1z * ca + g.e2z * sa;
-  const T lx = g.sx * g.cl + g.sl * px_;
-  const T ly = g.sy * g.cl + g.sl * py_;
-  const T lz = g.sz * g.cl + g.sl * pz_;
-  const T u = ca * g.ne1 + sa * g.ne2;                     // N.p
-  const T c = g.cl * g.ns + g.sl * u;                      // L.N
-  // detector normal z_d = z/2 - (sqrt3/2)(cos phibar x + sin phibar y)
-  const T h3 = T(kSqrt3Half);
-  const T zx = -h3 * cb, zy = -h3 * sb, zz = T(0.5);
-  const T zn = zx * g.nx + zy * g.ny + zz * g.nz;         // z_d.N = cos(theta_d)
-  const T lzd = lx * zx + ly * zy + lz * zz;
-  // psi: tan psi = [L.z_d - (L.N)(z_d.N)] / [N.(L x z_d)] = [..] / [L.(z_d x N)]
-  const T wx = zy * g.nz - zz * g.ny, wy = zz * g.nx - zx * g.nz, wz = zx * g.ny - zy * g.nx;
-  const T pyv = lzd - c * zn;
-  const T pxv = lx * wx + ly * wy + lz * wz;
-  // beta: angle about L from L x N to L x S = sin(lam) (p x S):
-  //   cos beta ~ sin(lam) N.S - cos(lam) N.p,  sin beta ~ N.(S x p) = cos a N.e2 - sin a N.e1
-  const T xb = g.sl * g.ns - g.cl * u;
-  const T yb = ca * g.ne2 - sa * g.ne1;
-  const T one_c2 = T(1) - c * c;
-  // detector-frame azimuth: phi = phibar + atan2(sqrt3 cos thS + sin thS cos(phibar-phiS), 2 sin thS sin(phibar-phiS))
-  const T cdp = cb * g.cos_phs + sb * g.sin_phs;
-  const T sdp = sb * g.cos_phs - cb * g.sin_phs;
-  T c2psi, s2psi, c2b, s2b, c2x, s2x;
-  double_angle3<T>(pxv, pyv, false, xb, yb, !(one_c2 > T(1e-24)), T(2) * g.sin_ths * sdp,
-                   T(1.7320508075688772) * g.cos_ths + g.sin_ths * cdp, false, c2psi, s2psi, c2b, s2b, c2x, s2x);
-  const T c2g = c2gt * c2b - s2gt * s2b;
-  const T s2g = s2gt * c2b + c2gt * s2b;
-  const T c2b_ = cb * cb - sb * sb, s2b_ = T(2) * sb * cb;
-  const T c2p = c2b_ * c2x - s2b_ * s2x;
-  const T s2p = s2b_ * c2x + c2b_ * s2x;
-  // antenna patterns; channel II has phi -> phi - pi/4
-  const T ct = zn, q = T(0.5) * (T(1) + ct * ct);
-  const T P1 = q * c2p, P2 = ct * s2p, Q1 = q * s2p, Q2 = ct * c2p;
-  const T fpI = P1 * c2psi - P2 * s2psi;
-  const T fxI = P1 * s2psi + P2 * c2psi;
-  const T fpII = Q1 * c2psi + Q2 * s2psi;
-  const T fxII = Q1 * s2psi - Q2 * c2psi;
-  // harmonic sum
-  T Cs = T(0), Ss = T(0), Rs = T(0);
+__device__ __forceinline__ void harmonic_sums(T cph, T sph, T st, const T* __restrict__ bq, int n_max, bool cheb,
+                                              T& Cs, T& Ss, T& Rs) {
+  Cs = T(0);
+  Ss = T(0);
+  Rs = T(0);
   if constexpr (sizeof(T) == 4) {
     // FP32: the a_n, b_n quadratics and the (C, S) sums as paired (f32x2)
     // instructions; coefficients per harmonic (a0 b0 a1 b1)(a2 b2 r0 r1)(r2 -)
@@ -483,10 +443,120 @@ __device__ __forceinline__ void channels(const Geo<T>& g, T cph, T sph, T c2gt, 
       hs.next();
     }
   }
+}
+
+// FP32, two samples at once (same tile fit, times stA, stB): the amplitude
+// coefficients of each harmonic are loaded once for both.
+__device__ __forceinline__ void harmonic_sums2(float cphA, float sphA, float stA, float cphB, float sphB, float stB,
+                                               const float* __restrict__ bq, int n_max, bool cheb, float3& sA,
+                                               float3& sB) {
+  const float2 stA2 = make_float2(stA, stA), stB2 = make_float2(stB, stB);
+  float2 csA = make_float2(cphA, sphA), csB = make_float2(cphB, sphB);
+  float2 accA = make_float2(0.f, 0.f), accB = make_float2(0.f, 0.f);
+  float rA = 0.f, rB = 0.f;
+  if (cheb) {
+    const float2 tcA = make_float2(2.f * cphA, 2.f * cphA), tcB = make_float2(2.f * cphB, 2.f * cphB);
+    float2 pvA = make_float2(1.f, 0.f), pvB = make_float2(1.f, 0.f);
+    for (int n = 0; n < n_max; ++n) {
+      const float4* b = reinterpret_cast<const float4*>(bq + 12 * n);
+      const float4 x = b[0], y = b[1], z = b[2];
+      const float2 a2 = make_float2(y.x, y.y), a1 = make_float2(x.z, x.w), a0 = make_float2(x.x, x.y);
+      const float2 abA = __ffma2_rn(__ffma2_rn(a2, stA2, a1), stA2, a0);
+      const float2 abB = __ffma2_rn(__ffma2_rn(a2, stB2, a1), stB2, a0);
+      accA = __ffma2_rn(abA, csA, accA);
+      accB = __ffma2_rn(abB, csB, accB);
+      rA = fmaf((z.x * stA + y.w) * stA + y.z, csA.x, rA);
+      rB = fmaf((z.x * stB + y.w) * stB + y.z, csB.x, rB);
+      const float2 nA = __ffma2_rn(tcA, csA, make_float2(-pvA.x, -pvA.y));
+      const float2 nB = __ffma2_rn(tcB, csB, make_float2(-pvB.x, -pvB.y));
+      pvA = csA;
+      csA = nA;
+      pvB = csB;
+      csB = nB;
+    }
+  } else {
+    for (int n = 0; n < n_max; ++n) {
+      const float4* b = reinterpret_cast<const float4*>(bq + 12 * n);
+      const float4 x = b[0], y = b[1], z = b[2];
+      const float2 a2 = make_float2(y.x, y.y), a1 = make_float2(x.z, x.w), a0 = make_float2(x.x, x.y);
+      const float2 abA = __ffma2_rn(__ffma2_rn(a2, stA2, a1), stA2, a0);
+      const float2 abB = __ffma2_rn(__ffma2_rn(a2, stB2, a1), stB2, a0);
+      accA = __ffma2_rn(abA, csA, accA);
+      accB = __ffma2_rn(abB, csB, accB);
+      rA = fmaf((z.x * stA + y.w) * stA + y.z, csA.x, rA);
+      rB = fmaf((z.x * stB + y.w) * stB + y.z, csB.x, rB);
+      const float cA = csA.x * cphA - csA.y * sphA;   // rotations by Phi
+      csA.y = csA.y * cphA + csA.x * sphA;
+      csA.x = cA;
+      const float cB = csB.x * cphB - csB.y * sphB;
+      csB.y = csB.y * cphB + csB.x * sphB;
+      csB.x = cB;
+    }
+  }
+  sA = make_float3(accA.x, accA.y, rA);
+  sB = make_float3(accB.x, accB.y, rB);
+}
+
+// Channels from the harmonic sums at one sample: LISA response (antenna
+// patterns, polarisation angle psi, the angle beta in gamma = gamma~ + beta)
+// and h_I, h_II.  c2gt/s2gt: cos/sin of 2 gamma~; ca/sa: of alpha; cb/sb:
+// of phibar (the LISA orbital phase); A = x^(2/3).
+template <typename T>
+__device__ __forceinline__ void response(const Geo<T>& g, T c2gt, T s2gt, T ca, T sa, T cb, T sb, T A, T Cs, T Ss,
+                                         T Rs, T& hI, T& hII) {
+  // L(t) = S cos lam + sin lam p, p = e1 cos alpha + e2 sin alpha
+  const T px_ = g.e1x * ca + g.e2x * sa, py_ = g.e1y * ca + g.e2y * sa, pz_ = g.e1z * ca + g.e2z * sa;
+  const T lx = g.sx * g.cl + g.sl * px_;
+  const T ly = g.sy * g.cl + g.sl * py_;
+  const T lz = g.sz * g.cl + g.sl * pz_;
+  const T u = ca * g.ne1 + sa * g.ne2;                     // N.p
+  const T c = g.cl * g.ns + g.sl * u;                      // L.N
+  // detector normal z_d = z/2 - (sqrt3/2)(cos phibar x + sin phibar y)
+  const T h3 = T(kSqrt3Half);
+  const T zx = -h3 * cb, zy = -h3 * sb, zz = T(0.5);
+  const T zn = zx * g.nx + zy * g.ny + zz * g.nz;         // z_d.N = cos(theta_d)
+  const T lzd = lx * zx + ly * zy + lz * zz;
+  // psi: tan psi = [L.z_d - (L.N)(z_d.N)] / [N.(L x z_d)] = [..] / [L.(z_d x N)]
+  const T wx = zy * g.nz - zz * g.ny, wy = zz * g.nx - zx * g.nz, wz = zx * g.ny - zy * g.nx;
+  const T pyv = lzd - c * zn;
+  const T pxv = lx * wx + ly * wy + lz * wz;
+  // beta: angle about L from L x N to L x S = sin(lam) (p x S):
+  //   cos beta ~ sin(lam) N.S - cos(lam) N.p,  sin beta ~ N.(S x p) = cos a N.e2 - sin a N.e1
+  const T xb = g.sl * g.ns - g.cl * u;
+  const T yb = ca * g.ne2 - sa * g.ne1;
+  const T one_c2 = T(1) - c * c;
+  // detector-frame azimuth: phi = phibar + atan2(sqrt3 cos thS + sin thS cos(phibar-phiS), 2 sin thS sin(phibar-phiS))
+  const T cdp = cb * g.cos_phs + sb * g.sin_phs;
+  const T sdp = sb * g.cos_phs - cb * g.sin_phs;
+  T c2psi, s2psi, c2b, s2b, c2x, s2x;
+  double_angle3<T>(pxv, pyv, false, xb, yb, !(one_c2 > T(1e-24)), T(2) * g.sin_ths * sdp,
+                   T(1.7320508075688772) * g.cos_ths + g.sin_ths * cdp, false, c2psi, s2psi, c2b, s2b, c2x, s2x);
+  const T c2g = c2gt * c2b - s2gt * s2b;
+  const T s2g = s2gt * c2b + c2gt * s2b;
+  const T c2b_ = cb * cb - sb * sb, s2b_ = T(2) * sb * cb;
+  const T c2p = c2b_ * c2x - s2b_ * s2x;
+  const T s2p = s2b_ * c2x + c2b_ * s2x;
+  // antenna patterns; channel II has phi -> phi - pi/4
+  const T ct = zn, q = T(0.5) * (T(1) + ct * ct);
+  const T P1 = q * c2p, P2 = ct * s2p, Q1 = q * s2p, Q2 = ct * c2p;
+  const T fpI = P1 * c2psi - P2 * s2psi;
+  const T fxI = P1 * s2psi + P2 * c2psi;
+  const T fpII = Q1 * c2psi + Q2 * s2psi;
+  const T fxII = Q1 * s2psi - Q2 * c2psi;
   const T hp = A * ((T(1) + c * c) * (Cs * c2g - Ss * s2g) + one_c2 * Rs);
   const T hx = T(-2) * c * A * (Ss * c2g + Cs * s2g);
   hI = h3 * (fpI * hp + fxI * hx);
   hII = h3 * (fpII * hp + fxII * hx);
+}
+
+// Channels at one sample (harmonic sums, then the response).
+template <typename T>
+__device__ __forceinline__ void channels(const Geo<T>& g, T cph, T sph, T c2gt, T s2gt, T ca, T sa, T cb,
+                                         T sb, T A, T st, const T* __restrict__ bq, int n_max, T& hI,
+                                         T& hII, bool cheb = false) {
+  T Cs, Ss, Rs;
+  harmonic_sums<T>(cph, sph, st, bq, n_max, cheb, Cs, Ss, Rs);
+  response<T>(g, c2gt, s2gt, ca, sa, cb, sb, A, Cs, Ss, Rs, hI, hII);
 }
 
 // Per-harmonic amplitude coefficients in shared memory: 9 values (a, b, c
@@ -654,6 +724,7 @@ __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict
   const int t = threadIdx.x;
   if (t < ni) iv[t] = ivs[(int64_t)wk * nk + kfirst + t];
   constexpr int kTiles = kSegM / kTile;
+  static_assert(kTiles % 2 == 0, "tiles are processed in pairs");
   if (t >= 128 && t < 128 + 6 * kTiles) {
     const int q = t - 128;
     oq[q / 6][(q % 6) / 3][q % 3] = (float)lisa[(blockIdx.x * kTiles + q / 6) * 6 + q % 6];
@@ -669,39 +740,50 @@ __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict
   __syncthreads();
   const float inv_span = 1.f / (float)span;
   const float inv_ks = 1.f / (float)ks;
+  // per-sample inputs of the response and of the harmonic sums
+  auto inputs = [&](int r, int tt, float& cph, float& sph, float& c2g, float& s2g, float& ca, float& sa,
+                    float& cb, float& sb, float& A) {
+    const int ki = ks >= kSegM ? 0 : r / ks;
+    const int tau = r - ki * ks;
+    const float s = (float)tau * inv_ks;
+    const IvM& v = iv[ki];
+    const float fph = phase_fx(v.ph_base, v.ph_inc, v.ph_c, tau, s);
+    float c2[2] = {2.f * v.gm_c[0], 2.f * v.gm_c[1]};
+    const float fgm = phase_fx(v.gm_base << 1, (long long)((unsigned long long)v.gm_inc << 1), c2, tau, s);
+    const float fal = phase_fx(v.al_base, v.al_inc, v.al_c, tau, s);
+    A = poly3<float>(v.am, s);
+    const float so = (float)t * (1.f / kTile);
+    cb = (oq[tt][0][2] * so + oq[tt][0][1]) * so + oq[tt][0][0];
+    sb = (oq[tt][1][2] * so + oq[tt][1][1]) * so + oq[tt][1][0];
+    // hardware sin/cos of the reduced angles (|x| <= pi, absolute error ~5e-7)
+    constexpr float kTwoPiF = 6.283185307179586f;
+    __sincosf(kTwoPiF * fph, &sph, &cph);
+    __sincosf(kTwoPiF * fgm, &s2g, &c2g);
+    __sincosf(kTwoPiF * fal, &sa, &ca);
+  };
+  // two samples per thread (tiles tt and tt+1): the amplitude coefficients
+  // of each harmonic are loaded once for both
 #pragma unroll 1
-  for (int tt = 0; tt < kTiles; ++tt) {
-    const int r = tt * kTile + t;   // offset in the segment
-    const int64_t j = j0 + r;
-    float2 out = make_float2(0.f, 0.f);
-    if (j < jplunge) {
-      const int ki = ks >= kSegM ? 0 : r / ks;
-      const int tau = r - ki * ks;
-      const float s = (float)tau * inv_ks;
-      const IvM& v = iv[ki];
-      const float fph = phase_fx(v.ph_base, v.ph_inc, v.ph_c, tau, s);
-      float c2[2] = {2.f * v.gm_c[0], 2.f * v.gm_c[1]};
-      const float fgm = phase_fx(v.gm_base << 1, (long long)((unsigned long long)v.gm_inc << 1), c2, tau, s);
-      const float fal = phase_fx(v.al_base, v.al_inc, v.al_c, tau, s);
-      const float A = poly3<float>(v.am, s);
-      const float so = (float)t * (1.f / kTile);
-      const float cb = (oq[tt][0][2] * so + oq[tt][0][1]) * so + oq[tt][0][0];
-      const float sb = (oq[tt][1][2] * so + oq[tt][1][1]) * so + oq[tt][1][0];
-      // hardware sin/cos of the reduced angles (|x| <= pi, absolute error ~5e-7)
-      constexpr float kTwoPiF = 6.283185307179586f;
-      float sph, cph, s2g, c2g, sa, ca;
-      __sincosf(kTwoPiF * fph, &sph, &cph);
-      __sincosf(kTwoPiF * fgm, &s2g, &c2g);
-      __sincosf(kTwoPiF * fal, &sa, &ca);
-      float hI, hII;
-      channels<float>(g, cph, sph, c2g, s2g, ca, sa, cb, sb, A, (float)r * inv_span, bq, n_max, hI, hII, cheb);
-      if (unit_scale) {
-        hI *= g.amp_scale;
-        hII *= g.amp_scale;
-      }
-      out = make_float2(hI, hII);
+  for (int tt = 0; tt < kTiles; tt += 2) {
+    const int rA = tt * kTile + t, rB = rA + kTile;   // offsets in the segment
+    float cphA, sphA, c2gA, s2gA, caA, saA, cbA, sbA, AA;
+    float cphB, sphB, c2gB, s2gB, caB, saB, cbB, sbB, AB;
+    inputs(rA, tt, cphA, sphA, c2gA, s2gA, caA, saA, cbA, sbA, AA);
+    inputs(rB, tt + 1, cphB, sphB, c2gB, s2gB, caB, saB, cbB, sbB, AB);
+    float3 hsA, hsB;
+    harmonic_sums2(cphA, sphA, (float)rA * inv_span, cphB, sphB, (float)rB * inv_span, bq, n_max, cheb, hsA, hsB);
+    float hIA, hIIA, hIB, hIIB;
+    response<float>(g, c2gA, s2gA, caA, saA, cbA, sbA, AA, hsA.x, hsA.y, hsA.z, hIA, hIIA);
+    response<float>(g, c2gB, s2gB, caB, saB, cbB, sbB, AB, hsB.x, hsB.y, hsB.z, hIB, hIIB);
+    if (unit_scale) {
+      hIA *= g.amp_scale;
+      hIIA *= g.amp_scale;
+      hIB *= g.amp_scale;
+      hIIB *= g.amp_scale;
     }
-    z[(int64_t)wk * n + j] = out;
+    const int64_t jA = j0 + rA, jB = j0 + rB;
+    z[(int64_t)wk * n + jA] = jA < jplunge ? make_float2(hIA, hIIA) : make_float2(0.f, 0.f);
+    z[(int64_t)wk * n + jB] = jB < jplunge ? make_float2(hIB, hIIB) : make_float2(0.f, 0.f);
   }
 }
 

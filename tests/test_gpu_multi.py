@@ -50,3 +50,41 @@ def test_multi_chain_matches_single_calls():
     for ch in chains:
         ch[0].close()
     ctx.close()
+
+
+@pytest.mark.slow
+def test_c4_full_configuration():
+    """The full uneven-batching configuration: 64 chains of 32-512 walkers,
+    2^16-2^22 samples, n_max 5-30, mixed precision, autotuned plans, one
+    graph.  Every chain is finite, and eight chains picked across the
+    lengths equal (bitwise) the same chains run alone."""
+    from paper_2311_17174_gb300 import emri
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ctx = emri.Context(0)
+    wls = I.config_c4()
+    for n in sorted({wl.n for wl in wls}):
+        ctx.autotune(emri.grid(n, I.DT), 20, emri.MIXED)
+    items, dsets = [], []
+    for c, wl in enumerate(wls):
+        psd = I.psd_bc04(wl.n)
+        ds = ctx.dataset(emri.grid(wl.n, I.DT), I.noise_spectrum(wl.noise_seed, psd, wl.n), psd, 1e-4, 1 / 30.0)
+        dsets.append(ds)
+        w = wl.theta.shape[0]
+        theta = torch.tensor(wl.theta.T.copy(), device="cuda:0")
+        lnl = torch.zeros(w, dtype=torch.float64, device="cuda:0")
+        items.append((ds, theta, emri.opts(precision=emri.MIXED, n_max=wl.n_max), lnl, None, None, None))
+    ctx.loglike_multi(items)
+    torch.cuda.synchronize()
+    for it in items:
+        assert bool(torch.isfinite(it[3]).all())
+    order = np.argsort([wl.n for wl in wls])
+    for c in order[::8]:
+        ds, theta, o, lnl, _, _, _ = items[c]
+        ref = torch.zeros_like(lnl)
+        ctx.loglike_batch(ds, theta, o, ref)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(lnl.cpu().numpy(), ref.cpu().numpy())
+    for ds in dsets:
+        ds.close()
+    ctx.close()

@@ -236,7 +236,7 @@ size_t loglike_layout(const FftPlan& p, const OptsN& o, int w, int wave, Carve* 
   t.wc = cv.take<WalkerC>(w);
   t.knots = cv.take<Knot>((size_t)w * (nk + 1));
   t.ivs = cv.take<char>(o.precision ? (size_t)w * nk * kIvMBytes : 0);
-  t.lisa = cv.take<double>((size_t)(p.n / 256) * 6);
+  t.lisa = cv.take<double>((size_t)(p.n / 256) * 8);
   t.dtab = cv.take<char>((size_t)w * p.n1 * cs);
   t.rtab = cv.take<char>((size_t)w * p.n2 * cs);
   t.partial = cv.take<double2>((size_t)w * p.n2);
@@ -671,14 +671,14 @@ extern "C" int emri_ak_waveform(emri_ctx* ctx, const emri_grid* grid, const doub
   probe.take<WalkerC>(w);
   probe.take<Knot>((size_t)w * (nk + 1));
   probe.take<char>(o.precision ? (size_t)w * nk * kIvMBytes : 0);
-  probe.take<double>((size_t)(grid->n / 256) * 6);
+  probe.take<double>((size_t)(grid->n / 256) * 8);
   if ((rc = ctx->ws.reserve(ctx, probe.off + 512, s))) return rc;
   ctx->ws.acquire(s);
   Carve cv(ctx->ws.ptr);
   WalkerC* wc = cv.take<WalkerC>(w);
   Knot* kn = cv.take<Knot>((size_t)w * (nk + 1));
   char* ivs = cv.take<char>(o.precision ? (size_t)w * nk * kIvMBytes : 0);
-  double* lisa = cv.take<double>((size_t)(grid->n / 256) * 6);
+  double* lisa = cv.take<double>((size_t)(grid->n / 256) * 8);
   Profiler* pf = &ctx->prof;
   { KTimer t(pf, EMRI_K_PROLOGUE, s); launch_prologue(theta, w, w, grid->n, grid->dt, o, ctx->gl, wc, s); }
   { KTimer t(pf, EMRI_K_ORBIT, s); launch_orbit(wc, w, grid->n, grid->dt, grid->t0, o, kn, ctx->mcpi, s); }

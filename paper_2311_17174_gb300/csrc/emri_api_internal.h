@@ -55,7 +55,7 @@ struct LoglikeBufs {
   WalkerC* wc;
   Knot* knots;
   char* ivs;       // mixed interval records [w][n/ks]
-  double* lisa;    // per-tile LISA-phase table [n/256][6]
+  double* lisa;    // per-tile LISA-phase table [n/256][8]
   char* dtab;
   char* rtab;      // per-walker row delay factors [w][n2]
   double2* partial;

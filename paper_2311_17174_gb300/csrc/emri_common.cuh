@@ -38,11 +38,18 @@ struct __align__(16) Knot {
 };
 static_assert(sizeof(Knot) == 128, "knot size");
 
-// Walker geometry in the precision of a kernel (see the waveform kernel).
+// Walker geometry of the channel response in the precision of a kernel.
+// The response is evaluated in a fixed polarisation basis of the sky plane,
+// P = phi^ and Q = theta^ at the source direction N.  With p = e1 cos(alpha)
+// + e2 sin(alpha) and L = S cos(lam) + p sin(lam), the orbital-plane vectors
+// u1 = p x S = sin(alpha) e1 - cos(alpha) e2 (the direction of L x S) and
+// u2 = L x u1 = cos(lam) p - sin(lam) S enter only through their components
+// along P and Q, which need the projections below.
 template <typename T>
 struct Geo {
-  T sx, sy, sz, e1x, e1y, e1z, e2x, e2y, e2z, cl, sl;
-  T nx, ny, nz, ns, ne1, ne2;           // N and N.S, N.e1, N.e2
+  T pe1, pe2, qe1, qe2;       // P.e1, P.e2, Q.e1, Q.e2
+  T cpe1, cpe2, cqe1, cqe2;   // cos(lam) P.e1, cos(lam) P.e2, cos(lam) Q.e1, cos(lam) Q.e2
+  T spS, sqS;                 // sin(lam) P.S, sin(lam) Q.S
   T sin_ths, cos_ths, sin_phs, cos_phs;
   T amp_scale;
 };
@@ -69,7 +76,8 @@ struct __align__(16) WalkerC {
   double sin_ths, cos_ths, sin_phs, cos_phs;
   double dop;                // (R/c) sin(theta_S) [s]
   double pad[3];
-  Geo<float> gf;             // the geometry rounded to FP32 (mixed kernels)
+  Geo<double> gd;            // response geometry (FP64 kernels)
+  Geo<float> gf;             // the same rounded to FP32 (mixed kernels)
   float cnf[2];              // (cn_re, cn_im) rounded to FP32
   int64_t j_plunge;          // first zeroed sample (n if none); written by the orbit kernel
   uint32_t status;           // status bits (prologue | orbit)

@@ -66,7 +66,7 @@ void launch_orbit(WalkerC* wc, int w, int64_t n, double dt, double t0, const Opt
                   const double* mcpi_tab, cudaStream_t s);
 
 // waveform: z[w][n] (double2 or float2); unit_scale multiplies by mu_s c (cm units)
-// lisa: per-tile phibar table [n/256][6] (launch_lisa_tiles); ivs: mixed
+// lisa: per-tile phibar table [n/256][8] (launch_lisa_tiles); ivs: mixed
 // interval records [w][n/ks] (launch_intervals_mixed; unused for FP64)
 void launch_wave(const Knot* knots, const WalkerC* wc, int w, int64_t n, double dt, double t0,
                  const OptsN& o, void* z, bool unit_scale, const BesselTab& bt, const double* lisa, const void* ivs,

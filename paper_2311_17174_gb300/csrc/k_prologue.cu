@@ -153,18 +153,24 @@ __global__ void k0_prologue(const double* __restrict__ theta, int64_t ld, int w,
   c.cnf[0] = (float)c.cn_re;
   c.cnf[1] = (float)c.cn_im;
   {
-    Geo<float>& g = c.gf;
-    g.sx = (float)c.sx; g.sy = (float)c.sy; g.sz = (float)c.sz;
-    g.e1x = (float)c.e1x; g.e1y = (float)c.e1y; g.e1z = (float)c.e1z;
-    g.e2x = (float)c.e2x; g.e2y = (float)c.e2y; g.e2z = (float)c.e2z;
-    g.cl = (float)c.coslam; g.sl = (float)c.sinlam;
-    g.nx = (float)c.nx; g.ny = (float)c.ny; g.nz = (float)c.nz;
-    g.ns = (float)(c.nx * c.sx + c.ny * c.sy + c.nz * c.sz);
-    g.ne1 = (float)(c.nx * c.e1x + c.ny * c.e1y + c.nz * c.e1z);
-    g.ne2 = (float)(c.nx * c.e2x + c.ny * c.e2y + c.nz * c.e2z);
-    g.sin_ths = (float)sts; g.cos_ths = (float)cts; g.sin_phs = (float)sps; g.cos_phs = (float)cps;
-    g.amp_scale = (float)c.amp_scale;
-
+    // projections on the fixed sky basis P = (-sin phS, cos phS, 0),
+    // Q = P x N = (cos phS cos thS, sin phS cos thS, -sin thS)
+    const double P[3] = {-sps, cps, 0.0}, Q[3] = {cps * cts, sps * cts, -sts};
+    const double e1[3] = {c.e1x, c.e1y, c.e1z}, e2[3] = {c.e2x, c.e2y, c.e2z}, S[3] = {c.sx, c.sy, c.sz};
+    auto dot = [](const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; };
+    Geo<double>& g = c.gd;
+    g.pe1 = dot(P, e1); g.pe2 = dot(P, e2); g.qe1 = dot(Q, e1); g.qe2 = dot(Q, e2);
+    g.cpe1 = c.coslam * g.pe1; g.cpe2 = c.coslam * g.pe2;
+    g.cqe1 = c.coslam * g.qe1; g.cqe2 = c.coslam * g.qe2;
+    g.spS = c.sinlam * dot(P, S); g.sqS = c.sinlam * dot(Q, S);
+    g.sin_ths = sts; g.cos_ths = cts; g.sin_phs = sps; g.cos_phs = cps;
+    g.amp_scale = c.amp_scale;
+    Geo<float>& f = c.gf;
+    f.pe1 = (float)g.pe1; f.pe2 = (float)g.pe2; f.qe1 = (float)g.qe1; f.qe2 = (float)g.qe2;
+    f.cpe1 = (float)g.cpe1; f.cpe2 = (float)g.cpe2; f.cqe1 = (float)g.cqe1; f.cqe2 = (float)g.cqe2;
+    f.spS = (float)g.spS; f.sqS = (float)g.sqS;
+    f.sin_ths = (float)sts; f.cos_ths = (float)cts; f.sin_phs = (float)sps; f.cos_phs = (float)cps;
+    f.amp_scale = (float)g.amp_scale;
   }
   c.j_plunge = n;
   c.status = st;

@@ -187,7 +187,12 @@ __device__ __forceinline__ unsigned long long to_q64(double f) {
   return (unsigned long long)(f * 18446744073709551616.0);
 }
 
-__device__ __forceinline__ long long to_q64s(double f) {   // |f| < 0.5
+// a per-sample phase increment [cycles] as a signed Q0.64 fraction: the
+// phase is kept mod 1, so the increment is reduced to [-1/2, 1/2) first (at
+// long sample intervals it exceeds half a cycle)
+__device__ __forceinline__ long long to_q64s(double f) {
+  f -= rint(f);
+  if (f >= 0.5) f -= 1.0;
   return (long long)llrint(f * 18446744073709551616.0);
 }
 
@@ -229,21 +234,20 @@ __global__ void k1b_intervals(const Knot* __restrict__ knots, int64_t nk, int ks
   build_iv_mixed(kn[k], kn[k + 1], (double)ks * dt, ks, out[wk * nk + k]);
 }
 
-// Per-tile quadratic coefficients of cos, sin of the LISA orbital phase
-// phibar = 2 pi t / T at tile offsets 0, 128, 256: tab[tile][0..2] (cos),
-// tab[tile][3..5] (sin), in t/256.
+// cos, sin of the LISA orbital phase phibar = 2 pi t / T at the four
+// pattern-fit nodes of each 256-sample tile (offsets 0, 256/3, 512/3, 256):
+// tab[tile][2q] = cos, tab[tile][2q + 1] = sin.
 __global__ void k_lisa_tiles(int64_t ntiles, double t0, double dt, double* __restrict__ tab) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ntiles) return;
-  double c[3], sn[3];
-  for (int q = 0; q < 3; ++q) {
-    double f = (t0 + (double)(i * 256 + 128 * q) * dt) / kYear;
+  for (int q = 0; q < 4; ++q) {
+    double f = (t0 + ((double)(i * 256) + 256.0 * (double)q / 3.0) * dt) / kYear;
     f -= floor(f);
-    sincospi(2.0 * f, &sn[q], &c[q]);
+    double sn, cs;
+    sincospi(2.0 * f, &sn, &cs);
+    tab[i * 8 + 2 * q] = cs;
+    tab[i * 8 + 2 * q + 1] = sn;
   }
-  double* o = tab + i * 6;
-  o[0] = c[0]; o[1] = -3.0 * c[0] + 4.0 * c[1] - c[2]; o[2] = 2.0 * c[0] - 4.0 * c[1] + 2.0 * c[2];
-  o[3] = sn[0]; o[4] = -3.0 * sn[0] + 4.0 * sn[1] - sn[2]; o[5] = 2.0 * sn[0] - 4.0 * sn[1] + 2.0 * sn[2];
 }
 
 void launch_intervals_mixed(const Knot* knots, int w, int64_t n, int ks, double dt, void* ivs, cudaStream_t s) {
@@ -271,20 +275,6 @@ __device__ __forceinline__ float phase_fx(unsigned long long base, long long inc
 
 // --------------------------------------------------- response + harmonics
 template <typename T>
-__device__ __forceinline__ void load_geo(const WalkerC& c, Geo<T>& g) {
-  g.sx = T(c.sx); g.sy = T(c.sy); g.sz = T(c.sz);
-  g.e1x = T(c.e1x); g.e1y = T(c.e1y); g.e1z = T(c.e1z);
-  g.e2x = T(c.e2x); g.e2y = T(c.e2y); g.e2z = T(c.e2z);
-  g.cl = T(c.coslam); g.sl = T(c.sinlam);
-  g.nx = T(c.nx); g.ny = T(c.ny); g.nz = T(c.nz);
-  g.ns = T(c.nx * c.sx + c.ny * c.sy + c.nz * c.sz);
-  g.ne1 = T(c.nx * c.e1x + c.ny * c.e1y + c.nz * c.e1z);
-  g.ne2 = T(c.nx * c.e2x + c.ny * c.e2y + c.nz * c.e2z);
-  g.sin_ths = T(c.sin_ths); g.cos_ths = T(c.cos_ths); g.sin_phs = T(c.sin_phs); g.cos_phs = T(c.cos_phs);
-  g.amp_scale = T(c.amp_scale);
-}
-
-template <typename T>
 __device__ __forceinline__ T rcp_fast(T x) { return T(1) / x; }
 template <>
 __device__ __forceinline__ float rcp_fast<float>(float x) { return __fdividef(1.f, x); }
@@ -301,40 +291,6 @@ __device__ __forceinline__ void double_angle(T x, T y, T& c2, T& s2, bool degene
     c2 = (x * x - y * y) * inv;
     s2 = T(2) * x * y * inv;
   }
-}
-
-// Three double angles at once.  FP64: one reciprocal of the product of the
-// three squared radii serves all three (a reciprocal costs several FP64
-// instructions, a product one); the radii are sums of squares of unit-vector
-// components (<= 4), so the product cannot overflow and underflows only below
-// 1e-300.  FP32: three hardware reciprocals.
-template <typename T>
-__device__ __forceinline__ void double_angle3(T xa, T ya, bool dega, T xb, T yb, bool degb, T xc, T yc, bool degc,
-                                              T& ca, T& sa, T& cb, T& sb, T& cc, T& sc) {
-  double_angle(xa, ya, ca, sa, dega);
-  double_angle(xb, yb, cb, sb, degb);
-  double_angle(xc, yc, cc, sc, degc);
-}
-template <>
-__device__ __forceinline__ void double_angle3<double>(double xa, double ya, bool dega, double xb, double yb,
-                                                      bool degb, double xc, double yc, bool degc, double& ca,
-                                                      double& sa, double& cb, double& sb, double& cc, double& sc) {
-  double ra = xa * xa + ya * ya, rb = xb * xb + yb * yb, rc = xc * xc + yc * yc;
-  dega = dega || !(ra > 0.0);
-  degb = degb || !(rb > 0.0);
-  degc = degc || !(rc > 0.0);
-  if (dega) ra = 1.0;
-  if (degb) rb = 1.0;
-  if (degc) rc = 1.0;
-  const double rab = ra * rb;
-  const double inv = 1.0 / (rab * rc);
-  const double ia = rb * rc * inv, ib = ra * rc * inv, ic = rab * inv;
-  ca = dega ? 1.0 : (xa * xa - ya * ya) * ia;
-  sa = dega ? 0.0 : 2.0 * xa * ya * ia;
-  cb = degb ? 1.0 : (xb * xb - yb * yb) * ib;
-  sb = degb ? 0.0 : 2.0 * xb * yb * ib;
-  cc = degc ? 1.0 : (xc * xc - yc * yc) * ic;
-  sc = degc ? 0.0 : 2.0 * xc * yc * ic;
 }
 
 // cos(n Phi), sin(n Phi) for n = 1, 2, ...: complex rotation (FP32) or the
@@ -497,66 +453,86 @@ __device__ __forceinline__ void harmonic_sums2(float cphA, float sphA, float stA
   sB = make_float3(accB.x, accB.y, rB);
 }
 
-// Channels from the harmonic sums at one sample: LISA response (antenna
-// patterns, polarisation angle psi, the angle beta in gamma = gamma~ + beta)
-// and h_I, h_II.  c2gt/s2gt: cos/sin of 2 gamma~; ca/sa: of alpha; cb/sb:
-// of phibar (the LISA orbital phase); A = x^(2/3).
+// ----------------------------------------------------------- response
+// The LISA response of Sec. 2 (Eq. 2 with the Barack-Cutler antenna
+// patterns) contracts the detector tensor with the polarisation tensors, and
+// the AK polarisations are the transverse-traceless projection of the
+// orbit's quadrupole tensor
+//   M = X (u1 u1 - u2 u2) + Y (u1 u2 + u2 u1) + Rs (u1 u1 + u2 u2),
+// u1, u2 the orbital-plane basis of Geo (pericentre at angle gamma~ from u1),
+// (X, Y) the harmonic sums (Cs, Ss) rotated by 2 gamma~.  The contraction does
+// not depend on the polarisation basis, so it is taken in the fixed sky basis
+// (P, Q) of Geo: the angle beta and the L-dependent polarisation angle psi
+// drop out, and
+//   h_I = F+_I H+ + Fx_I Hx,  H+ + i Hx = (Rs + X) z1^2 + (Rs - X) z2^2 + 2 Y z1 z2,
+// z_k = P.u_k + i Q.u_k, with F_I, F_II the antenna patterns at the
+// polarisation angle psi_P of P (tan psi_P = (z_d.Q)/(z_d.P), z_d the
+// detector normal).  The patterns depend on time only through the LISA
+// orbital phase phibar, a one-year period, so each tile fits them by a cubic.
+
+// The four patterns (sqrt3/2 F+_I, sqrt3/2 Fx_I, sqrt3/2 F+_II, sqrt3/2 Fx_II)
+// times scale at phibar = atan2(sb, cb): detector-frame polar angle
+// cos(theta_d) = z_d.N, azimuth phi_d = phibar + atan2(sqrt3 cos thS + sin thS
+// cos(phibar - phS), 2 sin thS sin(phibar - phS)), channel II at phi_d - pi/4.
 template <typename T>
-__device__ __forceinline__ void response(const Geo<T>& g, T c2gt, T s2gt, T ca, T sa, T cb, T sb, T A, T Cs, T Ss,
-                                         T Rs, T& hI, T& hII) {
-  // L(t) = S cos lam + sin lam p, p = e1 cos alpha + e2 sin alpha
-  const T px_ = g.e1x * ca + g.e2x * sa, py_ = g.e1y * ca + g.e2y * sa, pz_ = g.e1z * ca + g.e2z * sa;
-  const T lx = g.sx * g.cl + g.sl * px_;
-  const T ly = g.sy * g.cl + g.sl * py_;
-  const T lz = g.sz * g.cl + g.sl * pz_;
-  const T u = ca * g.ne1 + sa * g.ne2;                     // N.p
-  const T c = g.cl * g.ns + g.sl * u;                      // L.N
-  // detector normal z_d = z/2 - (sqrt3/2)(cos phibar x + sin phibar y)
+__device__ __forceinline__ void antenna_fixed(const Geo<T>& g, T cb, T sb, T scale, T F[4]) {
   const T h3 = T(kSqrt3Half);
-  const T zx = -h3 * cb, zy = -h3 * sb, zz = T(0.5);
-  const T zn = zx * g.nx + zy * g.ny + zz * g.nz;         // z_d.N = cos(theta_d)
-  const T lzd = lx * zx + ly * zy + lz * zz;
-  // psi: tan psi = [L.z_d - (L.N)(z_d.N)] / [N.(L x z_d)] = [..] / [L.(z_d x N)]
-  const T wx = zy * g.nz - zz * g.ny, wy = zz * g.nx - zx * g.nz, wz = zx * g.ny - zy * g.nx;
-  const T pyv = lzd - c * zn;
-  const T pxv = lx * wx + ly * wy + lz * wz;
-  // beta: angle about L from L x N to L x S = sin(lam) (p x S):
-  //   cos beta ~ sin(lam) N.S - cos(lam) N.p,  sin beta ~ N.(S x p) = cos a N.e2 - sin a N.e1
-  const T xb = g.sl * g.ns - g.cl * u;
-  const T yb = ca * g.ne2 - sa * g.ne1;
-  const T one_c2 = T(1) - c * c;
-  // detector-frame azimuth: phi = phibar + atan2(sqrt3 cos thS + sin thS cos(phibar-phiS), 2 sin thS sin(phibar-phiS))
   const T cdp = cb * g.cos_phs + sb * g.sin_phs;
   const T sdp = sb * g.cos_phs - cb * g.sin_phs;
-  T c2psi, s2psi, c2b, s2b, c2x, s2x;
-  double_angle3<T>(pxv, pyv, false, xb, yb, !(one_c2 > T(1e-24)), T(2) * g.sin_ths * sdp,
-                   T(1.7320508075688772) * g.cos_ths + g.sin_ths * cdp, false, c2psi, s2psi, c2b, s2b, c2x, s2x);
-  const T c2g = c2gt * c2b - s2gt * s2b;
-  const T s2g = s2gt * c2b + c2gt * s2b;
-  const T c2b_ = cb * cb - sb * sb, s2b_ = T(2) * sb * cb;
-  const T c2p = c2b_ * c2x - s2b_ * s2x;
-  const T s2p = s2b_ * c2x + c2b_ * s2x;
-  // antenna patterns; channel II has phi -> phi - pi/4
-  const T ct = zn, q = T(0.5) * (T(1) + ct * ct);
-  const T P1 = q * c2p, P2 = ct * s2p, Q1 = q * s2p, Q2 = ct * c2p;
-  const T fpI = P1 * c2psi - P2 * s2psi;
-  const T fxI = P1 * s2psi + P2 * c2psi;
-  const T fpII = Q1 * c2psi + Q2 * s2psi;
-  const T fxII = Q1 * s2psi - Q2 * c2psi;
-  const T hp = A * ((T(1) + c * c) * (Cs * c2g - Ss * s2g) + one_c2 * Rs);
-  const T hx = T(-2) * c * A * (Ss * c2g + Cs * s2g);
-  hI = h3 * (fpI * hp + fxI * hx);
-  hII = h3 * (fpII * hp + fxII * hx);
+  const T ct = T(0.5) * g.cos_ths - h3 * g.sin_ths * cdp;
+  T c2x, s2x, c2p, s2p;
+  double_angle<T>(T(2) * g.sin_ths * sdp, T(1.7320508075688772) * g.cos_ths + g.sin_ths * cdp, c2x, s2x, false);
+  double_angle<T>(h3 * sdp, h3 * g.cos_ths * cdp + T(0.5) * g.sin_ths, c2p, s2p, false);
+  const T c2b = cb * cb - sb * sb, s2b = T(2) * sb * cb;
+  const T c2f = c2b * c2x - s2b * s2x;   // cos, sin of 2 phi_d
+  const T s2f = s2b * c2x + c2b * s2x;
+  const T q = T(0.5) * (T(1) + ct * ct);
+  const T k = h3 * scale;
+  F[0] = k * (q * c2f * c2p - ct * s2f * s2p);
+  F[1] = k * (q * c2f * s2p + ct * s2f * c2p);
+  F[2] = k * (q * s2f * c2p + ct * c2f * s2p);
+  F[3] = k * (q * s2f * s2p - ct * c2f * c2p);
+}
+
+// Cubic c0 + c1 s + c2 s^2 + c3 s^3 through y0..y3 at s = 0, 1/3, 2/3, 1
+// (Newton forward differences in u = 3 s).
+template <typename T>
+__device__ __forceinline__ void fit_cubic4(T y0, T y1, T y2, T y3, T* c) {
+  const T d1 = y1 - y0, d2 = (y2 - y1) - d1, d3 = ((y3 - y2) - (y2 - y1)) - d2;
+  c[0] = y0;
+  c[1] = T(3) * (d1 - T(0.5) * d2 + d3 * T(1.0 / 3.0));
+  c[2] = T(4.5) * (d2 - d3);
+  c[3] = T(4.5) * d3;
+}
+
+template <typename T>
+__device__ __forceinline__ T cubic_at(const T* c, T s) {
+  return ((c[3] * s + c[2]) * s + c[1]) * s + c[0];
+}
+
+// Channels from the harmonic sums at one sample.  c2gt/s2gt: cos/sin of
+// 2 gamma~; ca/sa: of alpha; A = x^(2/3); F: the four patterns at the sample.
+template <typename T>
+__device__ __forceinline__ void response(const Geo<T>& g, T c2gt, T s2gt, T ca, T sa, T A, T Cs, T Ss, T Rs,
+                                         const T F[4], T& hI, T& hII) {
+  const T z1r = sa * g.pe1 - ca * g.pe2, z1i = sa * g.qe1 - ca * g.qe2;
+  const T z2r = ca * g.cpe1 + sa * g.cpe2 - g.spS, z2i = ca * g.cqe1 + sa * g.cqe2 - g.sqS;
+  const T X = Cs * c2gt - Ss * s2gt, Y = Cs * s2gt + Ss * c2gt;
+  const T a = A * (Rs + X), b = A * (Rs - X), y = T(2) * A * Y;
+  const T Hp = a * (z1r * z1r - z1i * z1i) + b * (z2r * z2r - z2i * z2i) + y * (z1r * z2r - z1i * z2i);
+  const T Hx = T(2) * (a * (z1r * z1i) + b * (z2r * z2i)) + y * (z1r * z2i + z1i * z2r);
+  hI = F[0] * Hp + F[1] * Hx;
+  hII = F[2] * Hp + F[3] * Hx;
 }
 
 // Channels at one sample (harmonic sums, then the response).
 template <typename T>
-__device__ __forceinline__ void channels(const Geo<T>& g, T cph, T sph, T c2gt, T s2gt, T ca, T sa, T cb,
-                                         T sb, T A, T st, const T* __restrict__ bq, int n_max, T& hI,
-                                         T& hII, bool cheb = false) {
+__device__ __forceinline__ void channels(const Geo<T>& g, T cph, T sph, T c2gt, T s2gt, T ca, T sa, T A, T st,
+                                         const T* __restrict__ bq, int n_max, const T F[4], T& hI, T& hII,
+                                         bool cheb = false) {
   T Cs, Ss, Rs;
   harmonic_sums<T>(cph, sph, st, bq, n_max, cheb, Cs, Ss, Rs);
-  response<T>(g, c2gt, s2gt, ca, sa, cb, sb, A, Cs, Ss, Rs, hI, hII);
+  response<T>(g, c2gt, s2gt, ca, sa, A, Cs, Ss, Rs, F, hI, hII);
 }
 
 // Per-harmonic amplitude coefficients in shared memory: 9 values (a, b, c
@@ -637,6 +613,11 @@ __device__ __forceinline__ void fit3(T f0, T fh, T f1, T* q) {
   q[2] = T(2) * f0 - T(4) * fh + T(2) * f1;
 }
 
+// Above these sample intervals the per-tile cubic of the antenna patterns
+// (error ~ (256 dt / T)^4) is replaced by their exact value per sample.
+constexpr double kPatternFitDtMax64 = 64.0;     // [s]; fit error < 2e-12 below
+constexpr double kPatternFitDtMaxM = 1024.0;    // [s]; fit error < 1e-7 below
+
 __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
                                                         int64_t n, double dt, double t0, int ks, int n_max,
                                                         double2* __restrict__ z, int unit_scale,
@@ -645,7 +626,8 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
   __shared__ IvD iv[kTile / 64];
   __shared__ double bnode[3 * 32 * 3];
   __shared__ double bq[32 * 9];
-  __shared__ double oq[2][3];
+  __shared__ double fn[4][4];   // the four patterns at the four fit nodes
+  __shared__ double fq[4][4];   // their cubics in t / 256
   __shared__ double2 ex[129];
   __shared__ Geo<double> g;
   const int wk = blockIdx.y;
@@ -657,11 +639,20 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
   const int ni = ks >= kTile ? 1 : kTile / ks;
   const int t = threadIdx.x;
   const double h = (double)ks * dt;
+  const bool exact_f = dt > kPatternFitDtMax64;
+  const double scale = unit_scale ? C.gd.amp_scale : 1.0;
   if (t < ni) build_iv(kn[kfirst + t], kn[kfirst + t + 1], h, iv[t]);
-  if (t >= 128 && t < 134) oq[(t - 128) / 3][(t - 128) % 3] = lisa[blockIdx.x * 6 + (t - 128)];
-  if (t == 160) load_geo<double>(C, g);
+  if (t >= 224 && t < 228 && !exact_f) {
+    const int q = t - 224;
+    antenna_fixed<double>(C.gd, lisa[blockIdx.x * 8 + 2 * q], lisa[blockIdx.x * 8 + 2 * q + 1], scale, fn[q]);
+  }
+  if (t == 160) g = C.gd;
   if (t < 129) ex[t] = g_exp128[t];
   __syncthreads();
+  if (t >= 224 && t < 228 && !exact_f) {
+    const int q = t - 224;
+    fit_cubic4<double>(fn[0][q], fn[1][q], fn[2][q], fn[3][q], fq[q]);
+  }
   const int span = tile_span(j0, C.j_plunge);
   tile_harmonics<double, IvD>(iv, ni, j0, kfirst, ks, n_max, span, bnode, bq, rk, ifact);
   __syncthreads();
@@ -680,19 +671,24 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
     double fal = poly3<double>(v.al, s);
     fal -= rint(fal);
     const double A = poly3<double>(v.am, s);
-    const double so = (double)t * (1.0 / kTile);
-    const double cb = (oq[0][2] * so + oq[0][1]) * so + oq[0][0];
-    const double sb = (oq[1][2] * so + oq[1][1]) * so + oq[1][0];
+    double F[4];
+    if (!exact_f) {
+      const double so = (double)t * (1.0 / kTile);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) F[q] = cubic_at<double>(fq[q], so);
+    } else {
+      double f = (t0 + (double)j * dt) / kYear;
+      f -= floor(f);
+      double sb, cb;
+      sincospi(2.0 * f, &sb, &cb);
+      antenna_fixed<double>(g, cb, sb, scale, F);
+    }
     double sph, cph, s2g, c2g, sa, ca;
     sincos2pi_tab(fph, ex, sph, cph);
     sincos2pi_tab(fgm, ex, s2g, c2g);
     sincos2pi_tab(fal, ex, sa, ca);
     double hI, hII;
-    channels<double>(g, cph, sph, c2g, s2g, ca, sa, cb, sb, A, (double)t * inv_span, bq, n_max, hI, hII);
-    if (unit_scale) {
-      hI *= g.amp_scale;
-      hII *= g.amp_scale;
-    }
+    channels<double>(g, cph, sph, c2g, s2g, ca, sa, A, (double)t * inv_span, bq, n_max, F, hI, hII);
     out = make_double2(hI, hII);
   }
   z[(int64_t)wk * n + j] = out;
@@ -712,7 +708,11 @@ __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict
   __shared__ IvM iv[kSegM / 64];
   __shared__ float bnode[3 * 32 * 3];
   __shared__ __align__(16) float bq[32 * 12];
-  __shared__ float oq[kSegM / kTile][2][3];
+  constexpr int kTiles = kSegM / kTile;
+  static_assert(kTiles % 2 == 0, "tiles are processed in pairs");
+  __shared__ float fn[kTiles][4][4];   // the four patterns at the fit nodes of each tile
+  __shared__ float fq[kTiles][4][4];   // their cubics in (t mod 256) / 256
+  __shared__ float cs0[kTiles][2];     // cos, sin phibar at each tile's start
   __shared__ Geo<float> g;
   __shared__ int64_t jplunge;
   const int wk = blockIdx.y;
@@ -722,27 +722,37 @@ __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict
   const int64_t kfirst = j0 / ks;
   const int ni = ks >= kSegM ? 1 : kSegM / ks;
   const int t = threadIdx.x;
+  const bool exact_f = dt > kPatternFitDtMaxM;
+  const float scale = unit_scale ? C.gf.amp_scale : 1.f;
   if (t < ni) iv[t] = ivs[(int64_t)wk * nk + kfirst + t];
-  constexpr int kTiles = kSegM / kTile;
-  static_assert(kTiles % 2 == 0, "tiles are processed in pairs");
-  if (t >= 128 && t < 128 + 6 * kTiles) {
-    const int q = t - 128;
-    oq[q / 6][(q % 6) / 3][q % 3] = (float)lisa[(blockIdx.x * kTiles + q / 6) * 6 + q % 6];
+  if (t >= 128 && t < 128 + 4 * kTiles) {   // node q of tile tt
+    const int i = t - 128, tt = i / 4, q = i % 4;
+    const double* L = lisa + (blockIdx.x * kTiles + tt) * 8 + 2 * q;
+    const float cb = (float)L[0], sb = (float)L[1];
+    antenna_fixed<float>(C.gf, cb, sb, scale, fn[tt][q]);
+    if (q == 0) {
+      cs0[tt][0] = cb;
+      cs0[tt][1] = sb;
+    }
   }
   if (t == 224) {
     g = C.gf;
     jplunge = C.j_plunge;
   }
   __syncthreads();
+  if (t >= 128 && t < 128 + 4 * kTiles) {   // pattern q of tile tt
+    const int i = t - 128, tt = i / 4, q = i % 4;
+    fit_cubic4<float>(fn[tt][0][q], fn[tt][1][q], fn[tt][2][q], fn[tt][3][q], fq[tt][q]);
+  }
   const int span = tile_span(j0, jplunge, kSegM);
   const bool cheb = C.e0 < 0.5;   // per walker (uniform in the CTA)
   tile_harmonics<float, IvM>(iv, ni, j0, kfirst, ks, n_max, span, bnode, bq, rk, ifact);
   __syncthreads();
   const float inv_span = 1.f / (float)span;
   const float inv_ks = 1.f / (float)ks;
+  constexpr float kTwoPiF = 6.283185307179586f;
   // per-sample inputs of the response and of the harmonic sums
-  auto inputs = [&](int r, int tt, float& cph, float& sph, float& c2g, float& s2g, float& ca, float& sa,
-                    float& cb, float& sb, float& A) {
+  auto inputs = [&](int r, float& cph, float& sph, float& c2g, float& s2g, float& ca, float& sa, float& A) {
     const int ki = ks >= kSegM ? 0 : r / ks;
     const int tau = r - ki * ks;
     const float s = (float)tau * inv_ks;
@@ -752,35 +762,39 @@ __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict
     const float fgm = phase_fx(v.gm_base << 1, (long long)((unsigned long long)v.gm_inc << 1), c2, tau, s);
     const float fal = phase_fx(v.al_base, v.al_inc, v.al_c, tau, s);
     A = poly3<float>(v.am, s);
-    const float so = (float)t * (1.f / kTile);
-    cb = (oq[tt][0][2] * so + oq[tt][0][1]) * so + oq[tt][0][0];
-    sb = (oq[tt][1][2] * so + oq[tt][1][1]) * so + oq[tt][1][0];
     // hardware sin/cos of the reduced angles (|x| <= pi, absolute error ~5e-7)
-    constexpr float kTwoPiF = 6.283185307179586f;
     __sincosf(kTwoPiF * fph, &sph, &cph);
     __sincosf(kTwoPiF * fgm, &s2g, &c2g);
     __sincosf(kTwoPiF * fal, &sa, &ca);
+  };
+  // the four patterns at offset t of tile tt
+  const float so = (float)t * (1.f / kTile);
+  auto patterns = [&](int tt, float F[4]) {
+    if (!exact_f) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) F[q] = cubic_at<float>(fq[tt][q], so);
+    } else {
+      float sd, cd;
+      __sincosf(kTwoPiF * (float)(dt / kYear) * (float)t, &sd, &cd);
+      antenna_fixed<float>(g, cs0[tt][0] * cd - cs0[tt][1] * sd, cs0[tt][1] * cd + cs0[tt][0] * sd, scale, F);
+    }
   };
   // two samples per thread (tiles tt and tt+1): the amplitude coefficients
   // of each harmonic are loaded once for both
 #pragma unroll 1
   for (int tt = 0; tt < kTiles; tt += 2) {
     const int rA = tt * kTile + t, rB = rA + kTile;   // offsets in the segment
-    float cphA, sphA, c2gA, s2gA, caA, saA, cbA, sbA, AA;
-    float cphB, sphB, c2gB, s2gB, caB, saB, cbB, sbB, AB;
-    inputs(rA, tt, cphA, sphA, c2gA, s2gA, caA, saA, cbA, sbA, AA);
-    inputs(rB, tt + 1, cphB, sphB, c2gB, s2gB, caB, saB, cbB, sbB, AB);
+    float cphA, sphA, c2gA, s2gA, caA, saA, AA;
+    float cphB, sphB, c2gB, s2gB, caB, saB, AB;
+    inputs(rA, cphA, sphA, c2gA, s2gA, caA, saA, AA);
+    inputs(rB, cphB, sphB, c2gB, s2gB, caB, saB, AB);
     float3 hsA, hsB;
     harmonic_sums2(cphA, sphA, (float)rA * inv_span, cphB, sphB, (float)rB * inv_span, bq, n_max, cheb, hsA, hsB);
-    float hIA, hIIA, hIB, hIIB;
-    response<float>(g, c2gA, s2gA, caA, saA, cbA, sbA, AA, hsA.x, hsA.y, hsA.z, hIA, hIIA);
-    response<float>(g, c2gB, s2gB, caB, saB, cbB, sbB, AB, hsB.x, hsB.y, hsB.z, hIB, hIIB);
-    if (unit_scale) {
-      hIA *= g.amp_scale;
-      hIIA *= g.amp_scale;
-      hIB *= g.amp_scale;
-      hIIB *= g.amp_scale;
-    }
+    float hIA, hIIA, hIB, hIIB, F[4];
+    patterns(tt, F);
+    response<float>(g, c2gA, s2gA, caA, saA, AA, hsA.x, hsA.y, hsA.z, F, hIA, hIIA);
+    patterns(tt + 1, F);
+    response<float>(g, c2gB, s2gB, caB, saB, AB, hsB.x, hsB.y, hsB.z, F, hIB, hIIB);
     const int64_t jA = j0 + rA, jB = j0 + rB;
     z[(int64_t)wk * n + jA] = jA < jplunge ? make_float2(hIA, hIIA) : make_float2(0.f, 0.f);
     z[(int64_t)wk * n + jB] = jB < jplunge ? make_float2(hIB, hIIB) : make_float2(0.f, 0.f);

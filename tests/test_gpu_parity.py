@@ -84,6 +84,27 @@ def test_waveform_options(ctx, kw):
         assert rel_l2(z[k], hI[k] + 1j * hII[k]) <= 1e-9
 
 
+@pytest.mark.parametrize("dt,doppler", [(60.0, 1), (100.0, 1), (2000.0, 0)])
+def test_waveform_long_sample_interval(ctx, dt, doppler):
+    # The antenna patterns are a per-tile cubic in time up to 64 s (FP64) and
+    # 1024 s (mixed) and exact per sample above: 60 s fits both, 100 s is
+    # exact in FP64 only, 2000 s exact in both.  Knots every 64 samples and
+    # slowly evolving sources keep the orbit interpolation (a cubic Hermite
+    # over the knot interval, error ~ (K_s dt)^4) near 1e-11 rad, so the
+    # patterns are what is tested.  At 2000 s the yearly Doppler modulation
+    # of the phase (~3 rad) alone would leave a ~3e-9 rad Hermite error over
+    # 64 * 2000 s, so that case runs without it.
+    n = 1 << 13
+    th = I.draw_sources(35, 3, n, dt=dt, t_margin=(50.0, 100.0))
+    hI, hII, _ = O.waveform(th, n, dt, O.Opts(n_max=6, doppler=doppler))
+    z, _ = gpu_waveform(ctx, th, n, dt, 6, knot_spacing=64, doppler=doppler)
+    zm, _ = gpu_waveform(ctx, th, n, dt, 6, precision=1, knot_spacing=64, doppler=doppler)
+    for k in range(th.shape[0]):
+        ref = hI[k] + 1j * hII[k]
+        assert rel_l2(z[k], ref) <= 1e-9, (k, rel_l2(z[k], ref))
+        assert rel_l2(zm[k].astype(np.complex128), ref) <= 2e-5, (k, rel_l2(zm[k], ref))
+
+
 def test_waveform_eccentricity_zero_and_edges(ctx):
     # e0 = 0 (only n = 2 survives), spin 0, lambda near 0, theta_K = 0
     n, dt = 1 << 12, 15.0

@@ -381,7 +381,7 @@ def paper_bench(ctx, steps: int, warmup: int):
                 times.append(e0.elapsed_time(e1))
             ms = float(np.median(times))
             res[f"{name}_{walkers}w"] = {"ms_per_batch": ms, "lnl_per_s": walkers / (ms / 1e3),
-                                         "lnl_injection_walker0": float(lnl[0])}
+                                         "lnl_walker0": float(lnl[0])}
     ds.close()
     return {"workload": "paper-lso-1yr-2^21-n10 (backward from the LSO, 1 Gpc, noise-free)", **res}
 

@@ -620,7 +620,7 @@ constexpr double kPatternFitDtMaxM = 1024.0;    // [s]; fit error < 1e-7 below
 
 __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
                                                         int64_t n, double dt, double t0, int ks, int n_max,
-                                                        double2* __restrict__ z, int unit_scale,
+                                                        double2* __restrict__ z, int unit_scale, int exact_f,
                                                         const double* __restrict__ rk, const double* __restrict__ ifact,
                                                         const double* __restrict__ lisa) {
   __shared__ IvD iv[kTile / 64];
@@ -639,7 +639,6 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
   const int ni = ks >= kTile ? 1 : kTile / ks;
   const int t = threadIdx.x;
   const double h = (double)ks * dt;
-  const bool exact_f = dt > kPatternFitDtMax64;
   const double scale = unit_scale ? C.gd.amp_scale : 1.0;
   if (t < ni) build_iv(kn[kfirst + t], kn[kfirst + t + 1], h, iv[t]);
   if (t >= 224 && t < 228 && !exact_f) {
@@ -700,8 +699,11 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
 // samples; over that span its error is far below FP32 resolution.
 constexpr int kSegM = 1024;
 
+// exact_f: exact patterns per sample (long sample intervals), dphib: the
+// LISA orbital phase step per sample [cycles] for them.  No FP64 instruction
+// runs per thread: e0 is tested once per CTA.
 __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
-                                                          int64_t n, double dt, double t0, int ks, int n_max,
+                                                          int64_t n, int exact_f, float dphib, int ks, int n_max,
                                                           float2* __restrict__ z, int unit_scale,
                                                           const float* __restrict__ rk, const float* __restrict__ ifact,
                                                           const double* __restrict__ lisa, const IvM* __restrict__ ivs) {
@@ -715,6 +717,7 @@ __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict
   __shared__ float cs0[kTiles][2];     // cos, sin phibar at each tile's start
   __shared__ Geo<float> g;
   __shared__ int64_t jplunge;
+  __shared__ int cheb_s;
   const int wk = blockIdx.y;
   const WalkerC& C = wcs[wk];
   const int64_t nk = n / ks;
@@ -722,7 +725,6 @@ __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict
   const int64_t kfirst = j0 / ks;
   const int ni = ks >= kSegM ? 1 : kSegM / ks;
   const int t = threadIdx.x;
-  const bool exact_f = dt > kPatternFitDtMaxM;
   const float scale = unit_scale ? C.gf.amp_scale : 1.f;
   if (t < ni) iv[t] = ivs[(int64_t)wk * nk + kfirst + t];
   if (t >= 128 && t < 128 + 4 * kTiles) {   // node q of tile tt
@@ -738,6 +740,7 @@ __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict
   if (t == 224) {
     g = C.gf;
     jplunge = C.j_plunge;
+    cheb_s = C.e0 < 0.5;
   }
   __syncthreads();
   if (t >= 128 && t < 128 + 4 * kTiles) {   // pattern q of tile tt
@@ -745,7 +748,7 @@ __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict
     fit_cubic4<float>(fn[tt][0][q], fn[tt][1][q], fn[tt][2][q], fn[tt][3][q], fq[tt][q]);
   }
   const int span = tile_span(j0, jplunge, kSegM);
-  const bool cheb = C.e0 < 0.5;   // per walker (uniform in the CTA)
+  const bool cheb = cheb_s != 0;   // per walker (uniform in the CTA)
   tile_harmonics<float, IvM>(iv, ni, j0, kfirst, ks, n_max, span, bnode, bq, rk, ifact);
   __syncthreads();
   const float inv_span = 1.f / (float)span;
@@ -775,7 +778,7 @@ __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict
       for (int q = 0; q < 4; ++q) F[q] = cubic_at<float>(fq[tt][q], so);
     } else {
       float sd, cd;
-      __sincosf(kTwoPiF * (float)(dt / kYear) * (float)t, &sd, &cd);
+      __sincosf(kTwoPiF * dphib * (float)t, &sd, &cd);
       antenna_fixed<float>(g, cs0[tt][0] * cd - cs0[tt][1] * sd, cs0[tt][1] * cd + cs0[tt][0] * sd, scale, F);
     }
   };
@@ -808,11 +811,12 @@ void launch_wave(const Knot* knots, const WalkerC* wc, int w, int64_t n, double 
   if (o.precision == 0) {
     dim3 grid((unsigned)(n / kTile), (unsigned)w);
     k2_wave_f64<<<grid, kTile, 0, s>>>(knots, wc, n, dt, t0, o.ks, o.n_max, (double2*)z, unit_scale ? 1 : 0,
-                                       bt.r64, bt.f64, lisa);
+                                       dt > kPatternFitDtMax64 ? 1 : 0, bt.r64, bt.f64, lisa);
   } else {
     dim3 grid((unsigned)(n / kSegM), (unsigned)w);
-    k2_wave_mixed<<<grid, kTile, 0, s>>>(knots, wc, n, dt, t0, o.ks, o.n_max, (float2*)z, unit_scale ? 1 : 0,
-                                         bt.r32, bt.f32, lisa, (const IvM*)ivs);
+    k2_wave_mixed<<<grid, kTile, 0, s>>>(knots, wc, n, dt > kPatternFitDtMaxM ? 1 : 0, (float)(dt / kYear), o.ks,
+                                         o.n_max, (float2*)z, unit_scale ? 1 : 0, bt.r32, bt.f32, lisa,
+                                         (const IvM*)ivs);
   }
 }
 

@@ -402,7 +402,9 @@ extern "C" int emri_ctx_create(int device, size_t budget, emri_ctx** out) {
     return cuda_err(e2, "cudaStreamCreate");
   }
   // twiddle and quadrature tables
-  size_t tb = 4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8 + 64 * 8 + 35 * 32 * 12 + 35 * 12 + 256 + (32 + 129) * 32 * 8;
+  constexpr size_t kBc = (size_t)emri::kBesselOrders * emri::kBesselTerms;
+  size_t tb = 4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8 + 64 * 8 + kBc * 12 + emri::kBesselOrders * 12 + 256 +
+              (32 + 129) * 32 * 8;
   char* p = nullptr;
   e2 = cudaMalloc(&p, tb);
   if (e2 != cudaSuccess) {
@@ -419,11 +421,14 @@ extern "C" int emri_ctx_create(int device, size_t budget, emri_ctx** out) {
   c->gl = (double*)(p + 4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8);
   {
     char* q = (char*)(c->gl + 64);
-    c->bt.r64 = (double*)q;
-    c->bt.f64 = (double*)(q + 35 * 32 * 8);
-    c->bt.r32 = (float*)(q + 35 * 32 * 8 + 35 * 8);
-    c->bt.f32 = (float*)(q + 35 * 32 * 8 + 35 * 8 + 35 * 32 * 4);
-    c->mcpi = (double*)(q + 35 * 32 * 12 + 35 * 12 + 4);   // 8-byte aligned: q is, and 13860 + 4 = 13864
+    constexpr size_t no = emri::kBesselOrders;
+    c->bt.c64 = (double*)q;
+    c->bt.f64 = (double*)(q + kBc * 8);
+    c->bt.c32 = (float*)(q + kBc * 8 + no * 8);
+    c->bt.f32 = (float*)(q + kBc * 8 + no * 8 + kBc * 4);
+    size_t off = kBc * 12 + no * 12;
+    off = (off + 7) & ~(size_t)7;   // 8-byte aligned (q is)
+    c->mcpi = (double*)(q + off);
   }
   double glh[64];
   gauss_legendre32(glh, glh + 32);
@@ -433,12 +438,12 @@ extern "C" int emri_ctx_create(int device, size_t budget, emri_ctx** out) {
     cudaMemcpy(c->mcpi, mt.data(), mt.size() * sizeof(double), cudaMemcpyHostToDevice);
   }
   launch_twiddle_init(c->tw, c->stream);
-  launch_bessel_tables(c->bt, c->stream);
   cudaMemcpyAsync(c->gl, glh, sizeof glh, cudaMemcpyHostToDevice, c->stream);
   fft_set_smem_limits();
   e2 = cudaStreamSynchronize(c->stream);
   if (e2 == cudaSuccess) e2 = cudaGetLastError();
   if (e2 == cudaSuccess && upload_exp128()) e2 = cudaErrorUnknown;
+  if (e2 == cudaSuccess && emri::upload_bessel_tables(c->bt)) e2 = cudaErrorUnknown;
   if (e2 != cudaSuccess) {
     cudaFree(p);
     cudaStreamDestroy(c->stream);

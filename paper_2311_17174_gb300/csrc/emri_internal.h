@@ -40,14 +40,18 @@ struct Twiddles {
 
 void launch_twiddle_init(Twiddles t, cudaStream_t s);
 
-// Bessel series tables: r[m*32 + k] = 1/(k (m+k)), f[m] = 1/m!, m < 35
+// Bessel series tables: c[m * kBesselTerms + k] = (-1)^k m!/(k! (m+k)!),
+// f[m] = 1/m!, m < kBesselOrders
+constexpr int kBesselOrders = 35;
+constexpr int kBesselTerms = 48;
 struct BesselTab {
-  double* r64;
-  float* r32;
+  double* c64;
+  float* c32;
   double* f64;
   float* f32;
 };
-void launch_bessel_tables(BesselTab t, cudaStream_t s);
+// fills the tables from the host (synchronous); 0 on success
+int upload_bessel_tables(const BesselTab& t);
 // the FP64 waveform kernel's exp(2 pi i k/128) table on the current device; 0 on success
 int upload_exp128();
 

@@ -27,6 +27,7 @@
 // FP64 variant: everything in double.  Mixed variant: the three phases are
 // evaluated in 64-bit fixed point (linear term) plus an FP32 correction, so
 // no FP64 instruction runs per sample; the rest is FP32.
+#include <vector>
 #include "emri_common.cuh"
 #include "emri_internal.h"
 
@@ -35,31 +36,30 @@ namespace emri {
 constexpr int kTile = 256;
 
 // --------------------------------------------------------------- Bessel
-// J_m(x) by its power series sum_k (-x^2/4)^k (x/2)^m / (k! (m+k)!), m >= 0;
-// rk[m*32 + k] = 1/(k (m+k)) and ifact[m] = 1/m! come from tables, so a term
-// costs two multiplications.
+// J_m(x) by its power series (x/2)^m / m! * sum_k a_k y^k, y = x^2/4,
+// a_k = (-1)^k m! / (k! (m+k)!), evaluated by Horner's rule (one FMA per
+// term) over the first K = min(ceil(12 + 1.05 x), 48) terms.  Wherever the
+// series is used (orders m >= n + 1 at x = n e, n <= 32, e < 0.999) the
+// omitted tail is below 1e-16 of the sum.  bc[m * kBesselTerms + k] = a_k and
+// ifact[m] = 1/m! are tables (host long double, rounded once).
 template <typename T>
-__device__ __forceinline__ T bessel_series(int m, T x, const T* __restrict__ rk, const T* __restrict__ ifact) {
+__device__ __forceinline__ T bessel_series(int m, T x, const T* __restrict__ bc, const T* __restrict__ ifact) {
   const T half = T(0.5) * x;
   T lead = T(1);
   T p = half;
-  int k = m;
-  while (k) {                       // (x/2)^m by squaring
+  for (int k = m; k; k >>= 1) {     // (x/2)^m by squaring
     if (k & 1) lead *= p;
     p *= p;
-    k >>= 1;
   }
   lead *= ifact[m];
-  const T q = -half * half;
-  const T* r = rk + m * 32;
-  const T eps = sizeof(T) == 8 ? T(1e-17) : T(3e-8);
-  T term = lead, sum = lead;
-  for (int kk = 1; kk < 32; ++kk) {
-    term *= q * r[kk];
-    sum += term;
-    if (fabs(term) <= eps * fabs(sum)) break;
-  }
-  return sum;
+  const T y = half * half;
+  int K = (int)(T(12) + T(1.05) * x) + 1;
+  if (K > kBesselTerms) K = kBesselTerms;
+  const T* a = bc + m * kBesselTerms;
+  T sum = a[K - 1];
+#pragma unroll 4
+  for (int k = K - 2; k >= 0; --k) sum = fma(sum, y, a[k]);
+  return lead * sum;
 }
 
 // Amplitudes of harmonic n at eccentricity e:
@@ -69,7 +69,7 @@ __device__ __forceinline__ T bessel_series(int m, T x, const T* __restrict__ rk,
 // J_{n+2}, J_{n+1} by series, the lower orders by the (stable) downward
 // recurrence J_{m-1} = (2m/x) J_m - J_{m+1}, which also gives J_{-1} = -J_1.
 template <typename T>
-__device__ __forceinline__ void harmonic_amps(int n, T e, T out[3], const T* __restrict__ rk,
+__device__ __forceinline__ void harmonic_amps(int n, T e, T out[3], const T* __restrict__ bc,
                                               const T* __restrict__ ifact) {
   T jm2, jm1, j0, jp1, jp2;
   if (e < T(1e-12)) {               // J_m(0) = delta_m0
@@ -79,8 +79,8 @@ __device__ __forceinline__ void harmonic_amps(int n, T e, T out[3], const T* __r
   } else {
     const T x = T(n) * e;
     const T ix = T(1) / x;
-    jp2 = bessel_series<T>(n + 2, x, rk, ifact);
-    jp1 = bessel_series<T>(n + 1, x, rk, ifact);
+    jp2 = bessel_series<T>(n + 2, x, bc, ifact);
+    jp1 = bessel_series<T>(n + 1, x, bc, ifact);
     j0 = T(2 * (n + 1)) * ix * jp1 - jp2;
     jm1 = T(2 * n) * ix * j0 - jp1;
     jm2 = T(2 * (n - 1)) * ix * jm1 - j0;
@@ -92,21 +92,28 @@ __device__ __forceinline__ void harmonic_amps(int n, T e, T out[3], const T* __r
   out[2] = T(2) * j0;
 }
 
-// Reciprocal tables for the series (built once per context).
-__global__ void k_bessel_tables(double* r64, float* r32, double* f64, float* f32) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < 35 * 32) {
-    const int m = i / 32, k = i % 32;
-    const double v = k == 0 ? 0.0 : 1.0 / ((double)k * (double)(m + k));
-    r64[i] = v;
-    r32[i] = (float)v;
+// Series tables (once per context): a_k(m) = a_{k-1}(m) * (-1) / (k (m+k))
+// and 1/m! in long double, rounded once to double and to float.
+int upload_bessel_tables(const BesselTab& t) {
+  std::vector<double> c64((size_t)kBesselOrders * kBesselTerms), f64(kBesselOrders);
+  std::vector<float> c32(c64.size()), f32(kBesselOrders);
+  long double fact = 1.0L;
+  for (int m = 0; m < kBesselOrders; ++m) {
+    if (m > 0) fact *= (long double)m;
+    f64[m] = (double)(1.0L / fact);
+    f32[m] = (float)(1.0L / fact);
+    long double a = 1.0L;
+    for (int k = 0; k < kBesselTerms; ++k) {
+      if (k > 0) a = -a / ((long double)k * (long double)(m + k));
+      c64[(size_t)m * kBesselTerms + k] = (double)a;
+      c32[(size_t)m * kBesselTerms + k] = (float)a;
+    }
   }
-  if (i < 35) {
-    double f = 1.0;
-    for (int j = 2; j <= i; ++j) f *= (double)j;
-    f64[i] = 1.0 / f;
-    f32[i] = (float)(1.0 / f);
-  }
+  bool ok = cudaMemcpy(t.c64, c64.data(), c64.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMemcpy(t.c32, c32.data(), c32.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMemcpy(t.f64, f64.data(), f64.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMemcpy(t.f32, f32.data(), f32.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+  return ok ? 0 : -1;
 }
 
 // exp(2 pi i k / 128), k = -64..64, for the FP64 sin/cos of reduced phases;
@@ -141,9 +148,6 @@ __device__ __forceinline__ void sincos2pi_tab(double f, const double2* __restric
   c = fma(t.x, cx, -t.y * sx);
 }
 
-void launch_bessel_tables(BesselTab t, cudaStream_t s) {
-  k_bessel_tables<<<(35 * 32 + 255) / 256, 256, 0, s>>>(t.r64, t.r32, t.f64, t.f32);
-}
 
 // ----------------------------------------------------- interval polynomials
 // Cubic Hermite p(s) = c0 + c1 s + c2 s^2 + c3 s^3 on s in [0,1] from values
@@ -555,11 +559,13 @@ struct AmpStride<float> {
 // the tile), quadratic in st = t / L.
 template <typename T, typename IV>
 __device__ __forceinline__ void tile_harmonics(const IV* iv, int ni, int64_t j0, int64_t kfirst, int ks,
-                                               int n_max, int span, T* bnode, T* bq, const T* __restrict__ rk,
+                                               int n_max, int span, T* bnode, T* bq, const T* __restrict__ bc,
                                                const T* __restrict__ ifact) {
   const int t = threadIdx.x;
   if (t < 3 * n_max) {
-    const int node = t / n_max, n = t % n_max + 1;
+    // harmonic-major: a warp holds neighbouring n, whose series lengths
+    // (growing with x = n e) are alike
+    const int node = t % 3, n = t / 3 + 1;
     // node at offset span*node/2: integer arithmetic in half samples, so no
     // FP64 instruction runs here in the FP32 kernel
     const int64_t pos2 = 2 * j0 + (int64_t)span * node;
@@ -570,7 +576,7 @@ __device__ __forceinline__ void tile_harmonics(const IV* iv, int ni, int64_t j0,
     const T s = T(rem2) / T(2 * ks);
     const T e = T(iv_e(iv[ki], s));
     T out[3];
-    harmonic_amps<T>(n, e, out, rk, ifact);
+    harmonic_amps<T>(n, e, out, bc, ifact);
     bnode[(node * 32 + (n - 1)) * 3 + 0] = out[0];
     bnode[(node * 32 + (n - 1)) * 3 + 1] = out[1];
     bnode[(node * 32 + (n - 1)) * 3 + 2] = out[2];
@@ -621,7 +627,7 @@ constexpr double kPatternFitDtMaxM = 1024.0;    // [s]; fit error < 1e-7 below
 __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
                                                         int64_t n, double dt, double t0, int ks, int n_max,
                                                         double2* __restrict__ z, int unit_scale, int exact_f,
-                                                        const double* __restrict__ rk, const double* __restrict__ ifact,
+                                                        const double* __restrict__ bc, const double* __restrict__ ifact,
                                                         const double* __restrict__ lisa) {
   __shared__ IvD iv[kTile / 64];
   __shared__ double bnode[3 * 32 * 3];
@@ -653,7 +659,7 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
     fit_cubic4<double>(fn[0][q], fn[1][q], fn[2][q], fn[3][q], fq[q]);
   }
   const int span = tile_span(j0, C.j_plunge);
-  tile_harmonics<double, IvD>(iv, ni, j0, kfirst, ks, n_max, span, bnode, bq, rk, ifact);
+  tile_harmonics<double, IvD>(iv, ni, j0, kfirst, ks, n_max, span, bnode, bq, bc, ifact);
   __syncthreads();
   const double inv_span = 1.0 / (double)span;
 
@@ -705,7 +711,7 @@ constexpr int kSegM = 1024;
 __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
                                                           int64_t n, int exact_f, float dphib, int ks, int n_max,
                                                           float2* __restrict__ z, int unit_scale,
-                                                          const float* __restrict__ rk, const float* __restrict__ ifact,
+                                                          const float* __restrict__ bc, const float* __restrict__ ifact,
                                                           const double* __restrict__ lisa, const IvM* __restrict__ ivs) {
   __shared__ IvM iv[kSegM / 64];
   __shared__ float bnode[3 * 32 * 3];
@@ -749,7 +755,7 @@ __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict
   }
   const int span = tile_span(j0, jplunge, kSegM);
   const bool cheb = cheb_s != 0;   // per walker (uniform in the CTA)
-  tile_harmonics<float, IvM>(iv, ni, j0, kfirst, ks, n_max, span, bnode, bq, rk, ifact);
+  tile_harmonics<float, IvM>(iv, ni, j0, kfirst, ks, n_max, span, bnode, bq, bc, ifact);
   __syncthreads();
   const float inv_span = 1.f / (float)span;
   const float inv_ks = 1.f / (float)ks;
@@ -811,11 +817,11 @@ void launch_wave(const Knot* knots, const WalkerC* wc, int w, int64_t n, double 
   if (o.precision == 0) {
     dim3 grid((unsigned)(n / kTile), (unsigned)w);
     k2_wave_f64<<<grid, kTile, 0, s>>>(knots, wc, n, dt, t0, o.ks, o.n_max, (double2*)z, unit_scale ? 1 : 0,
-                                       dt > kPatternFitDtMax64 ? 1 : 0, bt.r64, bt.f64, lisa);
+                                       dt > kPatternFitDtMax64 ? 1 : 0, bt.c64, bt.f64, lisa);
   } else {
     dim3 grid((unsigned)(n / kSegM), (unsigned)w);
     k2_wave_mixed<<<grid, kTile, 0, s>>>(knots, wc, n, dt > kPatternFitDtMaxM ? 1 : 0, (float)(dt / kYear), o.ks,
-                                         o.n_max, (float2*)z, unit_scale ? 1 : 0, bt.r32, bt.f32, lisa,
+                                         o.n_max, (float2*)z, unit_scale ? 1 : 0, bt.c32, bt.f32, lisa,
                                          (const IvM*)ivs);
   }
 }

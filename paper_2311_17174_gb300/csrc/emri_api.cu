@@ -442,7 +442,7 @@ extern "C" int emri_ctx_create(int device, size_t budget, emri_ctx** out) {
   fft_set_smem_limits();
   e2 = cudaStreamSynchronize(c->stream);
   if (e2 == cudaSuccess) e2 = cudaGetLastError();
-  if (e2 == cudaSuccess && upload_exp128()) e2 = cudaErrorUnknown;
+  if (e2 == cudaSuccess && upload_exp512()) e2 = cudaErrorUnknown;
   if (e2 == cudaSuccess && emri::upload_bessel_tables(c->bt)) e2 = cudaErrorUnknown;
   if (e2 != cudaSuccess) {
     cudaFree(p);

@@ -52,8 +52,8 @@ struct BesselTab {
 };
 // fills the tables from the host (synchronous); 0 on success
 int upload_bessel_tables(const BesselTab& t);
-// the FP64 waveform kernel's exp(2 pi i k/128) table on the current device; 0 on success
-int upload_exp128();
+// the FP64 waveform kernel's exp(2 pi i k/512) table on the current device; 0 on success
+int upload_exp512();
 
 void launch_prologue(const double* theta, int64_t ld, int w, int64_t n, double dt, const OptsN& o,
                      const double* gl, WalkerC* out, cudaStream_t s);

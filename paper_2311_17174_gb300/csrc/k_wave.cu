@@ -116,38 +116,38 @@ int upload_bessel_tables(const BesselTab& t) {
   return ok ? 0 : -1;
 }
 
-// exp(2 pi i k / 128), k = -64..64, for the FP64 sin/cos of reduced phases;
-// filled from the host (long double) at context creation.
-__device__ double2 g_exp128[129];
+// exp(2 pi i k / 512), k = -256..256, for the FP64 sin/cos of reduced
+// phases; filled from the host (long double) at context creation.
+constexpr int kExpHalf = 256;
+constexpr int kExpLen = 2 * kExpHalf + 1;
+__device__ double2 g_exp512[kExpLen];
 
-int upload_exp128() {
-  double2 h[129];
+int upload_exp512() {
+  double2 h[kExpLen];
   const long double pi = 3.141592653589793238462643383279502884L;
-  for (int k = -64; k <= 64; ++k) {
-    const long double a = 2.0L * pi * (long double)k / 128.0L;
-    h[k + 64] = make_double2((double)cosl(a), (double)sinl(a));
+  for (int k = -kExpHalf; k <= kExpHalf; ++k) {
+    const long double a = 2.0L * pi * (long double)k / (2.0L * kExpHalf);
+    h[k + kExpHalf] = make_double2((double)cosl(a), (double)sinl(a));
   }
-  return cudaMemcpyToSymbol(g_exp128, h, sizeof(h)) == cudaSuccess ? 0 : -1;
+  return cudaMemcpyToSymbol(g_exp512, h, sizeof(h)) == cudaSuccess ? 0 : -1;
 }
 
-// cos(2 pi f), sin(2 pi f) for a phase |f| <= 1/2 cycle: f = k/128 + d with
-// |d| <= 1/256, exp(2 pi i k/128) from the table and the Taylor polynomials of
-// cos and sin at x = 2 pi d (|x| <= 0.0246: the first omitted terms, x^8/8!
-// and x^9/9!, are below 1e-18).  About 17 FP64 operations.
+// cos(2 pi f), sin(2 pi f) for a phase |f| <= 1/2 cycle: f = k/512 + d with
+// |d| <= 1/1024, exp(2 pi i k/512) from the table and the Taylor polynomials
+// of sin to x^5 and cos to x^4 at x = 2 pi d (|x| <= 0.00614: the first
+// omitted terms, x^7/7! and x^6/6!, are below 7e-20 and 8e-17).  About 14
+// FP64 operations.
 __device__ __forceinline__ void sincos2pi_tab(double f, const double2* __restrict__ tab, double& s, double& c) {
-  const double kd = rint(f * 128.0);
-  const double d = fma(kd, -0.0078125, f);   // exact
+  const double kd = rint(f * 512.0);
+  const double d = fma(kd, -0.001953125, f);   // exact
   const double x = d * 6.283185307179586;
   const double x2 = x * x;
-  const double p = fma(x2, fma(x2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0);
-  const double sx = fma(x2 * x, p, x);
-  const double q = fma(x2, fma(x2, -1.0 / 720.0, 1.0 / 24.0), -0.5);
-  const double cx = fma(x2, q, 1.0);
-  const double2 t = tab[(int)kd + 64];
+  const double sx = fma(x2 * x, fma(x2, 1.0 / 120.0, -1.0 / 6.0), x);
+  const double cx = fma(x2, fma(x2, 1.0 / 24.0, -0.5), 1.0);
+  const double2 t = tab[(int)kd + kExpHalf];
   s = fma(t.y, cx, t.x * sx);
   c = fma(t.x, cx, -t.y * sx);
 }
-
 
 // ----------------------------------------------------- interval polynomials
 // Cubic Hermite p(s) = c0 + c1 s + c2 s^2 + c3 s^3 on s in [0,1] from values
@@ -634,7 +634,7 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
   __shared__ double bq[32 * 9];
   __shared__ double fn[4][4];   // the four patterns at the four fit nodes
   __shared__ double fq[4][4];   // their cubics in t / 256
-  __shared__ double2 ex[129];
+  __shared__ double2 ex[kExpLen];
   __shared__ Geo<double> g;
   const int wk = blockIdx.y;
   const WalkerC& C = wcs[wk];
@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
     antenna_fixed<double>(C.gd, lisa[blockIdx.x * 8 + 2 * q], lisa[blockIdx.x * 8 + 2 * q + 1], scale, fn[q]);
   }
   if (t == 160) g = C.gd;
-  if (t < 129) ex[t] = g_exp128[t];
+  for (int i = t; i < kExpLen; i += kTile) ex[i] = g_exp512[i];
   __syncthreads();
   if (t >= 224 && t < 228 && !exact_f) {
     const int q = t - 224;

@@ -317,11 +317,11 @@ def serve_bench(ctx, precision: int, rate: float, duration: float, n_max: int, s
 
 
 # DRAM bytes per sample of k2_wave_f64 from one ncu capture of the kernel
-# (64 walkers x 2^20 samples, n_max 20: 72.16 MB read + 1013.64 MB written;
+# (64 walkers x 2^20 samples, n_max 20: 71.18 MB read + 1013.20 MB written;
 # profiles/ncu_k2_wave_f64_64w_2p20.md), scaled to a launch by the samples it
 # processes (the kernel's traffic is its 16-byte output per sample plus the
 # per-tile orbit records, both proportional to walkers x samples).
-K2_F64_DRAM_BYTES_PER_SAMPLE = (72.156e6 + 1013.643e6) / (64 * 2 ** 20)
+K2_F64_DRAM_BYTES_PER_SAMPLE = (71.178e6 + 1013.201e6) / (64 * 2 ** 20)
 
 
 def paper_bench(ctx, steps: int, warmup: int):

@@ -229,7 +229,7 @@ int emri_fft_batch(emri_ctx* ctx, void* z_dev, int64_t n, int batch, int precisi
  * allocator.  Same transform, layout and arguments as emri_fft_batch, but no
  * context: the one scratch sequence the second pass needs, and the twiddle
  * tables, are file-scope static device arrays of the library
- * (EMRI_NOALLOC_SCRATCH_BYTES of scratch plus 120 KiB of tables, held on
+ * (EMRI_NOALLOC_SCRATCH_BYTES of scratch plus 184 KiB of tables, held on
  * every GPU that loads the library until the process exits).  Nothing is
  * allocated by the call.
  *  - Limit: one sequence must fit the scratch, n * 16 B (FP64) or n * 8 B

@@ -404,7 +404,7 @@ extern "C" int emri_ctx_create(int device, size_t budget, emri_ctx** out) {
   // twiddle and quadrature tables
   constexpr size_t kBc = (size_t)emri::kBesselOrders * emri::kBesselTerms;
   size_t tb = 4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8 + 64 * 8 + kBc * 12 + emri::kBesselOrders * 12 + 256 +
-              (32 + 129) * 32 * 8;
+              (32 + 129) * 32 * 8 + 4096 * 16;
   char* p = nullptr;
   e2 = cudaMalloc(&p, tb);
   if (e2 != cudaSuccess) {
@@ -418,7 +418,8 @@ extern "C" int emri_ctx_create(int device, size_t budget, emri_ctx** out) {
   c->tw.tb64 = (double2*)(p + 4096 * 16);
   c->tw.ta32 = (float2*)(p + 4096 * 16 + 1024 * 16);
   c->tw.tb32 = (float2*)(p + 4096 * 16 + 1024 * 16 + 4096 * 8);
-  c->gl = (double*)(p + 4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8);
+  c->tw.tc64 = (double2*)(p + 4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8);   // 16-byte aligned offset
+  c->gl = (double*)(p + 4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8 + 4096 * 16);
   {
     char* q = (char*)(c->gl + 64);
     constexpr size_t no = emri::kBesselOrders;

@@ -32,10 +32,11 @@ FftPlan make_fft_plan(int64_t n, int n2 = 0);
 
 // Twiddle tables: ta[i] = exp(-2 pi i i/4096), i < 4096; tb[i] = exp(-2 pi i i/2^22), i < 1024.
 struct Twiddles {
-  double2* ta64;
-  double2* tb64;
+  double2* ta64;   // exp(-2 pi i k / 4096)
+  double2* tb64;   // exp(-2 pi i k / 2^22), k < 1024
   float2* ta32;
   float2* tb32;
+  double2* tc64;   // (cos, tan) of -2 pi k / 4096, |cos| >= 2^-60
 };
 
 void launch_twiddle_init(Twiddles t, cudaStream_t s);

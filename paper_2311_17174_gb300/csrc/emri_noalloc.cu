@@ -32,8 +32,9 @@ using namespace emri;
 // One sequence of scratch: EMRI_NOALLOC_SCRATCH_BYTES (32 MiB) holds 2^21
 // double2 or 2^22 float2 values.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[EMRI_NOALLOC_SCRATCH_BYTES];
-// Twiddle tables (same layout as a context's): ta64[4096], tb64[1024], ta32[4096], tb32[1024].
-static __device__ __align__(256) unsigned char g_noalloc_tables[4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8];
+// Twiddle tables: ta64[4096], tb64[1024], ta32[4096], tb32[1024], tc64[4096].
+static __device__ __align__(256) unsigned char g_noalloc_tables[4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8 +
+                                                                4096 * 16];
 
 namespace {
 
@@ -65,6 +66,7 @@ int setup_device(int dev, cudaStream_t s, DevState** out) {
     st.tw.tb64 = (double2*)(t + 4096 * 16);
     st.tw.ta32 = (float2*)(t + 4096 * 16 + 1024 * 16);
     st.tw.tb32 = (float2*)(t + 4096 * 16 + 1024 * 16 + 4096 * 8);
+    st.tw.tc64 = (double2*)(t + 4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8);
     launch_twiddle_init(st.tw, s);
     fft_set_smem_limits();
     e = cudaStreamSynchronize(s);

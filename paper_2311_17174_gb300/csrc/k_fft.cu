@@ -15,9 +15,10 @@
 // against the data and weights stored in the same (k2-major) order, and
 // writes one pair of partial sums per row.  A final kernel adds a walker's
 // rows in a fixed order, so results are bitwise independent of the batch.
-// Twiddles come from two FP64-built tables:
+// Twiddles come from FP64-built tables:
 //   ta[i] = exp(-2 pi i i / 4096), tb[i] = exp(-2 pi i i / 2^22),
-// exp(-2 pi i m / 2^22) = ta[m >> 10] * tb[m & 1023].
+// exp(-2 pi i m / 2^22) = ta[m >> 10] * tb[m & 1023]; the FP64 butterflies
+// read tc[i] = (cos, tan) of the same angles.
 #include "emri_common.cuh"
 #include "emri_internal.h"
 
@@ -44,13 +45,19 @@ FftPlan make_fft_plan(int64_t n, int n2) {
 }
 
 // ------------------------------------------------------------ twiddles
-__global__ void k_twiddle_init(double2* ta64, double2* tb64, float2* ta32, float2* tb32) {
+// tc64[i] = (cos, tan) of -2 pi i / 4096 for the FMA-folded FP64 butterflies;
+// where the cosine is zero (a quarter turn) it is replaced by 2^-60 and the
+// tangent by sin * 2^60, so c * t = sin exactly and the stray c * Re part is
+// below 1e-18 relative.
+__global__ void k_twiddle_init(double2* ta64, double2* tb64, float2* ta32, float2* tb32, double2* tc64) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < 4096) {
     double s, c;
     sincospi(-2.0 * (double)i / 4096.0, &s, &c);
     ta64[i] = make_double2(c, s);
     ta32[i] = make_float2((float)c, (float)s);
+    const double cf = fabs(c) < 0x1p-60 ? 0x1p-60 : c;
+    tc64[i] = make_double2(cf, s / cf);
   }
   if (i < 1024) {
     double s, c;
@@ -61,7 +68,7 @@ __global__ void k_twiddle_init(double2* ta64, double2* tb64, float2* ta32, float
 }
 
 void launch_twiddle_init(Twiddles t, cudaStream_t s) {
-  k_twiddle_init<<<16, 256, 0, s>>>(t.ta64, t.tb64, t.ta32, t.tb32);
+  k_twiddle_init<<<16, 256, 0, s>>>(t.ta64, t.tb64, t.ta32, t.tb32, t.tc64);
 }
 
 // ----------------------------------------------------- complex helpers
@@ -102,14 +109,22 @@ __device__ __forceinline__ C2 twiddle22(const C2* __restrict__ ta, const C2* __r
   return conj_if(cmul(ta[m >> 10], tb[m & 1023u]), sign);
 }
 
+// x with its sign flipped when sign > 0 (the inverse transform's conjugate
+// twiddles), by an integer XOR on the high word: no FP64 instruction
+__device__ __forceinline__ double flip_sign(double x, int sign) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (sign > 0 ? (long long)0x8000000000000000ULL : 0LL));
+}
+
 // ------------------------------------------------- shared-memory Stockham
 // NB transforms of length L = 2^LG (compile-time), element i of transform c at
 // buf[i*NB + c] (row-major tile; NB = 1 for a single contiguous transform).
 // Butterfly b works on transform b % NB, element b / NB, so consecutive
 // threads touch consecutive addresses.  Each thread stages its outputs in
 // registers so a stage reads everything before anything is overwritten.
+// FP64 only (C2 = double2); tf[i] = (cos, tan) of -2 pi i / 4096.
 template <typename C2, int LG, int NB, int NTH>
-__device__ __forceinline__ void smem_fft(C2* buf, int sign, const C2* __restrict__ ta) {
+__device__ __forceinline__ void smem_fft(C2* buf, int sign, const C2* __restrict__ tf) {
+  static_assert(sizeof(C2) == 16, "FP64 transform");
   constexpr int L = 1 << LG;
   constexpr int NR4 = LG / 2;
   constexpr int NBF4 = NB * (L / 4);
@@ -131,18 +146,36 @@ __device__ __forceinline__ void smem_fft(C2* buf, int sign, const C2* __restrict
         C2* col = buf + c;
         C2 a0 = col[j * NB], a1 = col[(j + Q4) * NB], a2 = col[(j + 2 * Q4) * NB], a3 = col[(j + 3 * Q4) * NB];
         if (st > 0) {
-          const int u = (k * 4096) >> (2 * st + 2);   // twiddle step in 1/4096 cycles
-          a1 = cmul(a1, conj_if(ta[u], sign));
-          a2 = cmul(a2, conj_if(ta[2 * u], sign));
-          a3 = cmul(a3, conj_if(ta[3 * u], sign));
+          // FMA-folded butterfly (after Goedecker): with w = c (1 + i t),
+          // w1 = W^u, w2 = W^2u, w3 = w1 w2,
+          //   y0, y2 = (a0 + w2 a2) +- w1 (a1 + w2 a3)
+          //   y1, y3 = (a0 - w2 a2) -+ i w1 (a1 - w2 a3)   (forward)
+          // in 24 FMAs instead of three products and eight sums (28)
+          const int u = (k * 4096) >> (2 * st + 2);
+          const double2 w1 = tf[u], w2 = tf[2 * u];
+          const double t1 = flip_sign(w1.y, sign), t2 = flip_sign(w2.y, sign), c1 = w1.x, c2 = w2.x;
+          const double2 v2 = make_double2(fma(-t2, a2.y, a2.x), fma(t2, a2.x, a2.y));
+          const double2 v3 = make_double2(fma(-t2, a3.y, a3.x), fma(t2, a3.x, a3.y));
+          const double2 pp = make_double2(fma(c2, v2.x, a0.x), fma(c2, v2.y, a0.y));
+          const double2 pm = make_double2(fma(-c2, v2.x, a0.x), fma(-c2, v2.y, a0.y));
+          const double2 qp = make_double2(fma(c2, v3.x, a1.x), fma(c2, v3.y, a1.y));
+          const double2 qm = make_double2(fma(-c2, v3.x, a1.x), fma(-c2, v3.y, a1.y));
+          const double2 e = make_double2(fma(-t1, qp.y, qp.x), fma(t1, qp.x, qp.y));
+          const double2 f = make_double2(fma(-t1, qm.y, qm.x), fma(t1, qm.x, qm.y));
+          const double c1s = flip_sign(c1, sign);
+          y[r][0] = make_double2(fma(c1, e.x, pp.x), fma(c1, e.y, pp.y));
+          y[r][2] = make_double2(fma(-c1, e.x, pp.x), fma(-c1, e.y, pp.y));
+          y[r][1] = make_double2(fma(c1s, f.y, pm.x), fma(-c1s, f.x, pm.y));
+          y[r][3] = make_double2(fma(-c1s, f.y, pm.x), fma(c1s, f.x, pm.y));
+        } else {
+          const C2 b0 = cadd(a0, a2), b1 = csub(a0, a2), b2 = cadd(a1, a3);
+          const C2 d = csub(a1, a3);
+          const C2 b3 = sign < 0 ? CT<C2>::make(d.y, -d.x) : CT<C2>::make(-d.y, d.x);   // -i d or +i d
+          y[r][0] = cadd(b0, b2);
+          y[r][1] = cadd(b1, b3);
+          y[r][2] = csub(b0, b2);
+          y[r][3] = csub(b1, b3);
         }
-        const C2 b0 = cadd(a0, a2), b1 = csub(a0, a2), b2 = cadd(a1, a3);
-        const C2 d = csub(a1, a3);
-        const C2 b3 = sign < 0 ? CT<C2>::make(d.y, -d.x) : CT<C2>::make(-d.y, d.x);   // -i d or +i d
-        y[r][0] = cadd(b0, b2);
-        y[r][1] = cadd(b1, b3);
-        y[r][2] = csub(b0, b2);
-        y[r][3] = csub(b1, b3);
         dst[r] = c + (((j >> (2 * st)) << (2 * st + 2)) + k) * NB;
       }
     }
@@ -173,10 +206,13 @@ __device__ __forceinline__ void smem_fft(C2* buf, int sign, const C2* __restrict
         const int c = b % NB, j = b / NB;
         const int k = j & (NS - 1);
         C2* col = buf + c;
-        C2 a0 = col[j * NB], a1 = col[(j + H2) * NB];
-        if (NS > 1) a1 = cmul(a1, conj_if(ta[(k * 4096) / (NS * 2)], sign));
-        y[r][0] = cadd(a0, a1);
-        y[r][1] = csub(a0, a1);
+        const C2 a0 = col[j * NB], a1 = col[(j + H2) * NB];
+        // a0 +- w a1 with w = c (1 + i t): 6 FMAs
+        const double2 w = tf[(k * 4096) / (NS * 2)];
+        const double t = flip_sign(w.y, sign);
+        const double2 v = make_double2(fma(-t, a1.y, a1.x), fma(t, a1.x, a1.y));
+        y[r][0] = make_double2(fma(w.x, v.x, a0.x), fma(w.x, v.y, a0.y));
+        y[r][1] = make_double2(fma(-w.x, v.x, a0.x), fma(-w.x, v.y, a0.y));
         dst[r] = c + (((j / NS) * NS * 2) + k) * NB;
       }
     }
@@ -311,13 +347,14 @@ __device__ __forceinline__ void r8_stages(C2* buf, int sign, const C2* __restric
   }
 }
 
-// The transform of a shared tile: radix-8 stages in FP32, radix-4 in FP64.
+// The transform of a shared tile: radix-8 stages in FP32 (tf = (cos, sin)
+// table), FMA-folded radix-4 in FP64 (tf = (cos, tan) table).
 template <typename C2, int LG, int NB, int NTH>
-__device__ __forceinline__ void tile_fft(C2* buf, int sign, const C2* __restrict__ ta) {
+__device__ __forceinline__ void tile_fft(C2* buf, int sign, const C2* __restrict__ tf) {
   if constexpr (sizeof(C2) == 8)
-    r8_stages<C2, LG, NB, NTH, 0>(buf, sign, ta);
+    r8_stages<C2, LG, NB, NTH, 0>(buf, sign, tf);
   else
-    smem_fft<C2, LG, NB, NTH>(buf, sign, ta);
+    smem_fft<C2, LG, NB, NTH>(buf, sign, tf);
 }
 
 template <typename C2>
@@ -390,7 +427,8 @@ struct FftCfg<float2> {
 // index, and written back in place with the inter-pass twiddle.
 template <typename C2, int LG, int NB>
 __global__ void __launch_bounds__(kFftThreads, sizeof(C2) == 8 ? 2 : 1) k3_pass1(C2* __restrict__ z, int64_t n, int n1, int sign, int shift22,
-                                                        const C2* __restrict__ ta, const C2* __restrict__ tb) {
+                                                        const C2* __restrict__ ta, const C2* __restrict__ tb,
+                                                        const C2* __restrict__ tf) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C2* buf = reinterpret_cast<C2*>(smraw);
   constexpr int N2 = 1 << LG;
@@ -398,7 +436,7 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(C2) == 8 ? 2 : 1) k3_pass1
   const int j10 = blockIdx.x * NB;
   tile_load<C2, 8>(buf, zw + j10, n1, NB, N2);
   __syncthreads();
-  tile_fft<C2, LG, NB, kFftThreads>(buf, sign, ta);
+  tile_fft<C2, LG, NB, kFftThreads>(buf, sign, tf);
   // write-back with the inter-pass twiddle W_n^{j1 k2}: a thread keeps its
   // column (kFftThreads is a multiple of NB) and steps k2 by kFftThreads/NB,
   // so the twiddle advances by a fixed factor; it is re-read from the table
@@ -419,7 +457,7 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(C2) == 8 ? 2 : 1) k3_pass1
 template <typename C2, int LG>
 __global__ void __launch_bounds__(kPass2Threads, 2) k4_pass2_store(const C2* __restrict__ y, C2* __restrict__ out,
                                                                    int64_t n, int n2, int sign,
-                                                                   const C2* __restrict__ ta) {
+                                                                   const C2* __restrict__ tf) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C2* buf = reinterpret_cast<C2*>(smraw);
   constexpr int N1 = 1 << LG;
@@ -427,7 +465,7 @@ __global__ void __launch_bounds__(kPass2Threads, 2) k4_pass2_store(const C2* __r
   const C2* row = y + (int64_t)blockIdx.y * n + (int64_t)N1 * k2;
   tile_load<C2, 4>(buf, row, 0, N1, 1);
   __syncthreads();
-  tile_fft<C2, LG, 1, kPass2Threads>(buf, sign, ta);
+  tile_fft<C2, LG, 1, kPass2Threads>(buf, sign, tf);
   C2* o = out + (int64_t)blockIdx.y * n;
   for (int k1 = threadIdx.x; k1 < N1; k1 += kPass2Threads) o[k2 + (int64_t)n2 * k1] = buf[k1];
 }
@@ -554,7 +592,7 @@ struct P2Smem {
 
 template <typename C2, typename WT, typename Acc, int LG, bool FD>
 __global__ void __launch_bounds__(kPass2Threads, sizeof(C2) == 8 ? 4 : 2)
-    k4_pass2_ip(const C2* __restrict__ y, int64_t n, int n2, const C2* __restrict__ ta,
+    k4_pass2_ip(const C2* __restrict__ y, int64_t n, int n2, const C2* __restrict__ tf,
                 const WalkerC* __restrict__ wcs, const C2* __restrict__ dtab, const C2* __restrict__ rtab,
                 const C2* __restrict__ dperm, const WT* __restrict__ wperm, double2* __restrict__ partial,
                 const FdW* __restrict__ fdw) {
@@ -583,7 +621,7 @@ __global__ void __launch_bounds__(kPass2Threads, sizeof(C2) == 8 ? 4 : 2)
   const C2 cnv = cn_factor<C2>(wcs[wk]);
   cp_async_wait<1>();
   __syncthreads();
-  tile_fft<C2, LG, 1, kPass2Threads>(buf, -1, ta);
+  tile_fft<C2, LG, 1, kPass2Threads>(buf, -1, tf);
   cp_async_wait<0>();
   __syncthreads();
   // a thread's own bins (N1/256 of them) in plain arithmetic; the
@@ -716,23 +754,25 @@ static size_t csize() { return sizeof(C2); }
 
 template <typename C2, int NB, int LG>
 static void pass1_inst(C2* z, int batch, const FftPlan& p, int sign, int shift, const C2* ta, const C2* tb,
-                       cudaStream_t s) {
+                       const C2* tf, cudaStream_t s) {
   dim3 g(p.n1 / NB, batch);
-  k3_pass1<C2, LG, NB><<<g, kFftThreads, (size_t)NB * (1 << LG) * sizeof(C2), s>>>(z, p.n, p.n1, sign, shift, ta, tb);
+  k3_pass1<C2, LG, NB><<<g, kFftThreads, (size_t)NB * (1 << LG) * sizeof(C2), s>>>(z, p.n, p.n1, sign, shift, ta, tb,
+                                                                                    tf);
 }
 
 template <typename C2, int NB>
-static void pass1_dispatch(C2* z, int batch, const FftPlan& p, int sign, const C2* ta, const C2* tb, cudaStream_t s) {
+static void pass1_dispatch(C2* z, int batch, const FftPlan& p, int sign, const C2* ta, const C2* tb, const C2* tf,
+                           cudaStream_t s) {
   const int shift = 22 - p.log2n;
   int lg = 0;
   while ((1 << lg) < p.n2) ++lg;
   switch (lg) {
-    case 5: pass1_inst<C2, NB, 5>(z, batch, p, sign, shift, ta, tb, s); break;
-    case 6: pass1_inst<C2, NB, 6>(z, batch, p, sign, shift, ta, tb, s); break;
-    case 7: pass1_inst<C2, NB, 7>(z, batch, p, sign, shift, ta, tb, s); break;
-    case 8: pass1_inst<C2, NB, 8>(z, batch, p, sign, shift, ta, tb, s); break;
-    case 9: pass1_inst<C2, NB, 9>(z, batch, p, sign, shift, ta, tb, s); break;
-    default: pass1_inst<C2, NB, 10>(z, batch, p, sign, shift, ta, tb, s); break;
+    case 5: pass1_inst<C2, NB, 5>(z, batch, p, sign, shift, ta, tb, tf, s); break;
+    case 6: pass1_inst<C2, NB, 6>(z, batch, p, sign, shift, ta, tb, tf, s); break;
+    case 7: pass1_inst<C2, NB, 7>(z, batch, p, sign, shift, ta, tb, tf, s); break;
+    case 8: pass1_inst<C2, NB, 8>(z, batch, p, sign, shift, ta, tb, tf, s); break;
+    case 9: pass1_inst<C2, NB, 9>(z, batch, p, sign, shift, ta, tb, tf, s); break;
+    default: pass1_inst<C2, NB, 10>(z, batch, p, sign, shift, ta, tb, tf, s); break;
   }
 }
 
@@ -740,9 +780,9 @@ void launch_fft_pass1(void* z, int batch, const FftPlan& p, bool fp32, int sign,
                       cudaStream_t s) {
   if (batch <= 0) return;
   if (fp32)
-    pass1_dispatch<float2, FftCfg<float2>::kCols>((float2*)z, batch, p, sign, t.ta32, t.tb32, s);
+    pass1_dispatch<float2, FftCfg<float2>::kCols>((float2*)z, batch, p, sign, t.ta32, t.tb32, t.ta32, s);
   else
-    pass1_dispatch<double2, FftCfg<double2>::kCols>((double2*)z, batch, p, sign, t.ta64, t.tb64, s);
+    pass1_dispatch<double2, FftCfg<double2>::kCols>((double2*)z, batch, p, sign, t.ta64, t.tb64, t.tc64, s);
 }
 
 #define EMRI_LG_SWITCH(lg, CALL)  \
@@ -775,7 +815,7 @@ void launch_fft_pass2_store(const void* y, void* out, int batch, const FftPlan& 
 #undef CALL32
   } else {
 #define CALL64(L) k4_pass2_store<double2, L><<<g, kPass2Threads, p.n1 * sizeof(double2), s>>>( \
-      (const double2*)y, (double2*)out, p.n, p.n2, sign, t.ta64)
+      (const double2*)y, (double2*)out, p.n, p.n2, sign, t.tc64)
     EMRI_LG_SWITCH(lg, CALL64)
 #undef CALL64
   }
@@ -795,7 +835,7 @@ static void pass2_ip_dispatch(const void* y, int w, const FftPlan& p, bool fp32,
 #undef CALLI32
   } else {
 #define CALLI64(L) k4_pass2_ip<double2, double, AccD, L, FD><<<g, kPass2Threads, P2Smem<double2, double, L>::bytes(), s>>>( \
-      (const double2*)y, p.n, p.n2, t.ta64, wc, (const double2*)delay_tab, (const double2*)row_tab,                 \
+      (const double2*)y, p.n, p.n2, t.tc64, wc, (const double2*)delay_tab, (const double2*)row_tab,                 \
       (const double2*)data_perm, (const double*)wt_perm, partial, fd)
     EMRI_LG_SWITCH(lg, CALLI64)
 #undef CALLI64

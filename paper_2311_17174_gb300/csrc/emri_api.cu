@@ -276,7 +276,7 @@ int run_loglike(emri_ctx* ctx, const emri_dataset* ds, const double* theta, int6
     nl += 1;
   }
   const int64_t nk = p.n / o.ks;
-  const void* dperm = f32 ? (const void*)ds->d_perm32 : (const void*)ds->d_perm;
+  const void* dperm = f32 ? (const void*)ds->g_perm32 : (const void*)ds->g_perm;
   const void* wperm = f32 ? (const void*)ds->w_perm32 : (const void*)ds->w_perm;
   const double dh_scale = f32 ? 1.0 / (ds->d_scale * ds->w_scale) : 1.0;
   const double hh_scale = f32 ? 1.0 / ds->w_scale : 1.0;
@@ -549,9 +549,9 @@ extern "C" int emri_dataset_create(emri_ctx* ctx, const emri_grid* grid, const v
     ctx->used += keep;
   }
   Carve k(kp), t(tp);
-  ds->d_perm = k.take<double2>(n);
+  ds->g_perm = k.take<double2>(n);
   ds->w_perm = k.take<double>(n);
-  ds->d_perm32 = k.take<float2>(n);
+  ds->g_perm32 = k.take<float2>(n);
   ds->w_perm32 = k.take<float>(n);
   double2* dnat = t.take<double2>(n);
   double2* scratch = t.take<double2>(n);
@@ -589,7 +589,7 @@ extern "C" int emri_dataset_create(emri_ctx* ctx, const emri_grid* grid, const v
     }
     ds->d_scale = dmax > 0 ? 1.0 / dmax : 1.0;
     ds->w_scale = 1.0 / wmax;
-    launch_dataset_permute(dnat, wnat, ds->plan, ds->d_perm, ds->w_perm, ds->d_perm32, ds->w_perm32, ds->d_scale,
+    launch_dataset_permute(dnat, wnat, ds->plan, ds->g_perm, ds->w_perm, ds->g_perm32, ds->w_perm32, ds->d_scale,
                            ds->w_scale, s);
     launch_inner_dd(dnat, wnat, n, ddv, s);
     if ((e = cudaMemcpyAsync(&ds->dd, ddv, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;

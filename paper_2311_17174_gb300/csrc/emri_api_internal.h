@@ -131,9 +131,9 @@ struct emri_dataset {
   emri::FftPlan plan{};
   char* mem = nullptr;
   size_t bytes = 0;
-  double2* d_perm = nullptr;
+  double2* g_perm = nullptr;   // w conj(D) in pass-2 order (FP64), then the FP32 copies
   double* w_perm = nullptr;
-  float2* d_perm32 = nullptr;
+  float2* g_perm32 = nullptr;
   float* w_perm32 = nullptr;
   double d_scale = 1.0, w_scale = 1.0;
   double dd = 0.0;

@@ -96,10 +96,11 @@ void launch_finalize(const double2* partial, int n2, const WalkerC* wc, int w, d
                      double* lnl, double* dh, double* hh, uint32_t* status, cudaStream_t s);
 void fft_set_smem_limits();
 
-// dataset preparation: permute the natural-order spectrum and weights into
-// the pass-2 order (k2-major), and build FP32 scaled copies
-void launch_dataset_permute(const double2* d_nat, const double* w_nat, const FftPlan& p, double2* d_perm,
-                            double* w_perm, float2* d_perm32, float* w_perm32, double d_scale,
+// dataset preparation: the weighted conjugate spectrum g = w conj(D) and
+// the weights w in the pass-2 order (k2-major), plus FP32 copies scaled by
+// d_scale w_scale and w_scale
+void launch_dataset_permute(const double2* d_nat, const double* w_nat, const FftPlan& p, double2* g_perm,
+                            double* w_perm, float2* g_perm32, float* w_perm32, double d_scale,
                             double w_scale, cudaStream_t s);
 void launch_weights(const double* psd, int64_t n, double dt, double fmin, double fmax, double* w,
                     cudaStream_t s);

@@ -625,30 +625,34 @@ __global__ void __launch_bounds__(kPass2Threads, sizeof(C2) == 8 ? 4 : 2)
   cp_async_wait<0>();
   __syncthreads();
   // a thread's own bins (N1/256 of them) in plain arithmetic; the
-  // compensated accumulator then merges the threads in a fixed order
-  T sdh = T(0), shh = T(0);
+  // compensated accumulator then merges the threads in a fixed order.
+  // The bin's delay factor is a * ts[k1] (times cn for negative
+  // frequencies; the table carries it for k1 > N1/2), and the row factor a
+  // is common to the row: <d|h> collects Z = sum g ts H and takes Re(a Z).
+  T zr = T(0), zi = T(0), shh = T(0);
   FdW fd;
   if (FD) fd = fdw[wk];
   for (int k1 = threadIdx.x; k1 < N1; k1 += kPass2Threads) {
     const C2 H = buf[k1];
     const T wv = SM::kPrefetch ? (T)ws[k1] : (T)wperm[base + k1];
-    const C2 D = SM::kPrefetch ? ds[k1] : dperm[base + k1];
-    C2 f = cmul(a, SM::kPrefetch ? ts[k1] : tabw[k1]);
-    const bool neg = 2 * k1 > N1 || (2 * k1 == N1 && k2 > 0);
-    if (neg) f = cmul(f, cnv);   // signed index k - n
+    const C2 G = SM::kPrefetch ? ds[k1] : dperm[base + k1];
+    C2 P = cmul(H, SM::kPrefetch ? ts[k1] : tabw[k1]);
+    if (2 * k1 == N1 && k2 > 0) P = cmul(P, cnv);   // the one negative bin of this column not in the table
     T A2 = T(1);
     if (FD) {
+      const bool neg = 2 * k1 > N1 || (2 * k1 == N1 && k2 > 0);
       const long long kk = (long long)k2 + (long long)n2 * k1;
       const unsigned long long ak = (unsigned long long)(neg ? n - kk : kk);
       T c, sn;
       const T A = fd_factor<T>(fd, ak, neg, c, sn);
-      f = cmul(f, CT<C2>::make(A * c, A * sn));
+      P = cmul(P, CT<C2>::make(A * c, A * sn));
       A2 = A * A;
     }
-    const C2 Hd = cmul(H, f);
-    sdh += wv * (D.x * Hd.x + D.y * Hd.y);
+    zr += G.x * P.x - G.y * P.y;
+    zi += G.x * P.y + G.y * P.x;
     shh += wv * (H.x * H.x + H.y * H.y) * A2;
   }
+  const T sdh = a.x * zr - a.y * zi;
   Acc acc;
   acc.init();
   acc.add(sdh, shh);
@@ -714,18 +718,24 @@ __global__ void k_weights(const double* __restrict__ psd, int64_t n, double dt, 
   w[k] = in ? 2.0 * dt * dt * df / psd[kk] : 0.0;
 }
 
+// Dataset arrays in pass-2 order (bin k2 + n2 k1 at k2 * n1 + k1): the
+// weighted conjugate data g = w conj(D) (the inner product needs only this
+// product) and the weights w, in FP64 and scaled FP32 (g by ds ws, w by ws).
 __global__ void k_permute(const double2* __restrict__ d, const double* __restrict__ w, int n1, int n2,
-                          double2* __restrict__ dp, double* __restrict__ wp, float2* __restrict__ dp32,
+                          double2* __restrict__ gp, double* __restrict__ wp, float2* __restrict__ gp32,
                           float* __restrict__ wp32, double ds, double ws) {
   const int k1 = blockIdx.x * blockDim.x + threadIdx.x;
   const int k2 = blockIdx.y;
   if (k1 >= n1) return;
   const int64_t src = k2 + (int64_t)n2 * k1, dst = (int64_t)k2 * n1 + k1;
   const double2 v = d[src];
-  dp[dst] = v;
-  wp[dst] = w[src];
-  dp32[dst] = make_float2((float)(v.x * ds), (float)(v.y * ds));
-  wp32[dst] = (float)(w[src] * ws);
+  const double wv = w[src];
+  const double2 g = make_double2(wv * v.x, -(wv * v.y));
+  gp[dst] = g;
+  wp[dst] = wv;
+  const double sc = ds * ws;
+  gp32[dst] = make_float2((float)(g.x * sc), (float)(g.y * sc));
+  wp32[dst] = (float)(wv * ws);
 }
 
 __global__ void k_pack(const double* __restrict__ d2, int64_t n, double2* __restrict__ z) {
@@ -862,11 +872,11 @@ void launch_weights(const double* psd, int64_t n, double dt, double fmin, double
   k_weights<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(psd, n, dt, fmin, fmax, w);
 }
 
-void launch_dataset_permute(const double2* d_nat, const double* w_nat, const FftPlan& p, double2* d_perm,
-                            double* w_perm, float2* d_perm32, float* w_perm32, double d_scale, double w_scale,
+void launch_dataset_permute(const double2* d_nat, const double* w_nat, const FftPlan& p, double2* g_perm,
+                            double* w_perm, float2* g_perm32, float* w_perm32, double d_scale, double w_scale,
                             cudaStream_t s) {
   dim3 g((p.n1 + 255) / 256, p.n2);
-  k_permute<<<g, 256, 0, s>>>(d_nat, w_nat, p.n1, p.n2, d_perm, w_perm, d_perm32, w_perm32, d_scale, w_scale);
+  k_permute<<<g, 256, 0, s>>>(d_nat, w_nat, p.n1, p.n2, g_perm, w_perm, g_perm32, w_perm32, d_scale, w_scale);
 }
 
 void launch_pack_time_series(const double* d2, int64_t n, double2* z, cudaStream_t s) {

@@ -181,9 +181,12 @@ __global__ void k0_prologue(const double* __restrict__ theta, int64_t ld, int w,
 // Per-walker delay tables for the factorisation
 // exp(-2 pi i k r) = exp(-2 pi i k2 r) exp(-2 pi i n2 k1 r) of bin k = k2 + n2 k1:
 // tab[k] = exp(-2 pi i frac(mult k r)), k < count (mult = n2 over k1 < n1, and
-// mult = 1 over k2 < n2).
+// mult = 1 over k2 < n2).  fold_neg: the entries with 2 k > count also carry
+// exp(+2 pi i frac(N r)), the factor of the signed index k - N (negative
+// frequencies).
 template <typename C2>
-__global__ void k0_delay_table(const WalkerC* __restrict__ wc, int count, int mult, C2* __restrict__ tab) {
+__global__ void k0_delay_table(const WalkerC* __restrict__ wc, int count, int mult, int fold_neg,
+                               C2* __restrict__ tab) {
   const int k1 = blockIdx.x * blockDim.x + threadIdx.x;
   const int wk = blockIdx.y;
   if (k1 >= count) return;
@@ -193,9 +196,16 @@ __global__ void k0_delay_table(const WalkerC* __restrict__ wc, int count, int mu
   dd f = dd_frac(p);
   double s, c;
   sincospi(2.0 * f.hi, &s, &c);
+  double vx = c, vy = -s;
+  if (fold_neg && 2 * k1 > count) {
+    const double cr = wc[wk].cn_re, ci = wc[wk].cn_im;
+    const double x = vx * cr - vy * ci;
+    vy = vx * ci + vy * cr;
+    vx = x;
+  }
   C2 v;
-  v.x = c;
-  v.y = -s;
+  v.x = vx;
+  v.y = vy;
   tab[(int64_t)wk * count + k1] = v;
 }
 
@@ -221,11 +231,11 @@ void launch_delay_table(const WalkerC* wc, int w, int n1, int n2, bool fp32, voi
   if (w <= 0) return;
   dim3 g1((n1 + 255) / 256, w), g2((n2 + 255) / 256, w);
   if (fp32) {
-    k0_delay_table<float2><<<g1, 256, 0, s>>>(wc, n1, n2, (float2*)tab);
-    k0_delay_table<float2><<<g2, 256, 0, s>>>(wc, n2, 1, (float2*)rtab);
+    k0_delay_table<float2><<<g1, 256, 0, s>>>(wc, n1, n2, 1, (float2*)tab);
+    k0_delay_table<float2><<<g2, 256, 0, s>>>(wc, n2, 1, 0, (float2*)rtab);
   } else {
-    k0_delay_table<double2><<<g1, 256, 0, s>>>(wc, n1, n2, (double2*)tab);
-    k0_delay_table<double2><<<g2, 256, 0, s>>>(wc, n2, 1, (double2*)rtab);
+    k0_delay_table<double2><<<g1, 256, 0, s>>>(wc, n1, n2, 1, (double2*)tab);
+    k0_delay_table<double2><<<g2, 256, 0, s>>>(wc, n2, 1, 0, (double2*)rtab);
   }
 }
 

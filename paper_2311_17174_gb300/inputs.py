@@ -176,7 +176,10 @@ def config_c2(walkers: int = 1024, n: int = 1 << 21, n_max: int = 20) -> Workloa
     2^21 samples (~1 yr), n <= 20, SNR 50."""
     inj = draw_sources(2, 1, n)[0]
     th = scatter_walkers(1002, inj, walkers)
-    return Workload("c2-1024w-2^21-n20", th, n, DT, n_max, inj, 102, 50.0)
+    lg = int(np.log2(n))
+    name = "c2-1024w-2^21-n20" if (walkers, n, n_max) == (1024, 1 << 21, 20) else \
+        f"c2-recipe-{walkers}w-2^{lg}-n{n_max}"
+    return Workload(name, th, n, DT, n_max, inj, 102, 50.0)
 
 
 def config_c3(walkers: int = 4096, n: int = 1 << 20, snr: float = 50.0) -> Workload:

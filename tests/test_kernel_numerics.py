@@ -1,0 +1,162 @@
+"""CPU pins of the numerical schemes the CUDA kernels use, each restated here
+in numpy from its definition (no kernel code is imported or run):
+
+  * the Bessel power series J_m(x) = (x/2)^m/m! sum_k a_k y^k, y = x^2/4, cut
+    after K = min(ceil(12 + 1.05 x), 48) terms: the omitted tail is below
+    1e-16 of the sum for every order the waveform kernels use (m = n+1, n+2
+    at x = n e, n <= 32, e < 0.999), and Horner's rule over the rounded
+    coefficient table matches scipy's J_m;
+  * the FP64 FFT's FMA-folded radix-4 / radix-2 Stockham stages with
+    (cos, tan) twiddles (|cos| floored at 2^-60): the whole transform, with the
+    kernels' index arithmetic, equals numpy's FFT in both directions;
+  * the FP64 sin/cos of a reduced phase from a 512-point exp table and
+    Taylor polynomials to x^5 / x^4: absolute error ~2 ulp.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.special import gammaln, jv
+
+K_TERMS = 48
+
+
+def series_terms(x: float) -> int:
+    return min(int(12.0 + 1.05 * x) + 1, K_TERMS)
+
+
+def test_bessel_term_count_leaves_tail_below_1e16():
+    for n in range(1, 33):
+        for m in (n + 1, n + 2):
+            for e in np.linspace(0.001, 0.998, 120):
+                x = n * e
+                y = x * x / 4
+                k = np.arange(0, 120)
+                t = np.exp(gammaln(m + 1) - gammaln(k + 1) - gammaln(m + k + 1) + k * np.log(y)) * (-1.0) ** k
+                K = series_terms(x)
+                tail = np.abs(t[K:]).sum()
+                assert tail <= 1e-16 * abs(t.sum()), (n, m, e, K)
+
+
+def bessel_horner(m: int, x: float, table: np.ndarray) -> float:
+    half = 0.5 * x
+    lead = half ** m / math.factorial(m)
+    y = half * half
+    K = series_terms(x)
+    s = table[m, K - 1]
+    for k in range(K - 2, -1, -1):
+        s = s * y + table[m, k]
+    return lead * s
+
+
+def test_bessel_horner_matches_scipy():
+    from fractions import Fraction
+    table = np.zeros((35, K_TERMS))
+    for m in range(35):
+        a = Fraction(1)
+        for k in range(K_TERMS):
+            if k:
+                a = -a / (k * (m + k))
+            table[m, k] = float(a)
+    worst = 0.0
+    for n in range(1, 31):
+        for m in (n + 1, n + 2):
+            for e in np.linspace(0.01, 0.6, 25):
+                ref = jv(m, n * e)
+                worst = max(worst, abs(bessel_horner(m, n * e, table) - ref) / abs(ref))
+    assert worst < 1e-13, worst
+
+
+# ------------------------------------------------------------------ FFT
+def ct_table():
+    i = np.arange(4096)
+    c = np.cos(-2 * np.pi * i / 4096)
+    s = np.sin(-2 * np.pi * i / 4096)
+    c[i % 1024 == 0] = np.rint(c[i % 1024 == 0])          # exact values at quarter turns
+    s[i % 1024 == 0] = np.rint(s[i % 1024 == 0])
+    cf = np.where(np.abs(c) < 2.0 ** -60, 2.0 ** -60, c)
+    return cf, s / cf
+
+
+def stockham_fma(x: np.ndarray, sign: int) -> np.ndarray:
+    """The FP64 shared-memory transform of one row: radix-4 stages (the first
+    without twiddles, the rest FMA-folded), then one FMA-folded radix-2 stage
+    when log2(L) is odd; Stockham indexing as in the kernels."""
+    L = x.size
+    LG = int(np.log2(L))
+    cf, tf = ct_table()
+    if sign > 0:
+        tf = -tf
+    buf = x.astype(np.complex128).copy()
+    Q4 = L // 4
+    for st in range(LG // 2):
+        ns = 1 << (2 * st)
+        j = np.arange(Q4)
+        k = j & (ns - 1)
+        a0, a1, a2, a3 = buf[j], buf[j + Q4], buf[j + 2 * Q4], buf[j + 3 * Q4]
+        if st > 0:
+            u = (k * 4096) >> (2 * st + 2)
+            c1, t1, c2, t2 = cf[u], tf[u], cf[2 * u], tf[2 * u]
+            v2 = (a2.real - t2 * a2.imag) + 1j * (a2.imag + t2 * a2.real)
+            v3 = (a3.real - t2 * a3.imag) + 1j * (a3.imag + t2 * a3.real)
+            pp, pm = a0 + c2 * v2, a0 - c2 * v2
+            qp, qm = a1 + c2 * v3, a1 - c2 * v3
+            e = (qp.real - t1 * qp.imag) + 1j * (qp.imag + t1 * qp.real)
+            f = (qm.real - t1 * qm.imag) + 1j * (qm.imag + t1 * qm.real)
+            c1s = c1 if sign < 0 else -c1
+            y = [pp + c1 * e, (pm.real + c1s * f.imag) + 1j * (pm.imag - c1s * f.real),
+                 pp - c1 * e, (pm.real - c1s * f.imag) + 1j * (pm.imag + c1s * f.real)]
+        else:
+            b0, b1, b2, d = a0 + a2, a0 - a2, a1 + a3, a1 - a3
+            b3 = -1j * d if sign < 0 else 1j * d
+            y = [b0 + b2, b1 + b3, b0 - b2, b1 - b3]
+        dst = ((j >> (2 * st)) << (2 * st + 2)) + k
+        out = np.empty_like(buf)
+        for q in range(4):
+            out[dst + q * ns] = y[q]
+        buf = out
+    if LG & 1:
+        H2 = L // 2
+        NS = 1 << (2 * (LG // 2))
+        j = np.arange(H2)
+        k = j & (NS - 1)
+        a0, a1 = buf[j], buf[j + H2]
+        w = (k * 4096) // (NS * 2)
+        c, t = cf[w], tf[w]
+        v = (a1.real - t * a1.imag) + 1j * (a1.imag + t * a1.real)
+        dst = (j // NS) * NS * 2 + k
+        out = np.empty_like(buf)
+        out[dst] = a0 + c * v
+        out[dst + NS] = a0 - c * v
+        buf = out
+    return buf
+
+
+@pytest.mark.parametrize("lg", [4, 5, 10, 11])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_fma_folded_stockham_equals_dft(lg, sign):
+    g = np.random.default_rng(lg)
+    x = g.standard_normal(1 << lg) + 1j * g.standard_normal(1 << lg)
+    got = stockham_fma(x, sign)
+    ref = np.fft.fft(x) if sign < 0 else np.fft.ifft(x) * x.size
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 2e-15 * lg
+
+
+def test_sincos_512_table():
+    pil = np.longdouble("3.14159265358979323846264338327950288")
+    ks = np.arange(-256, 257).astype(np.longdouble)
+    tc = np.cos(2 * pil * ks / 512).astype(np.float64)
+    ts = np.sin(2 * pil * ks / 512).astype(np.float64)
+    f = np.random.default_rng(3).uniform(-0.5, 0.5, 500_000)
+    kd = np.rint(f * 512.0)
+    d = f - kd / 512.0
+    x = d * 6.283185307179586
+    x2 = x * x
+    sx = (x2 * x) * (x2 * (1 / 120) - 1 / 6) + x
+    cx = x2 * (x2 * (1 / 24) - 0.5) + 1.0
+    idx = kd.astype(int) + 256
+    s = ts[idx] * cx + tc[idx] * sx
+    c = tc[idx] * cx - ts[idx] * sx
+    fl = f.astype(np.longdouble)
+    assert np.abs(s - np.sin(2 * pil * fl)).max() < 4e-16
+    assert np.abs(c - np.cos(2 * pil * fl)).max() < 4e-16

@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C-ABI) with the CPU oracle.
 
-Tolerances (spec bar, read as in the design notes):
+Tolerances (the accuracy bar of the path):
   * FP64 waveform: ||z_gpu - z_oracle||_2 / ||z_oracle||_2 <= 1e-9 per walker;
   * FP64 lnL: |dlnL| <= 1e-9 (|<d|h>| + <h|h>/2) per walker;
   * mixed lnL: |dlnL| <= 1e-2 absolute (SNR ~50).

@@ -101,13 +101,44 @@ def scatter_walkers(seed: int, center: np.ndarray, count: int, rel: float = 1e-4
 
 
 def psd_bc04(n: int, dt: float = DT) -> np.ndarray:
-    """One-sided instrumental noise curve of Barack & Cutler 2004 (the paper's
-    example noise model, Sec. 3) sampled at f_k = k / (N dt), k = 0..N/2:
+    """One-sided instrumental noise curve of Barack & Cutler 2004 (the noise
+    model of the paper's example, Sec. 3) sampled at f_k = k / (N dt), k = 0..N/2:
     S(f) = 9.18e-52 f^-4 + 1.59e-41 + 9.18e-38 f^2  [1/Hz].  The DC entry
     repeats the k=1 value (DC carries no weight)."""
     f = np.arange(n // 2 + 1) / (n * dt)
     f[0] = f[1]
     return 9.18e-52 * f ** -4 + 1.59e-41 + 9.18e-38 * f ** 2
+
+
+# Galactic-confusion fit parameters (alpha, beta, kappa, gamma, f_k) of the
+# Cornish-Robson LISA sensitivity for observation times of 0.5, 1, 2, 4 yr.
+_CR_CONFUSION = {0.5: (0.133, 243.0, 482.0, 917.0, 2.58e-3), 1.0: (0.171, 292.0, 1020.0, 1680.0, 2.15e-3),
+                 2.0: (0.165, 299.0, 611.0, 1340.0, 1.73e-3), 4.0: (0.138, -221.0, 521.0, 1680.0, 1.13e-3)}
+
+
+def psd_cornish_robson(n: int, dt: float = DT, t_obs_yr: float | None = 1.0) -> np.ndarray:
+    """The second noise model the paper's code implements (Sec. 3): the LISA
+    sensitivity of Robson, Cornish & Liu (2019), sampled at f_k = k/(N dt),
+    k = 0..N/2 (DC repeats k = 1):
+      S_n = 10/(3 L^2) [P_oms + 2 (1 + cos^2(f/f*)) P_acc / (2 pi f)^4] (1 + 0.6 (f/f*)^2) + S_c,
+      P_oms = (1.5e-11 m)^2 (1 + (2 mHz/f)^4),
+      P_acc = (3e-15 m/s^2)^2 (1 + (0.4 mHz/f)^2) (1 + (f/8 mHz)^4),
+    L = 2.5e9 m, f* = c/(2 pi L), plus the galactic confusion
+      S_c = 9e-45 f^(-7/3) exp(-f^a + b f sin(k f)) (1 + tanh(g (f_k - f)))
+    for the observation time t_obs_yr (0.5, 1, 2 or 4; None: instrument only).
+    It is an input array: both the oracle and the kernels take it as given."""
+    f = np.arange(n // 2 + 1) / (n * dt)
+    f[0] = f[1]
+    L = 2.5e9
+    fstar = 2.99792458e8 / (2.0 * np.pi * L)
+    p_oms = (1.5e-11) ** 2 * (1.0 + (2e-3 / f) ** 4)
+    p_acc = (3e-15) ** 2 * (1.0 + (0.4e-3 / f) ** 2) * (1.0 + (f / 8e-3) ** 4)
+    s = 10.0 / (3.0 * L * L) * (p_oms + 2.0 * (1.0 + np.cos(f / fstar) ** 2) * p_acc / (2.0 * np.pi * f) ** 4) \
+        * (1.0 + 0.6 * (f / fstar) ** 2)
+    if t_obs_yr is not None:
+        a, b, k, g, fk = _CR_CONFUSION[t_obs_yr]
+        s = s + 9e-45 * f ** (-7.0 / 3.0) * np.exp(-f ** a + b * f * np.sin(k * f)) * (1.0 + np.tanh(g * (fk - f)))
+    return s
 
 
 def noise_spectrum(seed: int, psd: np.ndarray, n: int, dt: float = DT) -> np.ndarray:

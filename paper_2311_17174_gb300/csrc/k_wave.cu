@@ -411,48 +411,46 @@ __device__ __forceinline__ void harmonic_sums2(float cphA, float sphA, float stA
                                                const float* __restrict__ bq, int n_max, bool cheb, float3& sA,
                                                float3& sB) {
   const float2 stA2 = make_float2(stA, stA), stB2 = make_float2(stB, stB);
-  float2 csA = make_float2(cphA, sphA), csB = make_float2(cphB, sphB);
   float2 accA = make_float2(0.f, 0.f), accB = make_float2(0.f, 0.f);
   float rA = 0.f, rB = 0.f;
+  // harmonic n at (cos n Phi, sin n Phi) = csA, csB
+  auto harm = [&](int n, float2 csA, float2 csB) {
+    const float4* b = reinterpret_cast<const float4*>(bq + 12 * n);
+    const float4 x = b[0], y = b[1], z = b[2];
+    const float2 a2 = make_float2(y.x, y.y), a1 = make_float2(x.z, x.w), a0 = make_float2(x.x, x.y);
+    const float2 abA = __ffma2_rn(__ffma2_rn(a2, stA2, a1), stA2, a0);
+    const float2 abB = __ffma2_rn(__ffma2_rn(a2, stB2, a1), stB2, a0);
+    accA = __ffma2_rn(abA, csA, accA);
+    accB = __ffma2_rn(abB, csB, accB);
+    rA = fmaf((z.x * stA + y.w) * stA + y.z, csA.x, rA);
+    rB = fmaf((z.x * stB + y.w) * stB + y.z, csB.x, rB);
+  };
+  // Two harmonics per iteration, each new (cos, sin) pair written over the
+  // one it replaces, so no register copies carry the recurrence.
+  float2 uA = make_float2(cphA, sphA), uB = make_float2(cphB, sphB);   // harmonic n
+  int n = 0;
   if (cheb) {
     const float2 tcA = make_float2(2.f * cphA, 2.f * cphA), tcB = make_float2(2.f * cphB, 2.f * cphB);
-    float2 pvA = make_float2(1.f, 0.f), pvB = make_float2(1.f, 0.f);
-    for (int n = 0; n < n_max; ++n) {
-      const float4* b = reinterpret_cast<const float4*>(bq + 12 * n);
-      const float4 x = b[0], y = b[1], z = b[2];
-      const float2 a2 = make_float2(y.x, y.y), a1 = make_float2(x.z, x.w), a0 = make_float2(x.x, x.y);
-      const float2 abA = __ffma2_rn(__ffma2_rn(a2, stA2, a1), stA2, a0);
-      const float2 abB = __ffma2_rn(__ffma2_rn(a2, stB2, a1), stB2, a0);
-      accA = __ffma2_rn(abA, csA, accA);
-      accB = __ffma2_rn(abB, csB, accB);
-      rA = fmaf((z.x * stA + y.w) * stA + y.z, csA.x, rA);
-      rB = fmaf((z.x * stB + y.w) * stB + y.z, csB.x, rB);
-      const float2 nA = __ffma2_rn(tcA, csA, make_float2(-pvA.x, -pvA.y));
-      const float2 nB = __ffma2_rn(tcB, csB, make_float2(-pvB.x, -pvB.y));
-      pvA = csA;
-      csA = nA;
-      pvB = csB;
-      csB = nB;
+    float2 vA = make_float2(1.f, 0.f), vB = make_float2(1.f, 0.f);      // harmonic n - 1
+    for (; n + 1 < n_max; n += 2) {
+      harm(n, uA, uB);
+      vA = __ffma2_rn(tcA, uA, make_float2(-vA.x, -vA.y));               // harmonic n + 1
+      vB = __ffma2_rn(tcB, uB, make_float2(-vB.x, -vB.y));
+      harm(n + 1, vA, vB);
+      uA = __ffma2_rn(tcA, vA, make_float2(-uA.x, -uA.y));               // harmonic n + 2
+      uB = __ffma2_rn(tcB, vB, make_float2(-uB.x, -uB.y));
     }
   } else {
-    for (int n = 0; n < n_max; ++n) {
-      const float4* b = reinterpret_cast<const float4*>(bq + 12 * n);
-      const float4 x = b[0], y = b[1], z = b[2];
-      const float2 a2 = make_float2(y.x, y.y), a1 = make_float2(x.z, x.w), a0 = make_float2(x.x, x.y);
-      const float2 abA = __ffma2_rn(__ffma2_rn(a2, stA2, a1), stA2, a0);
-      const float2 abB = __ffma2_rn(__ffma2_rn(a2, stB2, a1), stB2, a0);
-      accA = __ffma2_rn(abA, csA, accA);
-      accB = __ffma2_rn(abB, csB, accB);
-      rA = fmaf((z.x * stA + y.w) * stA + y.z, csA.x, rA);
-      rB = fmaf((z.x * stB + y.w) * stB + y.z, csB.x, rB);
-      const float cA = csA.x * cphA - csA.y * sphA;   // rotations by Phi
-      csA.y = csA.y * cphA + csA.x * sphA;
-      csA.x = cA;
-      const float cB = csB.x * cphB - csB.y * sphB;
-      csB.y = csB.y * cphB + csB.x * sphB;
-      csB.x = cB;
+    for (; n + 1 < n_max; n += 2) {
+      harm(n, uA, uB);
+      const float2 vA = make_float2(uA.x * cphA - uA.y * sphA, uA.y * cphA + uA.x * sphA);   // rotations by Phi
+      const float2 vB = make_float2(uB.x * cphB - uB.y * sphB, uB.y * cphB + uB.x * sphB);
+      harm(n + 1, vA, vB);
+      uA = make_float2(vA.x * cphA - vA.y * sphA, vA.y * cphA + vA.x * sphA);
+      uB = make_float2(vB.x * cphB - vB.y * sphB, vB.y * cphB + vB.x * sphB);
     }
   }
+  if (n < n_max) harm(n, uA, uB);
   sA = make_float3(accA.x, accA.y, rA);
   sB = make_float3(accB.x, accB.y, rB);
 }

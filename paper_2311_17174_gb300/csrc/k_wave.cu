@@ -1,29 +1,31 @@
 // k_wave.cu -- steps S2-S4: dense orbit, LISA response and the
-// Peters-Mathews harmonic sum of Eq. (2), one CTA per 256-sample tile.
+// Peters-Mathews harmonic sum of Eq. (2), one CTA per 256-sample tile (FP64)
+// or per 1024-sample segment (mixed).
 //
-// Per tile (prologue, a few threads):
+// Per tile (set-up, a few threads):
 //  * the cubic Hermite interpolant of every orbit quantity over each knot
 //    interval the tile touches (values and rates at both knots);
 //  * the Bessel amplitudes of every harmonic at the tile's start, middle and
 //    end, fitted by a quadratic in time.  The amplitudes depend on time only
 //    through e(t), which moves by ~1e-4 relative per tile, so the quadratic
 //    is exact to ~1e-11 and the per-sample cost of a harmonic drops from a
-//    Bessel evaluation to a few FMAs.
-// Per sample (one thread each):
+//    Bessel evaluation to a few FMAs;
+//  * the four antenna patterns in a fixed sky polarisation basis at four
+//    nodes, fitted by a cubic in time (they depend on time only through the
+//    LISA orbital phase, a one-year period).
+// Per sample (one thread each; two per thread in the mixed kernel):
 //  * phases Phi_D (Doppler folded in), 2 gamma~ and alpha from the Hermite
-//    polynomials, reduced modulo one cycle;
-//  * geometry: L(t) on its precession cone, L.N, the polarisation angle psi
-//    and the angle beta (only 2 psi and 2 beta enter, taken as rational
-//    functions of the two atan2 arguments), the detector-frame source angles
-//    and the antenna patterns of the two Michelson channels;
+//    polynomials, reduced modulo one cycle, and their sin/cos;
 //  * the harmonic sum written as three running sums
 //      C = sum_n n pa_n cos(n Phi), S = sum_n n sqrt(1-e^2) pb_n sin(n Phi),
 //      R = sum_n 2 pc_n cos(n Phi),
-//    with cos(n Phi), sin(n Phi) by complex rotation, so that
-//      h+ = A[(1+c^2)(C cos 2g - S sin 2g) + (1-c^2) R],
-//      hx = -2 c A [S cos 2g + C sin 2g],
-//    which is Eq. (2)'s sum of A+_n and Ax_n regrouped;
-//  * h_I,II = (sqrt3/2)(F+_I,II h+ + Fx_I,II hx), written as z = h_I + i h_II.
+//    with cos(n Phi), sin(n Phi) by the Chebyshev recurrence (or complex
+//    rotation), Eq. (2)'s sum of A+_n and Ax_n regrouped;
+//  * the response as a contraction in the fixed basis: (C, S) rotated by
+//    2 gamma~, a quadratic form in the orbital-plane projections (linear in
+//    cos alpha, sin alpha), times the fitted patterns -- identical to the
+//    psi / beta form of the Barack-Cutler response, without either angle;
+//  * z = h_I + i h_II.
 // FP64 variant: everything in double.  Mixed variant: the three phases are
 // evaluated in 64-bit fixed point (linear term) plus an FP32 correction, so
 // no FP64 instruction runs per sample; the rest is FP32.

@@ -436,10 +436,10 @@ def flop_model(n_max: int) -> float:
     """Algorithmic FP64 flops per sample of the factored harmonic sum and
     response (see the design notes; an FMA counts two): 24 per harmonic
     (rotation 6, three quadratic amplitudes 12, three accumulations 6) plus
-    184 per sample (three phase cubics and x^(2/3) 28, three table sin/cos
-    72, four antenna-pattern cubics 25, fixed-basis response and the two
+    172 per sample (three phase cubics and x^(2/3) 28, three table sin/cos
+    60, four antenna-pattern cubics 25, fixed-basis response and the two
     channels 57, fit time 2)."""
-    return 24.0 * n_max + 184.0
+    return 24.0 * n_max + 172.0
 
 
 # ------------------------------------------------------------ CPU oracle

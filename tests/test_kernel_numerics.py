@@ -10,7 +10,10 @@ in numpy from its definition (no kernel code is imported or run):
     (cos, tan) twiddles (|cos| floored at 2^-60): the whole transform, with the
     kernels' index arithmetic, equals numpy's FFT in both directions;
   * the FP64 sin/cos of a reduced phase from a 512-point exp table and
-    Taylor polynomials to x^5 / x^4: absolute error ~2 ulp.
+    Taylor polynomials to x^5 / x^4: absolute error ~2 ulp;
+  * the mixed path's fixed-point phases (Q0.64 base + tau * increment, the
+    increment reduced mod 1 so that it fits a signed 64-bit integer): the
+    phase mod 1 is exact to 1e-9 cycles at any cycles per sample.
 """
 import math
 
@@ -160,3 +163,43 @@ def test_sincos_512_table():
     fl = f.astype(np.longdouble)
     assert np.abs(s - np.sin(2 * pil * fl)).max() < 4e-16
     assert np.abs(c - np.cos(2 * pil * fl)).max() < 4e-16
+
+
+# ------------------------------------------------- fixed-point phases (mixed)
+def to_q64(f):
+    """Phase fraction in [0, 1) -> unsigned Q0.64."""
+    f = f - math.floor(f)
+    return int(f * 2.0 ** 64) % 2 ** 64
+
+
+def to_q64s(f):
+    """Per-sample increment -> signed Q0.64, reduced mod 1 to [-1/2, 1/2);
+    the kernels convert with a 64-bit signed integer, so the value must fit
+    (without the reduction an increment above half a cycle would not)."""
+    f = f - round(f)
+    if f >= 0.5:
+        f -= 1.0
+    v = int(round(f * 2.0 ** 64))
+    assert -2 ** 63 <= v < 2 ** 63
+    return v
+
+
+@pytest.mark.parametrize("cycles_per_sample", [1e-4, 0.3, 0.7, 3.2, 41.9])
+def test_fixed_point_phase_wraps_mod_one(cycles_per_sample):
+    """The mixed kernels keep a phase as base + tau * inc (mod 2^64) plus a
+    small polynomial correction; the increment is reduced mod 1 first, which
+    matters once a phase moves more than half a cycle per sample (long
+    sample intervals).  The phase mod 1 stays within 1e-9 cycles of the exact
+    value (before the FP32 rounding of the final conversion)."""
+    g = np.random.default_rng(int(cycles_per_sample * 1000))
+    ks = 1024
+    for _ in range(20):
+        c0 = g.uniform(0, 1)
+        c1 = cycles_per_sample * ks          # linear term over the interval [cycles]
+        base, inc = to_q64(c0), to_q64s(c1 / ks)
+        for tau in g.integers(0, ks, 16):
+            p = (base + int(tau) * inc) % 2 ** 64
+            got = p / 2.0 ** 64
+            exact = (c0 + c1 * tau / ks) % 1.0
+            d = abs(got - exact)
+            assert min(d, 1 - d) < 1e-9, (tau, got, exact)

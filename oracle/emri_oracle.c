@@ -42,7 +42,11 @@
  *                            Peters a(e) invariant (e>0)
  *   AK RHS, precession       pinned: periastron advance leading term (x->0),
  *                            Lense-Thirring rate, spin/LT identity
- *   AK RHS, 1PN and spin-orbit radiation-reaction coefficients:
+ *   AK RHS, 1PN dnu/dt at e=0 pinned: textbook test-mass circular chirp
+ *                            (743/336) converted to the radial frequency by
+ *                            the 1PN periastron advance
+ *   AK RHS, the e-dependent 1PN and the spin-orbit radiation-reaction
+ *   coefficients, the 2PN periastron term:
  *                            PARITY UNPINNED (the coefficients come from
  *                            Barack & Cutler 2004, not printed in the paper)
  *   RK4 integrator           pinned: chirp closed form, step halving

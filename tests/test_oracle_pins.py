@@ -158,6 +158,23 @@ def test_periastron_advance_leading_order(oracle_mod):
         assert r[0] == pytest.approx(2 * np.pi * nu, rel=1e-15)
 
 
+def test_nu_dot_1pn_circular_from_chirp_and_periastron_advance(oracle_mod):
+    # The AK frequency nu is the radial (anomalistic) one.  For a test mass on
+    # a circular orbit the textbook 1PN chirp of the azimuthal frequency is
+    #   d w_phi/dt ∝ w_phi^(11/3) (1 - (743/336) x),
+    # and the 1PN periastron advance relates the two, w_phi = w_r (1 + 3 x),
+    # x ∝ w^(2/3).  Then d w_r/dt = d w_phi/dt (1 - 3x - 2x) and
+    # w_phi^(11/3) = w_r^(11/3) (1 + 11 x), so at 1PN
+    #   d nu/dt ∝ nu^(11/3) (1 + (11 - 5 - 743/336) x).
+    # The ratio of the full to the Newtonian rate at e = 0, spin 0 must be that.
+    th = theta_base(M=1e6, mu=10.0, spin=0.0)
+    for x in (1e-4, 1e-3, 1e-2):
+        nu = x ** 1.5 / (2 * np.pi * 1e6 * TSUN)
+        full = O.rhs(th, nu, 0.0, 1)[1]
+        newt = O.rhs(th, nu, 0.0, 0)[1]
+        assert full / newt == pytest.approx(1 + (6 - 743 / 336) * x, rel=1e-12)
+
+
 def test_lense_thirring_rates(oracle_mod):
     # Lense-Thirring precession of L about S: 2 S / (r^3 (1-e^2)^(3/2)), Kepler r^3 = M/(2 pi nu)^2
     # (G = c = 1, seconds); spin-orbit part of the periastron rate = -3 cos(lambda) x that.

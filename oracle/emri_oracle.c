@@ -45,8 +45,11 @@
  *   AK RHS, 1PN dnu/dt at e=0 pinned: textbook test-mass circular chirp
  *                            (743/336) converted to the radial frequency by
  *                            the 1PN periastron advance
- *   AK RHS, the e-dependent 1PN and the spin-orbit radiation-reaction
- *   coefficients, the 2PN periastron term:
+ *   AK RHS, 2PN periastron term at e=0
+ *                            pinned: exact circular-orbit Schwarzschild
+ *                            periastron advance expanded in the radial frequency
+ *   AK RHS, the e-dependent 1PN and 2PN terms and the spin-orbit
+ *   radiation-reaction coefficients:
  *                            PARITY UNPINNED (the coefficients come from
  *                            Barack & Cutler 2004, not printed in the paper)
  *   RK4 integrator           pinned: chirp closed form, step halving

@@ -175,6 +175,26 @@ def test_nu_dot_1pn_circular_from_chirp_and_periastron_advance(oracle_mod):
         assert full / newt == pytest.approx(1 + (6 - 743 / 336) * x, rel=1e-12)
 
 
+def test_periastron_advance_2pn_circular_schwarzschild(oracle_mod):
+    # Test mass on a circular Schwarzschild orbit: w_r = w_phi sqrt(1 - 6 x_phi)
+    # exactly (x_phi = (M w_phi)^(2/3) = M/r), so the advance per radial period,
+    # k = w_phi/w_r - 1, is known in closed form; in the radial variable
+    # x = (M w_r)^(2/3) it expands as 3 x (1 + 6.5 x + O(x^2)).  The oracle's
+    # dgamma~/dt / (2 pi nu) at e = 0, spin 0 must carry that 2PN coefficient.
+    def k_exact(xr):
+        xp = xr
+        for _ in range(200):
+            xp = xr * (1 - 6 * xp) ** (-1 / 3)
+        return (1 - 6 * xp) ** -0.5 - 1
+    th = theta_base(M=1e6, mu=10.0, spin=0.0)
+    for x in (1e-5, 1e-4, 1e-3):
+        nu = x ** 1.5 / (2 * np.pi * 1e6 * TSUN)
+        k_or = O.rhs(th, nu, 0.0, 1)[3] / (2 * np.pi * nu)
+        coef_or = (k_or / (3 * x) - 1) / x
+        coef_ex = (k_exact(x) / (3 * x) - 1) / x
+        assert abs(coef_or - coef_ex) < 60 * x, (x, coef_or, coef_ex)
+
+
 def test_lense_thirring_rates(oracle_mod):
     # Lense-Thirring precession of L about S: 2 S / (r^3 (1-e^2)^(3/2)), Kepler r^3 = M/(2 pi nu)^2
     # (G = c = 1, seconds); spin-orbit part of the periastron rate = -3 cos(lambda) x that.

@@ -227,8 +227,9 @@ int emri_fft_batch(emri_ctx* ctx, void* z_dev, int64_t n, int batch, int precisi
  * application hands it, a process whose device memory is fully reserved by
  * another allocator, or a real-time loop that must never enter the
  * allocator.  Same transform, layout and arguments as emri_fft_batch, but no
- * context: the one scratch sequence the second pass needs, and the twiddle
- * tables, are file-scope static device arrays of the library
+ * context: the scratch the second pass writes (32 MiB: at least one whole
+ * sequence, several when they are shorter) and the twiddle tables are
+ * file-scope static device arrays of the library
  * (EMRI_NOALLOC_SCRATCH_BYTES of scratch plus 184 KiB of tables, held on
  * every GPU that loads the library until the process exits).  Nothing is
  * allocated by the call.
@@ -238,7 +239,8 @@ int emri_fft_batch(emri_ctx* ctx, void* z_dev, int64_t n, int batch, int precisi
  *    batch size is accepted (processed in chunks that fit the scratch).
  *  - The first call on a device (the current device) resolves the arrays'
  *    addresses with cudaGetSymbolAddress and fills the tables, synchronising
- *    `stream`; make that first call before any stream capture.
+ *    `stream`; make that first call before any stream capture (a first call
+ *    on a capturing stream returns EMRI_EINVAL and does nothing).
  *  - All calls on a device share the scratch: calls whose work overlaps on
  *    the GPU (different streams, unordered host threads) race. */
 #define EMRI_NOALLOC_SCRATCH_BYTES (32u << 20)

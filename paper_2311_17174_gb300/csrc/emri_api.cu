@@ -249,11 +249,12 @@ int pick_wave(emri_ctx* ctx, const FftPlan& p, const OptsN& o, int w) {
   const size_t cs = o.precision ? sizeof(float2) : sizeof(double2);
   const size_t per = (size_t)p.n * cs;
   int plan = ctx_plan_wave(ctx, p.n, o);
-  if (plan > 0) return std::min(plan, w);
-  // default: waves of up to 16 GiB of time series
+  if (plan > 0) return std::min({plan, w, kMaxGridY});
+  // default: waves of up to 16 GiB of time series (and at most 65535
+  // walkers, the kernels' grid y)
   size_t cap = (size_t)16 << 30;
   int wave = (int)std::max<size_t>(1, cap / per);
-  return std::min(wave, w);
+  return std::min({wave, w, kMaxGridY});
 }
 
 // The launch sequence of steps S0-S7 for W walkers of one dataset.
@@ -717,7 +718,9 @@ extern "C" int emri_fft_batch(emri_ctx* ctx, void* z, int64_t n, int batch, int 
   const bool f32 = precision == EMRI_MIXED;
   const size_t cs = f32 ? 8 : 16;
   const FftPlan p = make_fft_plan(n);
-  const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(batch, ((int64_t)1 << 30) / ((int64_t)n * cs)));
+  // at most 1 GiB of scratch, and at most 65535 sequences (the passes' grid y)
+  const int chunk = (int)std::max<int64_t>(
+      1, std::min<int64_t>({(int64_t)batch, ((int64_t)1 << 30) / ((int64_t)n * (int64_t)cs), (int64_t)kMaxGridY}));
   if ((rc = ctx->ws.reserve(ctx, (size_t)chunk * n * cs + 256, s))) return rc;
   ctx->ws.acquire(s);
   int64_t nl = 0;

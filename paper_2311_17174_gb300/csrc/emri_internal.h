@@ -10,6 +10,10 @@ struct WalkerC;
 struct Knot;
 struct FdW;
 
+// Largest grid y of a launch: the batched kernels put walkers (or
+// sequences) on grid y, so a call processes at most this many per launch.
+constexpr int kMaxGridY = 65535;
+
 // Options after defaults and validation.
 struct OptsN {
   int precision;   // 0 FP64, 1 mixed
@@ -66,7 +70,7 @@ void launch_fdprop(const double* theta, int64_t ld, int w, int64_t n, double dt,
                    double fstar, const double* coef, FdW* fd, cudaStream_t s);
 
 // orbit: knots[w][nk+1], nk = n / ks
-// mcpi_tab: Chebyshev-Picard tables (qn then qk); NULL selects the serial RK4 integrator
+// mcpi_tab: Chebyshev-Picard tables (qn then qk), required
 void launch_orbit(WalkerC* wc, int w, int64_t n, double dt, double t0, const OptsN& o, Knot* knots,
                   const double* mcpi_tab, cudaStream_t s);
 

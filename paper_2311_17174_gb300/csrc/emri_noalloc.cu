@@ -8,14 +8,17 @@
 // callers cannot create an emri_ctx (its creation allocates tables and
 // workspaces), so this entry point takes no context at all.
 //
-// How: the FFT's second pass writes out of place, so it needs one scratch
-// sequence.  That scratch, and the twiddle tables the passes read, are
-// file-scope static device arrays of fixed size, present on every GPU that
-// loads the library until the process exits.  Their device addresses are
-// looked up once per device (cudaGetSymbolAddress, with that device current)
-// the first time the entry point runs there; that first call also fills the
-// twiddle tables and synchronises the stream, so it should come before any
-// stream capture.  Nothing here calls cudaMalloc, cudaFree or an allocating
+// How: the FFT's second pass writes out of place into scratch memory.  That
+// scratch (32 MiB, at least one whole sequence: 2^21 double2 or 2^22 float2
+// values, and several sequences per pass when they are shorter) and the
+// twiddle tables the passes read are file-scope static device arrays of
+// fixed size, present on every GPU that loads the library until the process
+// exits.  Their device addresses are looked up once per device
+// (cudaGetSymbolAddress, with that device current) the first time the entry
+// point runs there; that first call also fills the twiddle tables and
+// synchronises the stream, so it must not be made while the stream is being
+// captured (it is refused with EMRI_EINVAL then; later calls may be).
+// Nothing here calls cudaMalloc, cudaFree or an allocating
 // library routine.  Every call on a device shares the same scratch, so calls
 // whose work overlaps on the GPU (different streams, or host threads without
 // ordering) race; the scratch is fully overwritten by each call, so nothing
@@ -29,8 +32,8 @@
 
 using namespace emri;
 
-// One sequence of scratch: EMRI_NOALLOC_SCRATCH_BYTES (32 MiB) holds 2^21
-// double2 or 2^22 float2 values.
+// Scratch of EMRI_NOALLOC_SCRATCH_BYTES (32 MiB): at least one sequence
+// (2^21 double2 or 2^22 float2 values), more when they are shorter.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[EMRI_NOALLOC_SCRATCH_BYTES];
 // Twiddle tables: ta64[4096], tb64[1024], ta32[4096], tb32[1024], tc64[4096].
 static __device__ __align__(256) unsigned char g_noalloc_tables[4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8 +
@@ -55,6 +58,14 @@ int setup_device(int dev, cudaStream_t s, DevState** out) {
   std::lock_guard<std::mutex> lk(g_mu);
   DevState& st = g_dev[dev];
   if (!st.ready) {
+    // the set-up below synchronises the stream, which a capture forbids
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+    if (ce != cudaSuccess) return cuda_err(ce, "cudaStreamIsCapturing");
+    if (cap != cudaStreamCaptureStatusNone)
+      return set_err(EMRI_EINVAL,
+                     "emri_fft_batch_noalloc: the first call on a device sets up its tables and must not be made "
+                     "while the stream is being captured");
     void* sp = nullptr;
     void* tp = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&sp, g_noalloc_scratch);

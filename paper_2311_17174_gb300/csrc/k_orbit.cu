@@ -177,39 +177,6 @@ __device__ bool rk4_span(const OrbSrc& s, const WalkerC& c, OrbState& y, int64_t
   return true;
 }
 
-__global__ void k1_orbit(WalkerC* __restrict__ wcs, int w, int64_t n, double dt, double t0, int ks, int pn,
-                         int doppler, Knot* __restrict__ knots) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= w) return;
-  const WalkerC c = wcs[i];
-  const int64_t nk = n / ks;
-  Knot* kn = knots + (int64_t)i * (nk + 1);
-  if (c.status & ST_BADPARAM) {
-    Knot zk = {};
-    for (int64_t k = 0; k <= nk; ++k) kn[k] = zk;
-    wcs[i].j_plunge = 0;
-    return;
-  }
-  OrbSrc s{c.kv, c.ke, c.inv2pim, c.spin, c.coslam, pn};
-  OrbState y{c.v0_hi, c.v0_lo, c.e0, 0.0, c.phi0c, 0.0, c.gam0c, 0.0, c.alp0c, 0.0};
-  int64_t jp = n;
-  uint32_t st = 0;
-  double r[5];
-  ak_rhs_v(s, y.v_hi, y.e_hi, r[0], r[1], r[2], r[3], r[4]);
-  write_knot(kn, y, r, c, t0, doppler);
-  int64_t last = 0;   // last knot written
-  if (plunged(y.v_hi, y.e_hi)) {
-    jp = 0;
-    st |= ST_PLUNGE;
-  } else {
-    rk4_span(s, c, y, 0, nk, ks, dt, t0, doppler, n, kn, jp, st, last);
-  }
-  // knots past a plunge repeat the last one written (their samples are zeroed)
-  for (int64_t q = last + 1; q <= nk; ++q) kn[q] = kn[last];
-  wcs[i].j_plunge = jp;
-  wcs[i].status = c.status | st;
-}
-
 // ------------------------------------------------------ Chebyshev-Picard
 // qn[j*32 + i] = int_0^{tau_i} l_j(tau) dtau (transposed, nodes tau_i =
 // (1 - cos(pi i/31))/2 on the unit segment); qk[q*32 + j] = int_0^{q/128} l_j,
@@ -386,7 +353,7 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi(WalkerC* __res
       serial = anybad;
     }
     if (serial) {
-      // lane 0 redoes the segment with the knot-step RK4 of k1_orbit from
+      // lane 0 redoes the segment with knot-step RK4 (rk4_span) from
       // the segment start; its knots replace any written above
       warm = false;
       __syncwarp();
@@ -617,11 +584,9 @@ void launch_orbit(WalkerC* wc, int w, int64_t n, double dt, double t0, const Opt
   if (o.mode == 1) {   // backward from the LSO (the integration tables are always present)
     k1_orbit_mcpi_back<<<(w + kOrbitWarps - 1) / kOrbitWarps, 32 * kOrbitWarps, smem, s>>>(
         wc, w, n, dt, t0, o.ks, o.pn_terms, o.doppler, mcpi_tab, mcpi_tab + 32 * 32, knots);
-  } else if (mcpi_tab) {
+  } else {
     k1_orbit_mcpi<<<(w + kOrbitWarps - 1) / kOrbitWarps, 32 * kOrbitWarps, smem, s>>>(
         wc, w, n, dt, t0, o.ks, o.pn_terms, o.doppler, mcpi_tab, mcpi_tab + 32 * 32, knots);
-  } else {
-    k1_orbit<<<(w + 31) / 32, 32, 0, s>>>(wc, w, n, dt, t0, o.ks, o.pn_terms, o.doppler, knots);
   }
 }
 

@@ -228,14 +228,17 @@ void launch_prologue(const double* theta, int64_t ld, int w, int64_t n, double d
 }
 
 void launch_delay_table(const WalkerC* wc, int w, int n1, int n2, bool fp32, void* tab, void* rtab, cudaStream_t s) {
-  if (w <= 0) return;
-  dim3 g1((n1 + 255) / 256, w), g2((n2 + 255) / 256, w);
-  if (fp32) {
-    k0_delay_table<float2><<<g1, 256, 0, s>>>(wc, n1, n2, 1, (float2*)tab);
-    k0_delay_table<float2><<<g2, 256, 0, s>>>(wc, n2, 1, 0, (float2*)rtab);
-  } else {
-    k0_delay_table<double2><<<g1, 256, 0, s>>>(wc, n1, n2, 1, (double2*)tab);
-    k0_delay_table<double2><<<g2, 256, 0, s>>>(wc, n2, 1, 0, (double2*)rtab);
+  // walkers on grid y, at most kMaxGridY per launch
+  for (int w0 = 0; w0 < w; w0 += kMaxGridY) {
+    const int ww = w - w0 < kMaxGridY ? w - w0 : kMaxGridY;
+    dim3 g1((n1 + 255) / 256, ww), g2((n2 + 255) / 256, ww);
+    if (fp32) {
+      k0_delay_table<float2><<<g1, 256, 0, s>>>(wc + w0, n1, n2, 1, (float2*)tab + (int64_t)w0 * n1);
+      k0_delay_table<float2><<<g2, 256, 0, s>>>(wc + w0, n2, 1, 0, (float2*)rtab + (int64_t)w0 * n2);
+    } else {
+      k0_delay_table<double2><<<g1, 256, 0, s>>>(wc + w0, n1, n2, 1, (double2*)tab + (int64_t)w0 * n1);
+      k0_delay_table<double2><<<g2, 256, 0, s>>>(wc + w0, n2, 1, 0, (double2*)rtab + (int64_t)w0 * n2);
+    }
   }
 }
 

@@ -259,8 +259,12 @@ __global__ void k_lisa_tiles(int64_t ntiles, double t0, double dt, double* __res
 void launch_intervals_mixed(const Knot* knots, int w, int64_t n, int ks, double dt, void* ivs, cudaStream_t s) {
   if (w <= 0) return;
   const int64_t nk = n / ks;
-  dim3 g((unsigned)((nk + 127) / 128), (unsigned)w);
-  k1b_intervals<<<g, 128, 0, s>>>(knots, nk, ks, dt, (IvM*)ivs);
+  // walkers on grid y, at most kMaxGridY per launch
+  for (int w0 = 0; w0 < w; w0 += kMaxGridY) {
+    const int ww = w - w0 < kMaxGridY ? w - w0 : kMaxGridY;
+    dim3 g((unsigned)((nk + 127) / 128), (unsigned)ww);
+    k1b_intervals<<<g, 128, 0, s>>>(knots + (int64_t)w0 * (nk + 1), nk, ks, dt, (IvM*)ivs + (int64_t)w0 * nk);
+  }
 }
 
 void launch_lisa_tiles(int64_t n, double t0, double dt, double* tab, cudaStream_t s) {
@@ -814,15 +818,21 @@ void launch_wave(const Knot* knots, const WalkerC* wc, int w, int64_t n, double 
                  const OptsN& o, void* z, bool unit_scale, const BesselTab& bt, const double* lisa, const void* ivs,
                  cudaStream_t s) {
   if (w <= 0) return;
-  if (o.precision == 0) {
-    dim3 grid((unsigned)(n / kTile), (unsigned)w);
-    k2_wave_f64<<<grid, kTile, 0, s>>>(knots, wc, n, dt, t0, o.ks, o.n_max, (double2*)z, unit_scale ? 1 : 0,
-                                       dt > kPatternFitDtMax64 ? 1 : 0, bt.c64, bt.f64, lisa);
-  } else {
-    dim3 grid((unsigned)(n / kSegM), (unsigned)w);
-    k2_wave_mixed<<<grid, kTile, 0, s>>>(knots, wc, n, dt > kPatternFitDtMaxM ? 1 : 0, (float)(dt / kYear), o.ks,
-                                         o.n_max, (float2*)z, unit_scale ? 1 : 0, bt.c32, bt.f32, lisa,
-                                         (const IvM*)ivs);
+  const int64_t nk = n / o.ks;
+  // walkers on grid y, at most kMaxGridY per launch
+  for (int w0 = 0; w0 < w; w0 += kMaxGridY) {
+    const int ww = w - w0 < kMaxGridY ? w - w0 : kMaxGridY;
+    const Knot* kn = knots + (int64_t)w0 * (nk + 1);
+    if (o.precision == 0) {
+      dim3 grid((unsigned)(n / kTile), (unsigned)ww);
+      k2_wave_f64<<<grid, kTile, 0, s>>>(kn, wc + w0, n, dt, t0, o.ks, o.n_max, (double2*)z + (int64_t)w0 * n,
+                                         unit_scale ? 1 : 0, dt > kPatternFitDtMax64 ? 1 : 0, bt.c64, bt.f64, lisa);
+    } else {
+      dim3 grid((unsigned)(n / kSegM), (unsigned)ww);
+      k2_wave_mixed<<<grid, kTile, 0, s>>>(kn, wc + w0, n, dt > kPatternFitDtMaxM ? 1 : 0, (float)(dt / kYear),
+                                           o.ks, o.n_max, (float2*)z + (int64_t)w0 * n, unit_scale ? 1 : 0, bt.c32,
+                                           bt.f32, lisa, (const IvM*)ivs + (int64_t)w0 * nk);
+    }
   }
 }
 

@@ -5,8 +5,10 @@ application hands it, a process whose device memory another allocator has
 fully reserved, a real-time loop that must not enter the allocator).  This
 entry point gives them the library's batched FFT with a fixed, library-owned
 static scratch instead of a context.  The test calls it through the C-ABI
-twice in a row (different sizes, precisions and directions) and compares with
-emri_fft_batch, and checks that an oversized sequence is refused.  It runs
+on several calls in a row (different sizes, precisions and directions,
+batches that take one and several passes of its scratch) and compares every
+sequence with emri_fft_batch, and checks that an oversized sequence is
+refused.  It runs
 last so that a failure here leaves every other test already run.
 """
 import numpy as np
@@ -22,8 +24,13 @@ def test_fft_noalloc_matches_fft_batch_twice():
         pytest.skip("no CUDA device")
     ctx = emri.Context(0)
     g = np.random.default_rng(2024)
+    # the last two cases take more than one pass of the 32 MiB scratch: three
+    # 16 MiB FP64 sequences (two, then one), and two 2^21 FP64 sequences that
+    # each fill the whole scratch
     cases = [(1 << 16, emri.FP64, -1, 3, torch.complex128, 1e-14),
-             (1 << 18, emri.MIXED, +1, 5, torch.complex64, 3e-6)]
+             (1 << 18, emri.MIXED, +1, 5, torch.complex64, 3e-6),
+             (1 << 20, emri.FP64, -1, 3, torch.complex128, 1e-14),
+             (1 << 21, emri.FP64, +1, 2, torch.complex128, 1e-14)]
     for n, prec, sign, batch, dtype, tol in cases:
         x = g.standard_normal((batch, n)) + 1j * g.standard_normal((batch, n))
         ref = torch.tensor(x, dtype=dtype, device="cuda:0")

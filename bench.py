@@ -245,19 +245,31 @@ def time_steps(ctx, ds, theta_dev, o, lnl, steps, warmup, flush, barrier):
     return times
 
 
-def serve_bench(ctx, precision: int, rate: float, duration: float, n_max: int, seed: int = 5,
+def serve_datasets(ctx, count: int = 16):
+    """The serving configuration's resident datasets: ``count`` seeded noise
+    datasets spread over the lengths 2^16..2^22 (dataset i has length
+    2^(16 + i mod 7)).  Returns {n: [datasets of that length]}."""
+    from paper_2311_17174_gb300 import emri, inputs as I
+    out = {}
+    for i in range(count):
+        n = 1 << (16 + i % 7)
+        psd = I.psd_bc04(n)
+        ds = ctx.dataset(emri.grid(n, I.DT), I.noise_spectrum(700 + i, psd, n), psd, 1e-4, 1 / (2 * I.DT))
+        out.setdefault(n, []).append(ds)
+    return out
+
+
+def serve_bench(ctx, dsets, precision: int, rate: float, duration: float, n_max: int, seed: int = 5,
                 queue_capacity: int = 4096):
-    """Poisson-arriving requests (8-512 walkers, 2^16-2^22 samples, one
-    resident noise dataset per length) through the serving loop; latency is
-    completion minus arrival as stamped by the library."""
+    """Poisson-arriving requests (8-512 walkers, 2^16-2^22 samples; a request
+    of length n uses the resident dataset of that length its dataset index
+    selects) through the serving loop; latency is completion minus arrival as
+    stamped by the library.  Served lnL/s counts the walkers of completed
+    requests over the time from the first arrival to the last completion;
+    requests refused by a full queue are counted apart."""
     import threading
     from paper_2311_17174_gb300 import emri, inputs as I
     sched = I.config_c5(rate, duration, seed=seed)
-    dsets = {}
-    for logn in range(16, 23):
-        n = 1 << logn
-        psd = I.psd_bc04(n)
-        dsets[n] = ctx.dataset(emri.grid(n, I.DT), I.noise_spectrum(700 + logn, psd, n), psd, 1e-4, 1 / (2 * I.DT))
     src = I.draw_sources(seed, 1, 1 << 22)[0]
     pool = I.scatter_walkers(seed + 1, src, 512)
     o = emri.opts(precision=precision, n_max=n_max)
@@ -294,7 +306,7 @@ def serve_bench(ctx, precision: int, rate: float, duration: float, n_max: int, s
         if dt_ > 0:
             time.sleep(dt_)
         try:
-            tk = ctx.serve_submit(dsets[n], pool[:w].T.copy(), o)
+            tk = ctx.serve_submit(dsets[n][dsi % len(dsets[n])], pool[:w].T.copy(), o)
         except emri.EmriError as exc:   # a full queue refuses the request (EAGAIN)
             if exc.code != emri.EAGAIN:
                 raise
@@ -307,13 +319,12 @@ def serve_bench(ctx, precision: int, rate: float, duration: float, n_max: int, s
     th.join()
     elapsed = time.perf_counter() - t0
     ctx.serve_stop()
-    for d in dsets.values():
-        d.close()
     lat = np.array(lat)
     return {"precision": "fp64" if precision == 0 else "mixed", "rate_per_s": rate, "requests": int(len(lat)),
             "rejected": rejected[0], "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
             "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
-            "lnl_per_s": walkers[0] / elapsed, "seconds": elapsed, "slots": 4, "queue_capacity": queue_capacity}
+            "lnl_per_s": walkers[0] / elapsed, "seconds": elapsed, "slots": 4, "queue_capacity": queue_capacity,
+            "resident_datasets": sum(len(v) for v in dsets.values())}
 
 
 # DRAM bytes per sample of k2_wave_f64 from one ncu capture of the kernel
@@ -430,6 +441,59 @@ def stretch_bench(ctx, ds, theta_np, wl, steps: int, warmup: int, flush):
         res[name] = {"ms_per_step": tot / steps, "lnl_per_s": w * steps / (tot / 1e3),
                      "acceptance": accepted / (w * steps)}
     return {"walkers": w, "free_parameters": "M, mu, S/M^2, Xi_0", **res}
+
+
+def sharded_bench(ctx, args, rank: int, world: int, steps: int, warmup: int, flush, barrier):
+    """One ensemble of W x world walkers spread over the ranks (walker blocks
+    of each half per GPU, an all-gather of the moved blocks after each
+    half-step over NCCL): every rank builds the same seeded data and
+    ensemble, moves its blocks with emri_stretch_half and holds the whole
+    ensemble after each step.  lnL/s counts all ranks' proposals over the
+    slowest rank's time (max over ranks)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2311_17174_gb300 import emri, ensemble as EN, inputs as I
+
+    w = args.walkers * world
+    wl = I.config_c2(walkers=w, n=1 << args.logn, n_max=args.n_max)
+    ds, th, _ = injected_dataset(ctx, wl, wl.noise_seed)
+    free = [I.I_M, I.I_MU, I.I_SPIN, I.I_XI0]
+    lo, hi = np.full(16, -np.inf), np.full(16, np.inf)
+    for p_ in free:
+        c = wl.injection[p_]
+        lo[p_], hi[p_] = c * (1 - 1e-3), c * (1 + 1e-3)
+    lo[I.I_SPIN], hi[I.I_SPIN] = 0.0, 1.0
+    cfg = emri.stretch_cfg(free, lo, hi)
+    o = emri.opts(precision=emri.MIXED, n_max=wl.n_max)
+    dev = f"cuda:{torch.cuda.current_device()}"
+    theta = torch.tensor(th.T.copy(), device=dev)
+    lnp = torch.zeros(w, dtype=torch.float64, device=dev)
+    acc = torch.zeros(w, dtype=torch.int32, device=dev)
+    ctx.loglike_batch(ds, theta, o, lnp)
+    g = np.random.default_rng(13)
+    us = [torch.tensor(g.random((3, w)), device=dev) for _ in range(warmup + steps)]
+    ens = EN.ShardedEnsemble(ctx, ds, o, cfg, rank, world)
+    for k in range(warmup):
+        ens.step(theta, lnp, us[k], acc)
+    torch.cuda.synchronize()
+    times = []
+    for k in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ens.step(theta, lnp, us[warmup + k], acc)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    tot = torch.tensor([float(sum(times))], device=dev)
+    dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    ds.close()
+    return {"walkers": w, "ranks": world, "precision": "mixed", "ms_per_step": float(tot.item()) / steps,
+            "lnl_per_s": w * steps / (float(tot.item()) / 1e3),
+            "exchange": "all-gather of the moved walker blocks after each half-step (NCCL)"}
 
 
 def flop_model(n_max: int) -> float:
@@ -589,20 +653,35 @@ def main():
         e2e_tot = float(t.item())
 
     # ---- serving: p50/p99 latency under Poisson arrivals (rank 0)
+    # light load (the loop keeps up: latency) and a saturating rate per
+    # precision (queue full: served lnL/s is the loop's capacity)
     serving = None
-    if rank == 0 and args.serve_seconds > 0:
-        serving = [serve_bench(ctx, emri.MIXED, 20.0, args.serve_seconds, wl.n_max),
-                   serve_bench(ctx, emri.FP64, 1.5, args.serve_seconds, wl.n_max)]
-    if rank == 0 and args.serve_sweep:
-        serving = (serving or []) + \
-            [serve_bench(ctx, emri.MIXED, r, 4.0, wl.n_max, queue_capacity=64) for r in (10, 30, 100, 300, 1000, 2000)] + \
-            [serve_bench(ctx, emri.FP64, r, 4.0, wl.n_max, queue_capacity=64) for r in (1, 3, 10, 30)]
+    if rank == 0 and (args.serve_seconds > 0 or args.serve_sweep):
+        sdsets = serve_datasets(ctx)
+        if args.serve_seconds > 0:
+            serving = [serve_bench(ctx, sdsets, emri.MIXED, 20.0, args.serve_seconds, wl.n_max),
+                       serve_bench(ctx, sdsets, emri.FP64, 1.5, args.serve_seconds, wl.n_max),
+                       serve_bench(ctx, sdsets, emri.MIXED, 300.0, args.serve_seconds, wl.n_max, queue_capacity=32),
+                       serve_bench(ctx, sdsets, emri.FP64, 10.0, args.serve_seconds, wl.n_max, queue_capacity=16)]
+        if args.serve_sweep:
+            serving = (serving or []) + \
+                [serve_bench(ctx, sdsets, emri.MIXED, r, 4.0, wl.n_max, queue_capacity=64)
+                 for r in (10, 30, 100, 300, 1000, 2000)] + \
+                [serve_bench(ctx, sdsets, emri.FP64, r, 4.0, wl.n_max, queue_capacity=64) for r in (1, 3, 10, 30)]
+        for v in sdsets.values():
+            for d in v:
+                d.close()
 
     # ---- the paper's own workload and the on-device ensemble step (rank 0)
     paper = stretch = None
     if rank == 0 and not args.no_extra:
         stretch = stretch_bench(ctx, ds, theta, wl, 3, 1, flush)
         paper = paper_bench(ctx, 5, 2)
+
+    # ---- one ensemble spread over all ranks (N > 1 only)
+    sharded = None
+    if world > 1 and not args.no_extra:
+        sharded = sharded_bench(ctx, args, rank, world, 3, 1, flush, barrier)
 
     # ---- uneven batching: many chains in one captured launch (rank 0)
     multi = None
@@ -652,6 +731,7 @@ def main():
             "serving": serving,
             "multi_chain": multi,
             "ensemble_step": stretch,
+            "sharded_ensemble_step": sharded,
             "paper_workload": paper,
             "gpu_launches": int(launches),
             "kernels_ms_per_step": {k: round(v, 3) for k, v in per_step.items()},

@@ -347,14 +347,40 @@ int emri_stretch_step(emri_ctx* ctx, const emri_dataset* ds, double* theta_dev, 
                       const emri_opts* opts, const emri_stretch_cfg* cfg, const double* u_dev,
                       int32_t* accepted_dev, void* stream);
 
+/* One block of one half-step of emri_stretch_step, for an ensemble whose
+ * walkers are spread over several GPUs (paper Sec. 3, "Posterior sampling":
+ * the walkers of the parallel stretch move are independent within a half,
+ * so each GPU can move its own block of each half).  Updates walkers
+ * k0 <= k < k1 of half `half` (0: [0, W/2), 1: [W/2, W); the block must lie
+ * inside it) against the whole other half, exactly as emri_stretch_step does
+ * for them: theta_dev[EMRI_NPARAM][W] and lnp_dev[W] hold the whole ensemble
+ * (the other half must be current on this device), and only the block's
+ * columns, lnp and accepted entries are written; u_dev[3][W] as for
+ * emri_stretch_step.  Running half 0 over blocks that cover it, making the
+ * updated half 0 current everywhere, then half 1 likewise, gives the same
+ * ensemble bit for bit as one emri_stretch_step.  Errors as
+ * emri_stretch_step, plus EMRI_EINVAL for a block outside the half; an empty
+ * block is a no-op. */
+int emri_stretch_half(emri_ctx* ctx, const emri_dataset* ds, double* theta_dev, double* lnp_dev, int w, int half,
+                      int k0, int k1, const emri_opts* opts, const emri_stretch_cfg* cfg, const double* u_dev,
+                      int32_t* accepted_dev, void* stream);
+
 /* ------------------------------------------------------------- serving
- * A continuous-batching request loop on the context's device: requests
- * arriving while others run are admitted as HBM budget and slots free up,
- * and run concurrently on the device. */
+ * A continuous-batching request loop on the context's device (the serving
+ * configuration of paper Sec. 3's likelihood evaluations for many chains):
+ * requests arriving while others run are admitted as slots and HBM free up,
+ * and run concurrently on the device.  emri_serve_start allocates one device
+ * pool of the serving budget and charges it to the context until stop; each
+ * admitted request holds a contiguous range of it (its parameters, results
+ * and workspace) while it runs, so an admitted request never fails for
+ * memory and the loop never allocates device memory.  Requests are admitted
+ * in arrival order, except that later requests that fit may pass one that
+ * does not fit yet, at most 32 times, after which admission waits for it. */
 typedef struct {
   int slots;            /* concurrent requests on the device (streams), >= 1  */
   int queue_capacity;   /* pending requests before submit returns EAGAIN      */
-  size_t budget_bytes;  /* workspace budget for admitted requests (0 = ctx's)  */
+  size_t budget_bytes;  /* pool bytes, at most the context's remaining budget;
+                           0 = half of the context's remaining budget         */
 } emri_serve_cfg;
 
 typedef struct {
@@ -373,6 +399,11 @@ int emri_serve_stop(emri_ctx* ctx);
  * queue is full; EMRI_EBUDGET when the request alone exceeds the budget. */
 int emri_serve_submit(emri_ctx* ctx, const emri_dataset* ds, const double* theta_host, int w,
                       const emri_opts* opts, uint64_t* ticket);
+
+/* Pool bytes a request of W walkers against `ds` with `opts` holds while it
+ * runs (host query; a request larger than the pool is refused at submit). */
+int emri_serve_request_bytes(emri_ctx* ctx, const emri_dataset* ds, int w, const emri_opts* opts,
+                             size_t* bytes);
 
 /* Wait up to timeout_us (<0: forever) for a request; on completion copy its
  * W log-likelihoods to lnl_host, statuses to status_host (nullable) and the

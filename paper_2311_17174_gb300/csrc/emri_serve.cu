@@ -1,15 +1,23 @@
 // emri_serve.cu -- continuous-batching request loop, multi-chain launches
 // and the autotuner of libemri.
 //
-// Serving: a scheduler thread owns S stream slots.  Requests (a dataset and
-// W walkers) wait in a FIFO; whenever a slot is free and the HBM budget has
-// room for the request's workspace, the request is admitted: its parameters
-// go host->device from a pinned staging buffer, the likelihood path is
-// enqueued on the slot's stream, and the results come back device->host into
-// pinned memory, all asynchronously.  Requests in different slots overlap on
-// the device; completion is detected by polling an event per slot.  The
-// kernels reduce in a fixed order per walker, so a request's results are
-// bitwise the same alone or in a mix.
+// Serving: a scheduler thread owns S stream slots and one device pool, the
+// serving budget allocated once at start.  Requests (a dataset and W
+// walkers) wait in arrival order; a request is admitted when a slot is free
+// and a contiguous range of the pool holds everything it needs on the device
+// (parameters, results, and the likelihood path's workspace), so admission
+// and allocation are one decision and no request admitted can run out of
+// memory.  A request that does not fit yet keeps its place while later ones
+// that fit pass it, at most kMaxBypass times; then admission waits for it
+// (the ranges of running requests return to the pool as they complete, so it
+// is admitted at the latest when the device drains).  On admission its
+// parameters go host->device from the slot's pinned staging buffer, the
+// likelihood path is enqueued on the slot's stream and the results come back
+// device->host into pinned memory, all asynchronously.  Requests in different
+// slots overlap on the device; completion is detected by polling an event per
+// slot.  The scheduler never allocates or frees device memory.  The kernels
+// reduce in a fixed order per walker, so a request's results are bitwise the
+// same alone or in a mix.
 #include <time.h>
 
 #include <algorithm>
@@ -18,6 +26,7 @@
 #include <condition_variable>
 #include <deque>
 #include <fstream>
+#include <map>
 #include <memory>
 #include <sstream>
 #include <string>
@@ -39,13 +48,20 @@ static int64_t now_ns() {
   return (int64_t)ts.tv_sec * 1000000000LL + ts.tv_nsec;
 }
 
+// Admission may pass a request that does not fit yet at most this many times.
+constexpr int kMaxBypass = 32;
+// Pinned staging per slot at start (walkers); grows when a request is larger.
+constexpr int kStageWalkers = 1024;
+
 struct Request {
   uint64_t ticket = 0;
   const emri_dataset* ds = nullptr;
   std::vector<double> theta;   // [16][w]
   int w = 0;
   OptsN o{};
-  size_t need = 0;             // workspace bytes
+  size_t need = 0;             // pool bytes: parameters and results, then the workspace
+  size_t off = 0;              // its range of the pool while it runs
+  int bypassed = 0;            // later requests admitted while this one waited
   int wave = 0;
   std::vector<double> lnl;
   std::vector<uint32_t> st;
@@ -56,22 +72,20 @@ struct Request {
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  Workspace ws;
   double* h_theta = nullptr;   // pinned staging
   double* h_lnl = nullptr;
   uint32_t* h_st = nullptr;
   size_t h_cap = 0;            // walkers
-  double* d_io = nullptr;      // device theta + lnl + status
-  size_t d_cap = 0;
+  std::vector<void*> retired;  // outgrown staging, freed at stop
   std::shared_ptr<Request> req;
-  size_t reserved = 0;         // budget charged while busy
 };
 
 struct Server {
   emri_ctx* ctx = nullptr;
   emri_serve_cfg cfg{};
-  size_t budget = 0;
-  size_t in_use = 0;
+  size_t budget = 0;           // pool bytes
+  char* pool = nullptr;
+  std::map<size_t, size_t> free_ranges;   // offset -> bytes, coalesced
   std::mutex mu;
   std::condition_variable cv_sched, cv_done;
   std::deque<std::shared_ptr<Request>> queue;
@@ -83,41 +97,78 @@ struct Server {
   int64_t launches = 0;
 };
 
-static int slot_buffers(Slot& sl, int w) {
-  if ((size_t)w > sl.h_cap) {
-    if (sl.h_theta) cudaFreeHost(sl.h_theta);
-    if (sl.h_lnl) cudaFreeHost(sl.h_lnl);
-    if (sl.h_st) cudaFreeHost(sl.h_st);
-    sl.h_theta = nullptr;
-    sl.h_lnl = nullptr;
-    sl.h_st = nullptr;
-    if (cudaMallocHost(&sl.h_theta, sizeof(double) * kNParam * w) != cudaSuccess ||
-        cudaMallocHost(&sl.h_lnl, sizeof(double) * w) != cudaSuccess ||
-        cudaMallocHost(&sl.h_st, sizeof(uint32_t) * w) != cudaSuccess) {
-      sl.h_cap = 0;
-      return EMRI_ENOMEM;
-    }
-    sl.h_cap = w;
+// ------------------------------------------------------------ the pool
+// First fit over the free ranges (every size is a multiple of 256 bytes).
+static bool pool_take(Server* sv, size_t bytes, size_t* off) {
+  for (auto it = sv->free_ranges.begin(); it != sv->free_ranges.end(); ++it) {
+    if (it->second < bytes) continue;
+    *off = it->first;
+    const size_t rest = it->second - bytes, next = it->first + bytes;
+    sv->free_ranges.erase(it);
+    if (rest) sv->free_ranges[next] = rest;
+    return true;
   }
-  if ((size_t)w > sl.d_cap) {
-    if (sl.d_io) cudaFree(sl.d_io);
-    sl.d_io = nullptr;
-    if (cudaMalloc(&sl.d_io, sizeof(double) * (kNParam + 2) * w) != cudaSuccess) {
-      sl.d_cap = 0;
-      return EMRI_ENOMEM;
-    }
-    sl.d_cap = w;
+  return false;
+}
+
+// Return a range, merged with its free neighbours.
+static void pool_give(Server* sv, size_t off, size_t bytes) {
+  auto it = sv->free_ranges.emplace(off, bytes).first;
+  auto nx = std::next(it);
+  if (nx != sv->free_ranges.end() && it->first + it->second == nx->first) {
+    it->second += nx->second;
+    sv->free_ranges.erase(nx);
   }
+  if (it != sv->free_ranges.begin()) {
+    auto pv = std::prev(it);
+    if (pv->first + pv->second == it->first) {
+      pv->second += it->second;
+      sv->free_ranges.erase(it);
+    }
+  }
+}
+
+static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Pool bytes of a request: parameters, lnL and status, then the workspace of
+// the likelihood path.
+static size_t request_bytes(const emri_dataset* ds, const OptsN& o, int w, int wave) {
+  return round256(sizeof(double) * (kNParam + 2) * (size_t)w) +
+         round256(loglike_layout(ds->plan, o, w, wave, nullptr, nullptr));
+}
+
+// Pinned staging for w walkers (host memory only; outgrown buffers are kept
+// until stop, so nothing here waits for the device).
+static int slot_staging(Slot& sl, int w) {
+  if ((size_t)w <= sl.h_cap) return EMRI_OK;
+  const size_t cap = std::max<size_t>((size_t)w, 2 * sl.h_cap);
+  double *t = nullptr, *l = nullptr;
+  uint32_t* st = nullptr;
+  if (cudaHostAlloc(&t, sizeof(double) * kNParam * cap, cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc(&l, sizeof(double) * cap, cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc(&st, sizeof(uint32_t) * cap, cudaHostAllocDefault) != cudaSuccess) {
+    if (t) sl.retired.push_back(t);
+    if (l) sl.retired.push_back(l);
+    return set_err(EMRI_ENOMEM, "serve: pinned staging for %d walkers", w);
+  }
+  for (void* p : {(void*)sl.h_theta, (void*)sl.h_lnl, (void*)sl.h_st})
+    if (p) sl.retired.push_back(p);
+  sl.h_theta = t;
+  sl.h_lnl = l;
+  sl.h_st = st;
+  sl.h_cap = cap;
   return EMRI_OK;
 }
 
-// Enqueue a request on a slot (scheduler thread, lock held by caller).
+// Enqueue an admitted request (its pool range at r->off) on a slot
+// (scheduler thread, lock held by the caller).
 static void launch_request(Server* sv, Slot& sl, const std::shared_ptr<Request>& r) {
   emri_ctx* ctx = sv->ctx;
   r->stats.start_ns = now_ns();
-  int rc = slot_buffers(sl, r->w);
-  if (rc == EMRI_OK) rc = sl.ws.reserve(ctx, r->need, sl.stream);
+  r->stats.slot = (int32_t)(&sl - sv->slots.data());
+  int rc = slot_staging(sl, r->w);
   if (rc != EMRI_OK) {
+    pool_give(sv, r->off, r->need);
     r->stats.status = rc;
     r->stats.done_ns = now_ns();
     r->done = true;
@@ -125,11 +176,12 @@ static void launch_request(Server* sv, Slot& sl, const std::shared_ptr<Request>&
     return;
   }
   memcpy(sl.h_theta, r->theta.data(), sizeof(double) * kNParam * r->w);
-  double* d_theta = sl.d_io;
-  double* d_lnl = sl.d_io + (size_t)kNParam * r->w;
+  char* base = sv->pool + r->off;
+  double* d_theta = (double*)base;
+  double* d_lnl = d_theta + (size_t)kNParam * r->w;
   uint32_t* d_st = (uint32_t*)(d_lnl + r->w);
   cudaMemcpyAsync(d_theta, sl.h_theta, sizeof(double) * kNParam * r->w, cudaMemcpyHostToDevice, sl.stream);
-  Carve cv(sl.ws.ptr);
+  Carve cv(base + round256(sizeof(double) * (kNParam + 2) * (size_t)r->w));
   LoglikeBufs b;
   loglike_layout(r->ds->plan, r->o, r->w, r->wave, &cv, &b);
   int64_t nl = 0;
@@ -139,10 +191,7 @@ static void launch_request(Server* sv, Slot& sl, const std::shared_ptr<Request>&
   cudaEventRecord(sl.done, sl.stream);
   ctx->launches += nl;
   r->stats.status = rc;
-  r->stats.slot = (int32_t)(&sl - sv->slots.data());
   sl.req = r;
-  sl.reserved = r->need;
-  sv->in_use += r->need;
 }
 
 static void scheduler(Server* sv) {
@@ -164,26 +213,38 @@ static void scheduler(Server* sv) {
       }
       r->stats.done_ns = now_ns();
       r->done = true;
-      sv->in_use -= sl.reserved;
-      sl.reserved = 0;
+      pool_give(sv, r->off, r->need);
       sl.req.reset();
       progressed = true;
       sv->cv_done.notify_all();
     }
-    // admissions, FIFO: the head waits for a slot and for budget room
-    while (!sv->queue.empty()) {
-      auto r = sv->queue.front();
-      Slot* free_slot = nullptr;
-      for (Slot& sl : sv->slots)
-        if (!sl.req) {
-          free_slot = &sl;
-          break;
+    // admissions in arrival order: a request that does not fit the pool yet
+    // keeps its place, later ones that fit may pass the first such request
+    // up to kMaxBypass times, then admission waits for it
+    {
+      Request* waiting = nullptr;
+      for (auto it = sv->queue.begin(); it != sv->queue.end();) {
+        Slot* free_slot = nullptr;
+        for (Slot& sl : sv->slots)
+          if (!sl.req) {
+            free_slot = &sl;
+            break;
+          }
+        if (!free_slot) break;
+        if (waiting && waiting->bypassed >= kMaxBypass) break;
+        auto r = *it;
+        size_t off = 0;
+        if (!pool_take(sv, r->need, &off)) {
+          if (!waiting) waiting = r.get();
+          ++it;
+          continue;
         }
-      if (!free_slot) break;
-      if (sv->in_use + r->need > sv->budget) break;
-      sv->queue.pop_front();
-      launch_request(sv, *free_slot, r);
-      progressed = true;
+        r->off = off;
+        it = sv->queue.erase(it);
+        if (waiting) ++waiting->bypassed;
+        launch_request(sv, *free_slot, r);
+        progressed = true;
+      }
     }
     if (sv->stop) {
       bool busy = false;
@@ -225,13 +286,17 @@ void serve_shutdown(emri_ctx* ctx) {
   cudaSetDevice(ctx->device);
   for (Slot& sl : sv->slots) {
     cudaStreamSynchronize(sl.stream);
-    sl.ws.destroy(ctx);
     if (sl.h_theta) cudaFreeHost(sl.h_theta);
     if (sl.h_lnl) cudaFreeHost(sl.h_lnl);
     if (sl.h_st) cudaFreeHost(sl.h_st);
-    if (sl.d_io) cudaFree(sl.d_io);
+    for (void* p : sl.retired) cudaFreeHost(p);
     cudaEventDestroy(sl.done);
     cudaStreamDestroy(sl.stream);
+  }
+  if (sv->pool) {
+    cudaFree(sv->pool);
+    std::lock_guard<std::mutex> blk(ctx->budget_mu);
+    ctx->used -= sv->budget;
   }
   {
     // pollers still waiting wake up to completed or failed requests; the
@@ -286,22 +351,41 @@ extern "C" int emri_serve_start(emri_ctx* ctx, const emri_serve_cfg* cfg) {
   Server* sv = sp.get();
   sv->ctx = ctx;
   sv->cfg = c;
-  size_t room;
+  // the pool: the requested budget (at most what the context has left), or
+  // half the context's remaining budget (the other half stays for direct
+  // calls on the same context); charged to the context while serving runs
+  size_t want;
   {
     std::lock_guard<std::mutex> blk(ctx->budget_mu);
-    room = ctx->budget > ctx->used ? ctx->budget - ctx->used : 0;
+    const size_t room = ctx->budget > ctx->used ? ctx->budget - ctx->used : 0;
+    want = (c.budget_bytes ? std::min(c.budget_bytes, room) : room / 2) & ~(size_t)255;
+    if (want < 256) return set_err(EMRI_EBUDGET, "no room left in the context's budget for serving");
+    ctx->used += want;
   }
-  sv->budget = c.budget_bytes ? std::min(c.budget_bytes, room) : room;
+  sv->budget = want;
+  auto fail = [&](int code, const char* what) {
+    for (Slot& q : sv->slots) {
+      if (q.done) cudaEventDestroy(q.done);
+      if (q.stream) cudaStreamDestroy(q.stream);
+      for (void* hp : {(void*)q.h_theta, (void*)q.h_lnl, (void*)q.h_st})
+        if (hp) cudaFreeHost(hp);
+    }
+    if (sv->pool) cudaFree(sv->pool);
+    std::lock_guard<std::mutex> blk(ctx->budget_mu);
+    ctx->used -= want;
+    return set_err(code, "serve: %s", what);
+  };
+  if (cudaMalloc(&sv->pool, want) != cudaSuccess) {
+    sv->pool = nullptr;
+    return fail(EMRI_ENOMEM, "pool allocation failed");
+  }
+  sv->free_ranges[0] = want;
   sv->slots.resize(c.slots);
   for (Slot& sl : sv->slots) {
     if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
-      for (Slot& q : sv->slots) {
-        if (q.done) cudaEventDestroy(q.done);
-        if (q.stream) cudaStreamDestroy(q.stream);
-      }
-      return set_err(EMRI_ECUDA, "serve: stream/event creation failed");
-    }
+        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess)
+      return fail(EMRI_ECUDA, "stream/event creation failed");
+    if (slot_staging(sl, kStageWalkers) != EMRI_OK) return fail(EMRI_ENOMEM, "pinned staging");
   }
   ctx->server = sp;
   sv->th = std::thread(scheduler, sv);
@@ -339,7 +423,7 @@ extern "C" int emri_serve_submit(emri_ctx* ctx, const emri_dataset* ds, const do
     std::lock_guard<std::mutex> clk(ctx->mu);   // the tuned plans
     r->wave = pick_wave(ctx, ds->plan, r->o, w);
   }
-  r->need = loglike_layout(ds->plan, r->o, w, r->wave, nullptr, nullptr);
+  r->need = request_bytes(ds, r->o, w, r->wave);
   r->lnl.assign(w, 0.0);
   r->st.assign(w, 0u);
   std::lock_guard<std::mutex> lk(sv->mu);
@@ -354,6 +438,19 @@ extern "C" int emri_serve_submit(emri_ctx* ctx, const emri_dataset* ds, const do
   sv->reqs[r->ticket] = r;
   *ticket = r->ticket;
   sv->cv_sched.notify_all();
+  return EMRI_OK;
+}
+
+extern "C" int emri_serve_request_bytes(emri_ctx* ctx, const emri_dataset* ds, int w, const emri_opts* opts,
+                                        size_t* bytes) {
+  if (!ctx || !ds || !bytes) return set_err(EMRI_EINVAL, "NULL argument");
+  if (ds->ctx != ctx) return set_err(EMRI_EINVAL, "dataset belongs to another context");
+  if (w < 1) return set_err(EMRI_EINVAL, "w must be >= 1");
+  OptsN o;
+  int rc = normalize_opts(opts, ds->n, &o);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> clk(ctx->mu);   // the tuned plans
+  *bytes = request_bytes(ds, o, w, pick_wave(ctx, ds->plan, o, w));
   return EMRI_OK;
 }
 

@@ -100,8 +100,13 @@ _SIGS = {
                                     C.POINTER(C.c_uint64)]),
     "emri_serve_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.POINTER(ReqStats),
                                   C.c_int64]),
+    "emri_serve_request_bytes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(Opts),
+                                           C.POINTER(C.c_size_t)]),
     "emri_stretch_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(Opts),
                                     C.POINTER(StretchCfg), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "emri_stretch_half": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                    C.c_int, C.POINTER(Opts), C.POINTER(StretchCfg), C.c_void_p, C.c_void_p,
+                                    C.c_void_p]),
     "emri_autotune": (C.c_int, [C.c_void_p, C.POINTER(Grid), C.c_int, C.c_int, C.c_char_p,
                                 C.POINTER(C.c_int64)]),
 }
@@ -286,6 +291,14 @@ class Context:
         _check(self.lib.emri_stretch_step(self.h, ds.h, _ptr(theta), _ptr(lnp), w, C.byref(o), C.byref(cfg),
                                           _ptr(u), _ptr(accepted), _stream(stream)))
 
+    def stretch_half(self, ds: "Dataset", theta, lnp, o: Opts, cfg: StretchCfg, u, half: int, k0: int, k1: int,
+                     accepted=None, stream=None):
+        """emri_stretch_half: walkers k0..k1-1 of half ``half`` of the ensemble
+        theta [16][W] / lnp [W] (device tensors holding the whole ensemble)."""
+        w = int(theta.shape[1])
+        _check(self.lib.emri_stretch_half(self.h, ds.h, _ptr(theta), _ptr(lnp), w, int(half), int(k0), int(k1),
+                                          C.byref(o), C.byref(cfg), _ptr(u), _ptr(accepted), _stream(stream)))
+
     # ------------------------------------------------------------ serving
     def serve_start(self, slots: int = 4, queue_capacity: int = 1024, budget_bytes: int = 0):
         cfg = ServeCfg(int(slots), int(queue_capacity), int(budget_bytes))
@@ -300,6 +313,12 @@ class Context:
         t = C.c_uint64()
         _check(self.lib.emri_serve_submit(self.h, ds.h, th.ctypes.data, int(th.shape[1]), C.byref(o), C.byref(t)))
         return t.value
+
+    def serve_request_bytes(self, ds: "Dataset", w: int, o: Opts) -> int:
+        """Pool bytes a request of ``w`` walkers holds while it runs."""
+        b = C.c_size_t()
+        _check(self.lib.emri_serve_request_bytes(self.h, ds.h, int(w), C.byref(o), C.byref(b)))
+        return b.value
 
     def serve_poll(self, ticket: int, w: int, timeout_us: int = -1):
         """Returns (rc, lnl[w], status[w], stats); rc is OK or ETIMEDOUT."""

@@ -156,3 +156,43 @@ def test_stop_while_pollers_wait_and_direct_calls_in_parallel(env):
     with pytest.raises(emri.EmriError) as ei:
         ctx.serve_poll(tickets[0], 1, timeout_us=0)
     assert ei.value.code == emri.ENOTFOUND
+
+
+def test_pool_admission_backfill(env):
+    """A serving pool that holds one large request and two small ones at a
+    time, with large (FP64, 512 walkers) and small (mixed, 8 walkers)
+    requests submitted alternately: every admitted request completes without
+    a memory error, the large ones run one after another, a small request
+    submitted behind a waiting large one is served before it, and every
+    result equals the same request run alone."""
+    emri, ctx, dsets = env
+    o_l, o_s = emri.opts(precision=emri.FP64, n_max=8), emri.opts(precision=emri.MIXED, n_max=8)
+    ds_l, ds_s = dsets[16], dsets[14]
+    th_l = [I.scatter_walkers(40 + k, I.draw_sources(50 + k, 1, 1 << 16)[0], 512) for k in range(3)]
+    th_s = [I.scatter_walkers(60 + k, I.draw_sources(70 + k, 1, 1 << 14)[0], 8) for k in range(6)]
+    need_l = ctx.serve_request_bytes(ds_l, 512, o_l)
+    need_s = ctx.serve_request_bytes(ds_s, 8, o_s)
+    assert need_l > 4 * need_s
+    order = [("L", 0), ("L", 1), ("S", 0), ("S", 1), ("L", 2), ("S", 2), ("S", 3), ("S", 4), ("S", 5)]
+    alone = {(k, i): direct(emri, ctx, ds_l if k == "L" else ds_s, (th_l if k == "L" else th_s)[i],
+                            emri.FP64 if k == "L" else emri.MIXED) for k, i in order}
+    ctx.serve_start(slots=4, queue_capacity=64, budget_bytes=need_l + 2 * need_s + 4096)
+    try:
+        tickets = []
+        for k, i in order:
+            th = (th_l if k == "L" else th_s)[i]
+            tickets.append(ctx.serve_submit(ds_l if k == "L" else ds_s, th.T.copy(), o_l if k == "L" else o_s))
+        stats = {}
+        for (k, i), t in zip(order, tickets):
+            w = 512 if k == "L" else 8
+            rc, lnl, st, s = ctx.serve_poll(t, w, timeout_us=-1)
+            assert rc == emri.OK and s.status == emri.OK
+            np.testing.assert_array_equal(lnl, alone[(k, i)])
+            stats[(k, i)] = (s.arrival_ns, s.start_ns, s.done_ns)
+    finally:
+        ctx.serve_stop()
+    # the pool holds one large request: each starts after the previous one is done
+    assert stats[("L", 1)][1] >= stats[("L", 0)][2]
+    assert stats[("L", 2)][1] >= stats[("L", 1)][2]
+    # small requests submitted after the second large one passed it while it waited
+    assert min(stats[("S", i)][1] for i in range(2)) < stats[("L", 1)][1]

@@ -44,6 +44,46 @@ def in_box(y, free, lo, hi) -> bool:
     return all(lo[p] <= y[p] <= hi[p] for p in free)
 
 
+def halves_of(w: int):
+    """The two halves S0 = [0, h), S1 = [h, W), h = floor(W/2)."""
+    h = w // 2
+    return [np.arange(0, h), np.arange(h, w)]
+
+
+def stretch_block(x, lp, acc, margin, u, a: float, free, lo, hi, lnprob, s: int, k0: int, k1: int):
+    """Update the walkers k0 <= k < k1 of half s (in place) against the whole
+    other half, as one part of the half-step of ``stretch_step``: walker k
+    uses only its own uniforms u[:, k] and the other half's positions, so the
+    half-step over its walkers in any partition gives the same result."""
+    w = x.shape[0]
+    halves = halves_of(w)
+    other = halves[1 - s]
+    active = [k for k in halves[s] if k0 <= k < k1]
+    nc = len(other)
+    if not len(active) or not nc:
+        return
+    d = len(free)
+    ys, zs = [], []
+    for k in active:
+        j = other[min(int(np.floor(u[0][k] * nc)), nc - 1)]
+        z = float(stretch_z(u[1][k], a))
+        y = x[k].copy()
+        for p in free:
+            y[p] = x[j][p] + z * (x[k][p] - x[j][p])
+        ys.append(y)
+        zs.append(z)
+    ll, st = lnprob(np.array(ys))
+    for i, k in enumerate(active):
+        y = ys[i]
+        if not in_box(y, free, lo, hi) or (int(st[i]) & INVALID) or not np.isfinite(ll[i]):
+            continue
+        margin[k] = (d - 1) * np.log(zs[i]) + ll[i] - lp[k] - np.log(u[2][k])
+        if margin[k] > 0:
+            x[k] = y
+            lp[k] = ll[i]
+            acc[k] = 1
+
+
 def stretch_step(theta, lnp, u, a: float, free, lo, hi, lnprob):
     """One ensemble step.
 
@@ -58,33 +98,8 @@ def stretch_step(theta, lnp, u, a: float, free, lo, hi, lnprob):
     x = np.array(theta, dtype=np.float64, copy=True)
     lp = np.array(lnp, dtype=np.float64, copy=True)
     w = x.shape[0]
-    h = w // 2
-    halves = [np.arange(0, h), np.arange(h, w)]
-    d = len(free)
     acc = np.zeros(w, dtype=np.int32)
     margin = np.full(w, np.nan)
     for s in (0, 1):
-        active, other = halves[s], halves[1 - s]
-        nc = len(other)
-        if not len(active) or not nc:
-            continue
-        ys, zs = [], []
-        for k in active:
-            j = other[min(int(np.floor(u[0][k] * nc)), nc - 1)]
-            z = float(stretch_z(u[1][k], a))
-            y = x[k].copy()
-            for p in free:
-                y[p] = x[j][p] + z * (x[k][p] - x[j][p])
-            ys.append(y)
-            zs.append(z)
-        ll, st = lnprob(np.array(ys))
-        for i, k in enumerate(active):
-            y = ys[i]
-            if not in_box(y, free, lo, hi) or (int(st[i]) & INVALID) or not np.isfinite(ll[i]):
-                continue
-            margin[k] = (d - 1) * np.log(zs[i]) + ll[i] - lp[k] - np.log(u[2][k])
-            if margin[k] > 0:
-                x[k] = y
-                lp[k] = ll[i]
-                acc[k] = 1
+        stretch_block(x, lp, acc, margin, u, a, free, lo, hi, lnprob, s, 0, w)
     return x, lp, acc, margin

@@ -14,6 +14,8 @@
 // The proposal and the acceptance margin are evaluated with explicitly
 // rounded operations (no fused multiply-add), in the same order as the plain
 // definition, so that a proposal is bit-identical to the textbook formula.
+#include <algorithm>
+
 #include "../../include/emri.h"
 #include "emri_api_internal.h"
 #include "emri_common.cuh"
@@ -90,28 +92,33 @@ __global__ void k_stretch_accept(double* __restrict__ theta, double* __restrict_
 
 }  // namespace
 
-extern "C" int emri_stretch_step(emri_ctx* ctx, const emri_dataset* ds, double* theta, double* lnp, int w,
-                                 const emri_opts* opts, const emri_stretch_cfg* cfg, const double* u,
-                                 int32_t* accepted, void* stream) {
-  if (!ctx || !ds || !cfg) return set_err(EMRI_EINVAL, "NULL context, dataset or configuration");
-  if (ds->ctx != ctx) return set_err(EMRI_EINVAL, "dataset belongs to another context");
-  if (w < 0) return set_err(EMRI_EINVAL, "w must be >= 0");
-  if (w == 0) return EMRI_OK;
-  if (w < 2) return set_err(EMRI_EINVAL, "the stretch move needs at least 2 walkers");
-  if (!theta || !lnp || !u) return set_err(EMRI_EINVAL, "NULL pointer");
+namespace {
+
+// Validated stretch-move arguments of a configuration.
+int stretch_args(const emri_stretch_cfg* cfg, StretchArgs* sa) {
   if (!(cfg->a > 1.0) || !isfinite(cfg->a)) return set_err(EMRI_EINVAL, "stretch scale a must be finite and > 1");
-  StretchArgs sa{};
-  sa.a = cfg->a;
-  sa.free_mask = cfg->free_mask & ((1u << kNParam) - 1u);
-  if (sa.free_mask != cfg->free_mask) return set_err(EMRI_EINVAL, "free_mask has bits above parameter %d", kNParam - 1);
-  if (!sa.free_mask) return set_err(EMRI_EINVAL, "free_mask selects no parameter");
-  sa.d = __builtin_popcount(sa.free_mask);
+  *sa = StretchArgs{};
+  sa->a = cfg->a;
+  sa->free_mask = cfg->free_mask & ((1u << kNParam) - 1u);
+  if (sa->free_mask != cfg->free_mask)
+    return set_err(EMRI_EINVAL, "free_mask has bits above parameter %d", kNParam - 1);
+  if (!sa->free_mask) return set_err(EMRI_EINVAL, "free_mask selects no parameter");
+  sa->d = __builtin_popcount(sa->free_mask);
   for (int p = 0; p < kNParam; ++p) {
-    sa.lo[p] = cfg->lo[p];
-    sa.hi[p] = cfg->hi[p];
-    if (((sa.free_mask >> p) & 1u) && !(cfg->lo[p] <= cfg->hi[p]))
+    sa->lo[p] = cfg->lo[p];
+    sa->hi[p] = cfg->hi[p];
+    if (((sa->free_mask >> p) & 1u) && !(cfg->lo[p] <= cfg->hi[p]))
       return set_err(EMRI_EINVAL, "prior box of parameter %d is empty or NaN", p);
   }
+  return EMRI_OK;
+}
+
+// The walkers k0 <= k < k1 of halves first..last, each half against the
+// whole other half of theta, the halves in order (half 0 = [0, W/2),
+// half 1 = [W/2, W)).
+int stretch_run(emri_ctx* ctx, const emri_dataset* ds, double* theta, double* lnp, int w, const emri_opts* opts,
+                const StretchArgs& sa, const double* u, int32_t* accepted, cudaStream_t s, int first, int last,
+                int k0, int k1) {
   OptsN o;
   int rc = normalize_opts(opts, ds->n, &o);
   if (rc) return rc;
@@ -121,9 +128,19 @@ extern "C" int emri_stretch_step(emri_ctx* ctx, const emri_dataset* ds, double* 
     if (pk) o.ks = pk;
   }
   if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(EMRI_ECUDA, "cudaSetDevice");
-  cudaStream_t s = (cudaStream_t)stream;
   const int h = w / 2;
-  const int mmax = w - h;   // the larger half
+  auto block = [&](int half, int* a0, int* m) {
+    const int lo = half == 0 ? 0 : h, hi = half == 0 ? h : w;
+    *a0 = std::max(lo, k0);
+    *m = std::max(0, std::min(hi, k1) - *a0);
+  };
+  int mmax = 0;
+  for (int half = first; half <= last; ++half) {
+    int a0, m;
+    block(half, &a0, &m);
+    mmax = std::max(mmax, m);
+  }
+  if (mmax == 0) return EMRI_OK;
   const int wave = pick_wave(ctx, ds->plan, o, mmax);
   // workspace: proposals Y[P][m], z[m], lnL(Y)[m], status(Y)[m], then the likelihood buffers
   Carve probe(nullptr);
@@ -143,8 +160,9 @@ extern "C" int emri_stretch_step(emri_ctx* ctx, const emri_dataset* ds, double* 
   LoglikeBufs b;
   loglike_layout(ds->plan, o, mmax, wave, &cv, &b);
   int64_t nl = 0;
-  for (int half = 0; half < 2 && rc == EMRI_OK; ++half) {
-    const int a0 = half == 0 ? 0 : h, m = half == 0 ? h : w - h;
+  for (int half = first; half <= last && rc == EMRI_OK; ++half) {
+    int a0, m;
+    block(half, &a0, &m);
     const int o0 = half == 0 ? h : 0, nc = half == 0 ? w - h : h;
     if (m == 0 || nc == 0) continue;
     const int tb = 128, gb = (m + tb - 1) / tb;
@@ -159,4 +177,39 @@ extern "C" int emri_stretch_step(emri_ctx* ctx, const emri_dataset* ds, double* 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(e, "stretch step launch");
   return EMRI_OK;
+}
+
+}  // namespace
+
+extern "C" int emri_stretch_step(emri_ctx* ctx, const emri_dataset* ds, double* theta, double* lnp, int w,
+                                 const emri_opts* opts, const emri_stretch_cfg* cfg, const double* u,
+                                 int32_t* accepted, void* stream) {
+  if (!ctx || !ds || !cfg) return set_err(EMRI_EINVAL, "NULL context, dataset or configuration");
+  if (ds->ctx != ctx) return set_err(EMRI_EINVAL, "dataset belongs to another context");
+  if (w < 0) return set_err(EMRI_EINVAL, "w must be >= 0");
+  if (w == 0) return EMRI_OK;
+  if (w < 2) return set_err(EMRI_EINVAL, "the stretch move needs at least 2 walkers");
+  if (!theta || !lnp || !u) return set_err(EMRI_EINVAL, "NULL pointer");
+  StretchArgs sa;
+  int rc = stretch_args(cfg, &sa);
+  if (rc) return rc;
+  return stretch_run(ctx, ds, theta, lnp, w, opts, sa, u, accepted, (cudaStream_t)stream, 0, 1, 0, w);
+}
+
+extern "C" int emri_stretch_half(emri_ctx* ctx, const emri_dataset* ds, double* theta, double* lnp, int w, int half,
+                                 int k0, int k1, const emri_opts* opts, const emri_stretch_cfg* cfg, const double* u,
+                                 int32_t* accepted, void* stream) {
+  if (!ctx || !ds || !cfg) return set_err(EMRI_EINVAL, "NULL context, dataset or configuration");
+  if (ds->ctx != ctx) return set_err(EMRI_EINVAL, "dataset belongs to another context");
+  if (w < 2) return set_err(EMRI_EINVAL, "the stretch move needs at least 2 walkers");
+  if (half != 0 && half != 1) return set_err(EMRI_EINVAL, "half must be 0 or 1");
+  const int lo = half == 0 ? 0 : w / 2, hi = half == 0 ? w / 2 : w;
+  if (k0 < lo || k1 > hi || k0 > k1)
+    return set_err(EMRI_EINVAL, "walker block [%d, %d) is not inside half %d = [%d, %d)", k0, k1, half, lo, hi);
+  if (k0 == k1) return EMRI_OK;
+  if (!theta || !lnp || !u) return set_err(EMRI_EINVAL, "NULL pointer");
+  StretchArgs sa;
+  int rc = stretch_args(cfg, &sa);
+  if (rc) return rc;
+  return stretch_run(ctx, ds, theta, lnp, w, opts, sa, u, accepted, (cudaStream_t)stream, half, half, k0, k1);
 }

@@ -118,35 +118,41 @@ int upload_bessel_tables(const BesselTab& t) {
   return ok ? 0 : -1;
 }
 
-// exp(2 pi i k / 512), k = -256..256, for the FP64 sin/cos of reduced
-// phases; filled from the host (long double) at context creation.
-constexpr int kExpHalf = 256;
-constexpr int kExpLen = 2 * kExpHalf + 1;
+// exp(2 pi i k / 512), k = 0..511, for the FP64 sin/cos of phases in
+// cycles; filled from the host (long double) at context creation.
+constexpr int kExpLen = 512;
 __device__ double2 g_exp512[kExpLen];
 
 int upload_exp512() {
   double2 h[kExpLen];
   const long double pi = 3.141592653589793238462643383279502884L;
-  for (int k = -kExpHalf; k <= kExpHalf; ++k) {
-    const long double a = 2.0L * pi * (long double)k / (2.0L * kExpHalf);
-    h[k + kExpHalf] = make_double2((double)cosl(a), (double)sinl(a));
+  for (int k = 0; k < kExpLen; ++k) {
+    const long double a = 2.0L * pi * (long double)k / (long double)kExpLen;
+    h[k] = make_double2((double)cosl(a), (double)sinl(a));
   }
   return cudaMemcpyToSymbol(g_exp512, h, sizeof(h)) == cudaSuccess ? 0 : -1;
 }
 
-// cos(2 pi f), sin(2 pi f) for a phase |f| <= 1/2 cycle: f = k/512 + d with
-// |d| <= 1/1024, exp(2 pi i k/512) from the table and the Taylor polynomials
+// cos(2 pi f), sin(2 pi f) for a phase f in cycles (|f| < 2^20; whole cycles
+// need not be removed first): f = k/512 + d with |d| <= 1/1024,
+// exp(2 pi i k/512) from the table at k mod 512 and the Taylor polynomials
 // of sin to x^5 and cos to x^4 at x = 2 pi d (|x| <= 0.00614: the first
-// omitted terms, x^7/7! and x^6/6!, are below 7e-20 and 8e-17).  About 14
-// FP64 operations.
+// omitted terms, x^7/7! and x^6/6!, are below 7e-20 and 8e-17).  The
+// nearest integer k of 512 f comes from adding 1.5 * 2^52: the sum rounds to
+// an integer, its low word is k (two's complement) and subtracting the
+// constant back gives k exactly, so no separate rounding or conversion
+// instruction runs; d = f - k/512 is exact.  About 13 FP64 operations.
 __device__ __forceinline__ void sincos2pi_tab(double f, const double2* __restrict__ tab, double& s, double& c) {
-  const double kd = rint(f * 512.0);
+  constexpr double kRound = 6755399441055744.0;   // 1.5 * 2^52
+  const double kb = fma(f, 512.0, kRound);
+  const double kd = kb - kRound;
+  const int k = __double2loint(kb);
   const double d = fma(kd, -0.001953125, f);   // exact
   const double x = d * 6.283185307179586;
   const double x2 = x * x;
   const double sx = fma(x2 * x, fma(x2, 1.0 / 120.0, -1.0 / 6.0), x);
   const double cx = fma(x2, fma(x2, 1.0 / 24.0, -0.5), 1.0);
-  const double2 t = tab[(int)kd + kExpHalf];
+  const double2 t = tab[k & (kExpLen - 1)];
   s = fma(t.y, cx, t.x * sx);
   c = fma(t.x, cx, -t.y * sx);
 }
@@ -166,7 +172,7 @@ __device__ __forceinline__ T poly3(const T c[4], T s) {
   return ((c[3] * s + c[2]) * s + c[1]) * s + c[0];
 }
 
-struct IvD {           // FP64 interval data
+struct IvD {           // FP64 interval data (gm: of 2 gamma~)
   double ph[4], gm[4], al[4], am[4], ec[4];
 };
 
@@ -183,6 +189,7 @@ __device__ __forceinline__ void interval_phase(double ahi, double alo, double ar
 __device__ void build_iv(const Knot& a, const Knot& b, double h, IvD& o) {
   interval_phase(a.phd_hi, a.phd_lo, a.phd_rate, b.phd_hi, b.phd_lo, b.phd_rate, h, o.ph);
   interval_phase(a.gam_hi, a.gam_lo, a.gam_rate, b.gam_hi, b.gam_lo, b.gam_rate, h, o.gm);
+  for (int q = 0; q < 4; ++q) o.gm[q] *= 2.0;   // the kernel uses 2 gamma~ (exact scaling)
   interval_phase(a.alp_hi, a.alp_lo, a.alp_rate, b.alp_hi, b.alp_lo, b.alp_rate, h, o.al);
   hermite(a.amp, b.amp - a.amp, a.amp_rate, b.amp_rate, h, o.am);
   hermite(a.e, b.e - a.e, a.e_rate, b.e_rate, h, o.ec);
@@ -673,12 +680,11 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
     const int ki = ks >= kTile ? 0 : t / ks;
     const double s = (double)(j - (kfirst + ki) * ks) * (1.0 / (double)ks);   // ks: a power of two
     const IvD& v = iv[ki];
-    double fph = poly3<double>(v.ph, s);
-    fph -= rint(fph);
-    double fgm = 2.0 * poly3<double>(v.gm, s);
-    fgm -= rint(fgm);
-    double fal = poly3<double>(v.al, s);
-    fal -= rint(fal);
+    // phases in cycles over the knot interval (|f| < 2^20: the table index
+    // wraps them, no reduction to one cycle is needed)
+    const double fph = poly3<double>(v.ph, s);
+    const double fgm = poly3<double>(v.gm, s);
+    const double fal = poly3<double>(v.al, s);
     const double A = poly3<double>(v.am, s);
     double F[4];
     if (!exact_f) {

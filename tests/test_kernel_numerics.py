@@ -146,18 +146,30 @@ def test_fma_folded_stockham_equals_dft(lg, sign):
 
 
 def test_sincos_512_table():
+    """The FP64 kernel's sin/cos of phases in cycles (whole cycles kept):
+    nearest integer k of 512 f by adding 1.5 * 2^52 (the sum's low word is k,
+    subtracting the constant gives k exactly), table entry k mod 512, Taylor
+    polynomials of the exact residual d = f - k/512."""
     pil = np.longdouble("3.14159265358979323846264338327950288")
-    ks = np.arange(-256, 257).astype(np.longdouble)
+    ks = np.arange(512).astype(np.longdouble)
     tc = np.cos(2 * pil * ks / 512).astype(np.float64)
     ts = np.sin(2 * pil * ks / 512).astype(np.float64)
-    f = np.random.default_rng(3).uniform(-0.5, 0.5, 500_000)
-    kd = np.rint(f * 512.0)
+    g = np.random.default_rng(3)
+    f = np.concatenate([g.uniform(-0.5, 0.5, 300_000), g.uniform(-40.0, 40.0, 300_000),
+                        np.array([0.0, -0.0, 1 / 1024, -1 / 1024, 0.5, -0.5, 39.998046875])])
+    big = 6755399441055744.0
+    kb = f * 512.0 + big                        # f * 512 is exact: one rounding, as the FMA
+    kd = kb - big
+    assert np.array_equal(kd, np.rint(f * 512.0))   # round to nearest even
+    k = kb.view(np.int64).astype(np.int32)      # the low word, two's complement
+    assert np.array_equal(k, kd.astype(np.int64).astype(np.int32))
     d = f - kd / 512.0
+    assert np.abs(d).max() <= 1 / 1024
     x = d * 6.283185307179586
     x2 = x * x
     sx = (x2 * x) * (x2 * (1 / 120) - 1 / 6) + x
     cx = x2 * (x2 * (1 / 24) - 0.5) + 1.0
-    idx = kd.astype(int) + 256
+    idx = k & 511
     s = ts[idx] * cx + tc[idx] * sx
     c = tc[idx] * cx - ts[idx] * sx
     fl = f.astype(np.longdouble)

@@ -328,11 +328,11 @@ def serve_bench(ctx, dsets, precision: int, rate: float, duration: float, n_max:
 
 
 # DRAM bytes per sample of k2_wave_f64 from one ncu capture of the kernel
-# (64 walkers x 2^20 samples, n_max 20: 71.18 MB read + 1013.20 MB written;
+# (64 walkers x 2^20 samples, n_max 20: 71.52 MB read + 1013.74 MB written;
 # profiles/ncu_k2_wave_f64_64w_2p20.md), scaled to a launch by the samples it
 # processes (the kernel's traffic is its 16-byte output per sample plus the
 # per-tile orbit records, both proportional to walkers x samples).
-K2_F64_DRAM_BYTES_PER_SAMPLE = (71.178e6 + 1013.201e6) / (64 * 2 ** 20)
+K2_F64_DRAM_BYTES_PER_SAMPLE = (71.517e6 + 1013.742e6) / (64 * 2 ** 20)
 
 
 def paper_bench(ctx, steps: int, warmup: int):
@@ -496,6 +496,41 @@ def sharded_bench(ctx, args, rank: int, world: int, steps: int, warmup: int, flu
             "exchange": "all-gather of the moved walker blocks after each half-step (NCCL)"}
 
 
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of the GB300s (MEASURED_PEAKS.json),
+    else the recipe's fallback."""
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def mixed_roofline(kt, walkers: int, n: int, n_max: int, steps: int):
+    """Roofline of each kernel of the mixed step from the live event times:
+    the waveform kernel against the derived FP32 peak (algorithmic flops:
+    the flop model per sample, in FP32), the two FFT passes against the
+    measured HBM bandwidth (algorithmic bytes: pass 1 reads and writes the
+    8-byte series, pass 2 reads it once; the dataset and delay tables it also
+    reads are L2-resident and not counted)."""
+    hbm, src = hbm_peak_gbs()
+    out = {}
+    samples = float(walkers) * n * steps
+    if kt.get("wave", (0, 0))[1]:
+        ms = kt["wave"][0]
+        tf = flop_model(n_max) * samples / (ms / 1e3) / 1e12
+        out["k2_wave_mixed"] = {"bound": "alu", "achieved": tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                "frac": tf / FP32_PEAK_TFLOPS, "ms_per_step": ms / steps,
+                                "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x 2.07 GHz"}
+    for name, key, per_sample in (("k3_pass1<float2>", "fft_pass1", 16.0), ("k4_pass2_ip<float2>", "fft_pass2_ip", 8.0)):
+        if kt.get(key, (0, 0))[1]:
+            ms = kt[key][0]
+            gbs = per_sample * samples / (ms / 1e3) / 1e9
+            out[name] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "ms_per_step": ms / steps, "peak_source": src}
+    return out
+
+
 def flop_model(n_max: int) -> float:
     """Algorithmic FP64 flops per sample of the factored harmonic sum and
     response (see the design notes; an FMA counts two): 24 per harmonic
@@ -626,7 +661,8 @@ def main():
         lm = lnl.cpu().numpy()
         mixed = {"value": W * world * args.steps / (mt / 1e3), "unit": "lnL/s", "ms_per_step": mt / args.steps,
                  "dlnl_max_vs_fp64": float(np.max(np.abs(lm - lnl64))),
-                 "kernels_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in kt_mix.items() if v[1]}}
+                 "kernels_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in kt_mix.items() if v[1]},
+                 "roofline": mixed_roofline(kt_mix, W, wl.n, wl.n_max, args.steps)}
 
     # ---- end to end through the C-ABI with host buffers (FP64)
     th_host = torch.tensor(theta.T.copy(), dtype=torch.float64).pin_memory()

@@ -230,7 +230,7 @@ int emri_fft_batch(emri_ctx* ctx, void* z_dev, int64_t n, int batch, int precisi
  * context: the scratch the second pass writes (32 MiB: at least one whole
  * sequence, several when they are shorter) and the twiddle tables are
  * file-scope static device arrays of the library
- * (EMRI_NOALLOC_SCRATCH_BYTES of scratch plus 184 KiB of tables, held on
+ * (EMRI_NOALLOC_SCRATCH_BYTES of scratch plus 216 KiB of tables, held on
  * every GPU that loads the library until the process exits).  Nothing is
  * allocated by the call.
  *  - Limit: one sequence must fit the scratch, n * 16 B (FP64) or n * 8 B
@@ -309,6 +309,9 @@ typedef struct {
   double* dh_dev;          /* nullable */
   double* hh_dev;          /* nullable */
   uint32_t* status_dev;    /* nullable */
+  const emri_fdprop* fd;   /* nullable (host struct): the chain's frequency-dependent
+                              propagation, as in emri_loglike_batch_fd; its
+                              coef_dev [q_m + q_t][w] is part of the graph's key */
 } emri_work;
 
 int emri_loglike_multi(emri_ctx* ctx, const emri_work* items, int n_items, void* stream);
@@ -399,6 +402,15 @@ int emri_serve_stop(emri_ctx* ctx);
  * queue is full; EMRI_EBUDGET when the request alone exceeds the budget. */
 int emri_serve_submit(emri_ctx* ctx, const emri_dataset* ds, const double* theta_host, int w,
                       const emri_opts* opts, uint64_t* ticket);
+
+/* emri_serve_submit with the frequency-dependent propagation of
+ * emri_loglike_batch_fd (paper Sec. 2, alpha_M(f), alpha_T(f)): q_m, q_t in
+ * [0, 3], f_star > 0, coef_host[q_m + q_t][W] (host, copied before return;
+ * NULL allowed when q_m + q_t = 0).  Results equal emri_loglike_batch_fd on
+ * the same walkers. */
+int emri_serve_submit_fd(emri_ctx* ctx, const emri_dataset* ds, const double* theta_host, int w,
+                         const emri_opts* opts, int q_m, int q_t, double f_star, const double* coef_host,
+                         uint64_t* ticket);
 
 /* Pool bytes a request of W walkers against `ds` with `opts` holds while it
  * runs (host query; a request larger than the pool is refused at submit). */

@@ -405,7 +405,7 @@ extern "C" int emri_ctx_create(int device, size_t budget, emri_ctx** out) {
   // twiddle and quadrature tables
   constexpr size_t kBc = (size_t)emri::kBesselOrders * emri::kBesselTerms;
   size_t tb = 4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8 + 64 * 8 + kBc * 12 + emri::kBesselOrders * 12 + 256 +
-              (32 + 129) * 32 * 8 + 4096 * 16;
+              (32 + 129) * 32 * 8 + 4096 * 16 + 16 + 4096 * 8;
   char* p = nullptr;
   e2 = cudaMalloc(&p, tb);
   if (e2 != cudaSuccess) {
@@ -431,6 +431,9 @@ extern "C" int emri_ctx_create(int device, size_t budget, emri_ctx** out) {
     size_t off = kBc * 12 + no * 12;
     off = (off + 7) & ~(size_t)7;   // 8-byte aligned (q is)
     c->mcpi = (double*)(q + off);
+    // the FP32 stage twiddles after the orbit tables, 16-byte aligned
+    const uintptr_t tt = ((uintptr_t)(c->mcpi + (32 + 129) * 32) + 15) & ~(uintptr_t)15;
+    c->tw.tt32 = (float2*)tt;
   }
   double glh[64];
   gauss_legendre32(glh, glh + 32);

@@ -98,7 +98,7 @@ struct FdW {
 
 
 // Mixed-precision interval record of one knot interval: the three phases
-// (Doppler orbital phase, gamma~, alpha; cycles) as 64-bit fixed point
+// (Doppler orbital phase, 2 gamma~, alpha; cycles) as 64-bit fixed point
 // base + inc * tau plus FP32 s^2, s^3 corrections (s = tau / K_s), and the
 // amplitude x^(2/3) and eccentricity cubics in FP32.
 struct IvM {

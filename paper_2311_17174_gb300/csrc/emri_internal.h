@@ -41,6 +41,7 @@ struct Twiddles {
   float2* ta32;
   float2* tb32;
   double2* tc64;   // (cos, tan) of -2 pi k / 4096, |cos| >= 2^-60
+  float2* tt32;    // stage twiddles: tt32[M/2 + k] = exp(-2 pi i k / M), M = 2..4096, k < M/2
 };
 
 void launch_twiddle_init(Twiddles t, cudaStream_t s);

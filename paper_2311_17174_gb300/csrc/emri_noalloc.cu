@@ -35,9 +35,9 @@ using namespace emri;
 // Scratch of EMRI_NOALLOC_SCRATCH_BYTES (32 MiB): at least one sequence
 // (2^21 double2 or 2^22 float2 values), more when they are shorter.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[EMRI_NOALLOC_SCRATCH_BYTES];
-// Twiddle tables: ta64[4096], tb64[1024], ta32[4096], tb32[1024], tc64[4096].
+// Twiddle tables: ta64[4096], tb64[1024], ta32[4096], tb32[1024], tc64[4096], tt32[4096].
 static __device__ __align__(256) unsigned char g_noalloc_tables[4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8 +
-                                                                4096 * 16];
+                                                                4096 * 16 + 4096 * 8];
 
 namespace {
 
@@ -78,6 +78,7 @@ int setup_device(int dev, cudaStream_t s, DevState** out) {
     st.tw.ta32 = (float2*)(t + 4096 * 16 + 1024 * 16);
     st.tw.tb32 = (float2*)(t + 4096 * 16 + 1024 * 16 + 4096 * 8);
     st.tw.tc64 = (double2*)(t + 4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8);
+    st.tw.tt32 = (float2*)(t + 4096 * 16 + 1024 * 16 + 4096 * 8 + 1024 * 8 + 4096 * 16);
     launch_twiddle_init(st.tw, s);
     fft_set_smem_limits();
     e = cudaStreamSynchronize(s);

@@ -18,6 +18,7 @@
 // slot.  The scheduler never allocates or frees device memory.  The kernels
 // reduce in a fixed order per walker, so a request's results are bitwise the
 // same alone or in a mix.
+#include <math.h>
 #include <time.h>
 
 #include <algorithm>
@@ -59,6 +60,10 @@ struct Request {
   std::vector<double> theta;   // [16][w]
   int w = 0;
   OptsN o{};
+  bool fd = false;             // frequency-dependent propagation (paper Sec. 2)
+  int qm = 0, qt = 0;
+  double fstar = 1.0;
+  std::vector<double> coef;    // [qm + qt][w]
   size_t need = 0;             // pool bytes: parameters and results, then the workspace
   size_t off = 0;              // its range of the pool while it runs
   int bypassed = 0;            // later requests admitted while this one waited
@@ -130,11 +135,15 @@ static void pool_give(Server* sv, size_t off, size_t bytes) {
 
 static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Pool bytes of a request: parameters, lnL and status, then the workspace of
-// the likelihood path.
-static size_t request_bytes(const emri_dataset* ds, const OptsN& o, int w, int wave) {
-  return round256(sizeof(double) * (kNParam + 2) * (size_t)w) +
-         round256(loglike_layout(ds->plan, o, w, wave, nullptr, nullptr));
+// Most frequency-dependent coefficients per walker (q_m + q_t <= 6).
+constexpr int kMaxCoef = 6;
+
+// Pool bytes of a request: parameters, lnL and status (and the propagation
+// coefficients and records when fd), then the workspace of the likelihood
+// path.
+static size_t request_bytes(const emri_dataset* ds, const OptsN& o, int w, int wave, bool fd, int ncoef) {
+  return round256(sizeof(double) * (kNParam + 2 + (size_t)ncoef) * (size_t)w) +
+         (fd ? round256(sizeof(FdW) * (size_t)w) : 0) + round256(loglike_layout(ds->plan, o, w, wave, nullptr, nullptr));
 }
 
 // Pinned staging for w walkers (host memory only; outgrown buffers are kept
@@ -144,7 +153,7 @@ static int slot_staging(Slot& sl, int w) {
   const size_t cap = std::max<size_t>((size_t)w, 2 * sl.h_cap);
   double *t = nullptr, *l = nullptr;
   uint32_t* st = nullptr;
-  if (cudaHostAlloc(&t, sizeof(double) * kNParam * cap, cudaHostAllocDefault) != cudaSuccess ||
+  if (cudaHostAlloc(&t, sizeof(double) * (kNParam + kMaxCoef) * cap, cudaHostAllocDefault) != cudaSuccess ||
       cudaHostAlloc(&l, sizeof(double) * cap, cudaHostAllocDefault) != cudaSuccess ||
       cudaHostAlloc(&st, sizeof(uint32_t) * cap, cudaHostAllocDefault) != cudaSuccess) {
     if (t) sl.retired.push_back(t);
@@ -175,17 +184,32 @@ static void launch_request(Server* sv, Slot& sl, const std::shared_ptr<Request>&
     sv->cv_done.notify_all();
     return;
   }
+  const size_t nc = r->coef.size();
   memcpy(sl.h_theta, r->theta.data(), sizeof(double) * kNParam * r->w);
+  if (nc) memcpy(sl.h_theta + (size_t)kNParam * r->w, r->coef.data(), sizeof(double) * nc);
   char* base = sv->pool + r->off;
   double* d_theta = (double*)base;
   double* d_lnl = d_theta + (size_t)kNParam * r->w;
   uint32_t* d_st = (uint32_t*)(d_lnl + r->w);
+  double* d_coef = d_lnl + 2 * (size_t)r->w;   // [qm + qt][w], after lnL and status
   cudaMemcpyAsync(d_theta, sl.h_theta, sizeof(double) * kNParam * r->w, cudaMemcpyHostToDevice, sl.stream);
-  Carve cv(base + round256(sizeof(double) * (kNParam + 2) * (size_t)r->w));
+  if (nc) cudaMemcpyAsync(d_coef, sl.h_theta + (size_t)kNParam * r->w, sizeof(double) * nc, cudaMemcpyHostToDevice,
+                          sl.stream);
+  Carve cv(base + round256(sizeof(double) * (kNParam + 2 + nc / (size_t)r->w) * (size_t)r->w));
+  FdW* fdw = nullptr;
+  int64_t nl = 0;
+  if (r->fd) {
+    fdw = cv.take<FdW>(r->w);
+    cv.off = round256(cv.off);
+    launch_fdprop(d_theta, r->w, r->w, r->ds->n, r->ds->dt, r->o, r->qm, r->qt, r->fstar, d_coef, fdw, sl.stream);
+    nl += 1;
+  }
   LoglikeBufs b;
   loglike_layout(r->ds->plan, r->o, r->w, r->wave, &cv, &b);
-  int64_t nl = 0;
-  rc = run_loglike(ctx, r->ds, d_theta, r->w, r->w, r->o, r->wave, b, d_lnl, nullptr, nullptr, d_st, sl.stream, &nl);
+  int64_t nr = 0;
+  rc = run_loglike(ctx, r->ds, d_theta, r->w, r->w, r->o, r->wave, b, d_lnl, nullptr, nullptr, d_st, sl.stream, &nr,
+                   fdw);
+  nl += nr;
   cudaMemcpyAsync(sl.h_lnl, d_lnl, sizeof(double) * r->w, cudaMemcpyDeviceToHost, sl.stream);
   cudaMemcpyAsync(sl.h_st, d_st, sizeof(uint32_t) * r->w, cudaMemcpyDeviceToHost, sl.stream);
   cudaEventRecord(sl.done, sl.stream);
@@ -404,8 +428,9 @@ extern "C" int emri_serve_stop(emri_ctx* ctx) {
   return EMRI_OK;
 }
 
-extern "C" int emri_serve_submit(emri_ctx* ctx, const emri_dataset* ds, const double* theta_host, int w,
-                                 const emri_opts* opts, uint64_t* ticket) {
+static int serve_submit(emri_ctx* ctx, const emri_dataset* ds, const double* theta_host, int w,
+                        const emri_opts* opts, bool fd, int qm, int qt, double fstar, const double* coef_host,
+                        uint64_t* ticket) {
   if (!ctx || !ds || !ticket) return set_err(EMRI_EINVAL, "NULL argument");
   const std::shared_ptr<Server> sp = server_of(ctx);
   Server* sv = sp.get();
@@ -413,17 +438,29 @@ extern "C" int emri_serve_submit(emri_ctx* ctx, const emri_dataset* ds, const do
   if (ds->ctx != ctx) return set_err(EMRI_EINVAL, "dataset belongs to another context");
   if (w < 1) return set_err(EMRI_EINVAL, "w must be >= 1");
   if (!theta_host) return set_err(EMRI_EINVAL, "NULL theta");
+  if (fd) {
+    if (qm < 0 || qm > 3 || qt < 0 || qt > 3) return set_err(EMRI_EINVAL, "q_m and q_t must be in [0, 3]");
+    if (!(fstar > 0) || !isfinite(fstar)) return set_err(EMRI_EINVAL, "f_star must be positive and finite");
+    if (qm + qt > 0 && !coef_host) return set_err(EMRI_EINVAL, "NULL propagation coefficients");
+  }
   auto r = std::make_shared<Request>();
   int rc = normalize_opts(opts, ds->n, &r->o);
   if (rc) return rc;
   r->ds = ds;
   r->w = w;
   r->theta.assign(theta_host, theta_host + (size_t)kNParam * w);
+  r->fd = fd;
+  if (fd) {
+    r->qm = qm;
+    r->qt = qt;
+    r->fstar = fstar;
+    if (qm + qt > 0) r->coef.assign(coef_host, coef_host + (size_t)(qm + qt) * w);
+  }
   {
     std::lock_guard<std::mutex> clk(ctx->mu);   // the tuned plans
     r->wave = pick_wave(ctx, ds->plan, r->o, w);
   }
-  r->need = request_bytes(ds, r->o, w, r->wave);
+  r->need = request_bytes(ds, r->o, w, r->wave, fd, fd ? qm + qt : 0);
   r->lnl.assign(w, 0.0);
   r->st.assign(w, 0u);
   std::lock_guard<std::mutex> lk(sv->mu);
@@ -441,6 +478,17 @@ extern "C" int emri_serve_submit(emri_ctx* ctx, const emri_dataset* ds, const do
   return EMRI_OK;
 }
 
+extern "C" int emri_serve_submit(emri_ctx* ctx, const emri_dataset* ds, const double* theta_host, int w,
+                                 const emri_opts* opts, uint64_t* ticket) {
+  return serve_submit(ctx, ds, theta_host, w, opts, false, 0, 0, 1.0, nullptr, ticket);
+}
+
+extern "C" int emri_serve_submit_fd(emri_ctx* ctx, const emri_dataset* ds, const double* theta_host, int w,
+                                    const emri_opts* opts, int q_m, int q_t, double f_star, const double* coef_host,
+                                    uint64_t* ticket) {
+  return serve_submit(ctx, ds, theta_host, w, opts, true, q_m, q_t, f_star, coef_host, ticket);
+}
+
 extern "C" int emri_serve_request_bytes(emri_ctx* ctx, const emri_dataset* ds, int w, const emri_opts* opts,
                                         size_t* bytes) {
   if (!ctx || !ds || !bytes) return set_err(EMRI_EINVAL, "NULL argument");
@@ -450,7 +498,7 @@ extern "C" int emri_serve_request_bytes(emri_ctx* ctx, const emri_dataset* ds, i
   int rc = normalize_opts(opts, ds->n, &o);
   if (rc) return rc;
   std::lock_guard<std::mutex> clk(ctx->mu);   // the tuned plans
-  *bytes = request_bytes(ds, o, w, pick_wave(ctx, ds->plan, o, w));
+  *bytes = request_bytes(ds, o, w, pick_wave(ctx, ds->plan, o, w), false, 0);
   return EMRI_OK;
 }
 
@@ -526,6 +574,14 @@ extern "C" int emri_loglike_multi(emri_ctx* ctx, const emri_work* items, int n_i
     if (it.w > 0 && (!it.theta_dev || !it.lnl_dev)) return set_err(EMRI_EINVAL, "item %d: NULL pointer", i);
     int rc = normalize_opts(&it.opts, it.ds->n, &on[i]);
     if (rc) return rc;
+    if (it.fd) {
+      if (it.fd->q_m < 0 || it.fd->q_m > 3 || it.fd->q_t < 0 || it.fd->q_t > 3)
+        return set_err(EMRI_EINVAL, "item %d: q_m and q_t must be in [0, 3]", i);
+      if (!(it.fd->f_star > 0) || !isfinite(it.fd->f_star))
+        return set_err(EMRI_EINVAL, "item %d: f_star must be positive and finite", i);
+      if (it.w > 0 && it.fd->q_m + it.fd->q_t > 0 && !it.fd->coef_dev)
+        return set_err(EMRI_EINVAL, "item %d: NULL propagation coefficients", i);
+    }
     if (!it.opts.knot_spacing) {   // the autotuner's choice for this shape, if any
       const int pk = ctx_plan_ks(ctx, it.ds->n, on[i]);
       if (pk) on[i].ks = pk;
@@ -544,6 +600,15 @@ extern "C" int emri_loglike_multi(emri_ctx* ctx, const emri_work* items, int n_i
     memcpy(&f[1], &on[i].omega_m, 8);
     memcpy(&f[2], &on[i].h0, 8);
     key.insert(key.end(), f, f + 3);
+    if (it.fd) {
+      uint64_t fs;
+      memcpy(&fs, &it.fd->f_star, 8);
+      key.push_back(1 + ((uint64_t)it.fd->q_m << 8) + ((uint64_t)it.fd->q_t << 16));
+      key.push_back(fs);
+      key_push(key, it.fd->coef_dev);
+    } else {
+      key.push_back(0);
+    }
   }
   if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(EMRI_ECUDA, "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
@@ -574,8 +639,9 @@ extern "C" int emri_loglike_multi(emri_ctx* ctx, const emri_work* items, int n_i
       wave[i] = (int)std::max<size_t>(1, std::min<size_t>((size_t)items[i].w, ((size_t)512 << 20) / per));
       const int pw = ctx_plan_wave(ctx, items[i].ds->n, on[i]);
       if (pw > 0 && pw < wave[i]) wave[i] = pw;
-      int rc = m->ws[i].reserve(ctx, loglike_layout(items[i].ds->plan, on[i], items[i].w, wave[i], nullptr, nullptr),
-                                m->cap);
+      const size_t fdb = items[i].fd ? ((sizeof(FdW) * (size_t)items[i].w + 255) & ~(size_t)255) : 0;
+      int rc = m->ws[i].reserve(
+          ctx, fdb + loglike_layout(items[i].ds->plan, on[i], items[i].w, wave[i], nullptr, nullptr), m->cap);
       if (rc) {
         multi_destroy(ctx);
         return rc;
@@ -593,11 +659,20 @@ extern "C" int emri_loglike_multi(emri_ctx* ctx, const emri_work* items, int n_i
         cudaStreamWaitEvent(br, m->fork, 0);
         if (items[i].w > 0) {
           Carve cv(m->ws[i].ptr);
+          FdW* fdw = nullptr;
+          const emri_fdprop* fd = items[i].fd;
+          if (fd) {
+            fdw = cv.take<FdW>(items[i].w);
+            cv.off = (cv.off + 255) & ~(size_t)255;
+            launch_fdprop(items[i].theta_dev, items[i].w, items[i].w, items[i].ds->n, items[i].ds->dt, on[i],
+                          fd->q_m, fd->q_t, fd->f_star, fd->coef_dev, fdw, br);
+            m->launches += 1;
+          }
           LoglikeBufs b;
           loglike_layout(items[i].ds->plan, on[i], items[i].w, wave[i], &cv, &b);
           int64_t nl = 0;
           rc = run_loglike(ctx, items[i].ds, items[i].theta_dev, items[i].w, items[i].w, on[i], wave[i], b,
-                           items[i].lnl_dev, items[i].dh_dev, items[i].hh_dev, items[i].status_dev, br, &nl);
+                           items[i].lnl_dev, items[i].dh_dev, items[i].hh_dev, items[i].status_dev, br, &nl, fdw);
           m->launches += nl;
         }
         cudaEventRecord(m->joins[i], br);

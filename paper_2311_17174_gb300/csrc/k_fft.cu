@@ -49,7 +49,11 @@ FftPlan make_fft_plan(int64_t n, int n2) {
 // where the cosine is zero (a quarter turn) it is replaced by 2^-60 and the
 // tangent by sin * 2^60, so c * t = sin exactly and the stray c * Re part is
 // below 1e-18 relative.
-__global__ void k_twiddle_init(double2* ta64, double2* tb64, float2* ta32, float2* tb32, double2* tc64) {
+// tt32[M/2 + k] = exp(-2 pi i k / M) for M = 2, 4, ..., 4096 and k < M/2: the
+// twiddles of one FFT stage of size M in consecutive entries (the same values
+// as ta32[k 4096 / M]), so the threads of a stage read them coalesced.
+__global__ void k_twiddle_init(double2* ta64, double2* tb64, float2* ta32, float2* tb32, double2* tc64,
+                               float2* tt32) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < 4096) {
     double s, c;
@@ -58,6 +62,14 @@ __global__ void k_twiddle_init(double2* ta64, double2* tb64, float2* ta32, float
     ta32[i] = make_float2((float)c, (float)s);
     const double cf = fabs(c) < 0x1p-60 ? 0x1p-60 : c;
     tc64[i] = make_double2(cf, s / cf);
+    if (i == 0) {
+      tt32[0] = make_float2(1.f, 0.f);
+    } else {
+      const int half = 1 << (31 - __clz(i));   // M / 2
+      double ts, tc;
+      sincospi(-2.0 * (double)(i - half) / (double)(2 * half), &ts, &tc);
+      tt32[i] = make_float2((float)tc, (float)ts);
+    }
   }
   if (i < 1024) {
     double s, c;
@@ -68,7 +80,7 @@ __global__ void k_twiddle_init(double2* ta64, double2* tb64, float2* ta32, float
 }
 
 void launch_twiddle_init(Twiddles t, cudaStream_t s) {
-  k_twiddle_init<<<16, 256, 0, s>>>(t.ta64, t.tb64, t.ta32, t.tb32, t.tc64);
+  k_twiddle_init<<<16, 256, 0, s>>>(t.ta64, t.tb64, t.ta32, t.tb32, t.tc64, t.tt32);
 }
 
 // ----------------------------------------------------- complex helpers
@@ -421,6 +433,118 @@ struct FftCfg<float2> {
   static constexpr int kMaxB = 4;
 };
 
+// ------------------------------- FP32 pass 2 fused with the IP, in registers
+// Row FFT of N1 = 2^LG points (LG 8..12) by T = N1/8 threads with eight
+// points each in registers: radix-8 Stockham stages, then one radix-4 or
+// radix-2 stage for the remaining bits.  At the start of every stage thread
+// t holds the points t + q T (q < 8) of the stage's input; the first stage
+// loads them from the row in global memory, later ones from a shared buffer
+// the previous stage wrote (element i at i + i/16, which keeps the stride-8
+// writes of the first stage free of bank conflicts), and the last stage
+// leaves the bins k1 = t + q T in registers, where the inner products take
+// them.  Complex arithmetic runs as paired FP32 instructions (f32x2).  The
+// stage twiddles W_M^k (M = R NS) come from the stage table tt, W^2..W^7 by
+// complex products.
+namespace r8 {
+
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+__device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul(float2 a, float2 b) {   // complex a b
+  return __ffma2_rn(make_float2(-a.y, a.y), make_float2(b.y, b.x), __fmul2_rn(make_float2(a.x, a.x), b));
+}
+__device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }   // -i a
+
+// X_q = sum_r a_r exp(-2 pi i q r / 4), in place
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  const float2 s0 = add(a0, a2), s1 = sub(a0, a2), s2 = add(a1, a3), s3 = mul_mi(sub(a1, a3));
+  a0 = add(s0, s2);
+  a2 = sub(s0, s2);
+  a1 = add(s1, s3);
+  a3 = sub(s1, s3);
+}
+
+// X_q = sum_r a_r exp(-2 pi i q r / 8), in place (natural order): split in
+// halves b_r = a_r + a_{r+4} (even outputs) and c_r = (a_r - a_{r+4}) W8^r
+// (odd outputs), then two 4-point DFTs.
+__device__ __forceinline__ void dft8(float2 (&a)[8]) {
+  constexpr float h = 0.70710678118654752440f;
+  float2 b0 = add(a[0], a[4]), b1 = add(a[1], a[5]), b2 = add(a[2], a[6]), b3 = add(a[3], a[7]);
+  float2 c0 = sub(a[0], a[4]), d1 = sub(a[1], a[5]), d2 = sub(a[2], a[6]), d3 = sub(a[3], a[7]);
+  // W8 = h (1 - i): W8 d = h (dx + dy, dy - dx); W8^3 = -h (1 + i): h (dy - dx, -(dx + dy))
+  float2 c1 = __fmul2_rn(make_float2(h, h), add(d1, make_float2(d1.y, -d1.x)));
+  float2 c2 = mul_mi(d2);
+  float2 c3 = __fmul2_rn(make_float2(h, h), make_float2(d3.y - d3.x, -(d3.x + d3.y)));
+  dft4(b0, b1, b2, b3);
+  dft4(c0, c1, c2, c3);
+  a[0] = b0; a[2] = b1; a[4] = b2; a[6] = b3;
+  a[1] = c0; a[3] = c1; a[5] = c2; a[7] = c3;
+}
+
+// multiply a[q] by w^q, q = 1..7 (w^2..w^7 by products)
+__device__ __forceinline__ void twiddle8(float2 (&a)[8], float2 w1) {
+  const float2 w2 = mul(w1, w1), w3 = mul(w2, w1), w4 = mul(w2, w2);
+  const float2 w5 = mul(w4, w1), w6 = mul(w4, w2), w7 = mul(w4, w3);
+  a[1] = mul(a[1], w1); a[2] = mul(a[2], w2); a[3] = mul(a[3], w3); a[4] = mul(a[4], w4);
+  a[5] = mul(a[5], w5); a[6] = mul(a[6], w6); a[7] = mul(a[7], w7);
+}
+
+// Radix-8 stage S (sub-transform length NS = 8^S) of an N1-point row; the
+// inputs are in v, the outputs go to xb (or stay in v for the last stage).
+// NB interleaved transforms: transform c's element i at xb[pad16(i) NB + c];
+// t is the thread's index within its transform.
+template <int LG, int S, int NB = 1>
+__device__ __forceinline__ void stage8(float2 (&v)[8], float2* xb, const float2* __restrict__ tt, int t, int c) {
+  constexpr int N1 = 1 << LG, T = N1 / 8, NS = 1 << (3 * S);
+  const int k = t & (NS - 1);
+  if constexpr (NS > 1) twiddle8(v, tt[4 * NS + k]);   // W_{8 NS}^k
+  dft8(v);
+  if constexpr (8 * NS < N1) {
+    const int d0 = (t / NS) * NS * 8 + k;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) xb[pad16(d0 + q * NS) * NB + c] = v[q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = xb[pad16(t + q * T) * NB + c];
+    __syncthreads();   // every read done before the next stage writes
+  }
+}
+
+template <int LG, int S, int NB = 1>
+__device__ __forceinline__ void stages8(float2 (&v)[8], float2* xb, const float2* __restrict__ tt, int t, int c) {
+  if constexpr (S < LG / 3) {
+    stage8<LG, S, NB>(v, xb, tt, t, c);
+    stages8<LG, S + 1, NB>(v, xb, tt, t, c);
+  }
+}
+
+// The last stage for LG % 3 != 0: radix 4 (two butterflies per thread) or
+// radix 2 (four).  Slot q of v holds bin t + q T afterwards.
+template <int LG>
+__device__ __forceinline__ void last_stage(float2 (&v)[8], const float2* __restrict__ tt, int t) {
+  constexpr int N1 = 1 << LG, T = N1 / 8;
+  if constexpr (LG % 3 == 2) {        // NS = N1/4: butterflies t and t + T over v[0,2,4,6] and v[1,3,5,7]
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float2 w1 = tt[N1 / 2 + t + h * T];   // W_{N1}^k, k = t + h T
+      const float2 w2 = mul(w1, w1), w3 = mul(w2, w1);
+      float2 a0 = v[h], a1 = mul(v[h + 2], w1), a2 = mul(v[h + 4], w2), a3 = mul(v[h + 6], w3);
+      dft4(a0, a1, a2, a3);
+      v[h] = a0; v[h + 2] = a1; v[h + 4] = a2; v[h + 6] = a3;
+    }
+  } else if constexpr (LG % 3 == 1) { // NS = N1/2: butterflies t + i T over v[i], v[i + 4]
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 b = mul(v[i + 4], tt[N1 / 2 + t + i * T]);
+      const float2 a = v[i];
+      v[i] = add(a, b);
+      v[i + 4] = sub(a, b);
+    }
+  }
+}
+
+}  // namespace r8
+
 // ------------------------------------------------------------- pass 1
 // CTA = NB adjacent columns j1, all n2 = 2^LG rows: the tile is staged
 // row-major (rows of NB contiguous elements), transformed along the rows
@@ -451,6 +575,47 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(C2) == 8 ? 2 : 1) k3_pass1
     w = (i & 3) == 0 ? twiddle22(ta, tb, (uint32_t)((j10 + c) * k2) << shift22, sign) : cmul(w, wstep);
     zw[j10 + c + (int64_t)n1 * k2] = cmul(buf[idx], w);
   }
+}
+
+// ------------------------------------------- pass 1, FP32, in registers
+// Forward column transforms of N2 = 2^LG points (LG 8..10), NB adjacent
+// columns per CTA, N2/8 threads per column with eight points each in
+// registers (the radix-8 stages of the pass-2 kernel, the NB columns
+// interleaved in the exchange buffer); thread (c, t) loads column j1 = j10 + c
+// at rows t + q T and, after the transform, holds its bins k2 = t + q T, which
+// it writes back in place times the inter-pass twiddle W_n^{j1 k2}.  The
+// twiddles of a thread are read from the tables at k2 = t and t + 4T and
+// stepped three times by W_n^{j1 T} from each.
+template <int LG, int NB>
+__global__ void __launch_bounds__(NB * (1 << LG) / 8)
+    k3_pass1_r8(float2* __restrict__ z, int64_t n, int n1, int shift22, const float2* __restrict__ ta,
+                const float2* __restrict__ tb, const float2* __restrict__ tt) {
+  constexpr int N2 = 1 << LG, T = N2 / 8;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* xb = reinterpret_cast<float2*>(smraw);
+  const int c = threadIdx.x % NB, t = threadIdx.x / NB;
+  const int j1 = blockIdx.x * NB + c;
+  float2* col = z + (int64_t)blockIdx.y * n + j1;
+  float2 v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = col[(int64_t)n1 * (t + q * T)];
+  r8::stages8<LG, 0, NB>(v, xb, tt, t, c);
+  r8::last_stage<LG>(v, tt, t);
+  const float2 step = twiddle22(ta, tb, (uint32_t)(j1 * T) << shift22, -1);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float2 w = twiddle22(ta, tb, (uint32_t)(j1 * (t + 4 * h * T)) << shift22, -1);
+#pragma unroll
+    for (int q = 4 * h; q < 4 * h + 4; ++q) {
+      col[(int64_t)n1 * (t + q * T)] = r8::mul(v[q], w);
+      w = r8::mul(w, step);
+    }
+  }
+}
+
+template <int LG, int NB>
+constexpr size_t r8p1_smem() {
+  return (size_t)((1 << LG) + (1 << LG) / 16) * NB * sizeof(float2);
 }
 
 // --------------------------------------------------- pass 2, natural order
@@ -674,6 +839,89 @@ __global__ void __launch_bounds__(kPass2Threads, sizeof(C2) == 8 ? 4 : 2)
   }
 }
 
+
+template <int LG, bool FD>
+__global__ void __launch_bounds__((1 << LG) / 8)
+    k4_pass2_ip_r8(const float2* __restrict__ y, int64_t n, int n2, const float2* __restrict__ tt,
+                   const WalkerC* __restrict__ wcs, const float2* __restrict__ dtab, const float2* __restrict__ rtab,
+                   const float2* __restrict__ dperm, const float* __restrict__ wperm, double2* __restrict__ partial,
+                   const FdW* __restrict__ fdw) {
+  constexpr int N1 = 1 << LG, T = N1 / 8, PAD = N1 + N1 / 16;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* xb = reinterpret_cast<float2*>(smraw);   // stage exchange, padded
+  float2* ds = xb + PAD;                            // the row's g = w conj(D)
+  float2* ts = ds + N1;                             // the walker's delay factors
+  float* ws = reinterpret_cast<float*>(ts + N1);    // the row's weights
+  __shared__ AccF red[T / 32];
+  const int t = threadIdx.x;
+  const int k2 = blockIdx.x, wk = blockIdx.y;
+  const int64_t base = (int64_t)k2 * N1;
+  // the inner product's operands, asynchronously while the row is transformed
+  row_async(ds, dperm + base, N1 * (int)sizeof(float2));
+  row_async(ts, dtab + (int64_t)wk * N1, N1 * (int)sizeof(float2));
+  row_async(ws, wperm + base, N1 * (int)sizeof(float));
+  cp_async_commit();
+  const float2* row = y + (int64_t)wk * n + (int64_t)N1 * k2;
+  float2 v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = row[t + q * T];
+  const float2 a = rtab[(int64_t)wk * n2 + k2];   // exp(-2 pi i frac(k2 r))
+  const float2 cnv = make_float2(wcs[wk].cnf[0], wcs[wk].cnf[1]);
+  r8::stages8<LG, 0>(v, xb, tt, t, 0);
+  r8::last_stage<LG>(v, tt, t);
+  cp_async_wait<0>();
+  __syncthreads();
+  // the thread's bins k1 = t + q T in plain FP32, then the compensated tree
+  float zr = 0.f, zi = 0.f, shh = 0.f;
+  FdW fd;
+  if (FD) fd = fdw[wk];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int k1 = t + q * T;
+    const float2 H = v[q];
+    const float wv = ws[k1];
+    const float2 G = ds[k1];
+    float2 P = cmul(H, ts[k1]);
+    if (2 * k1 == N1 && k2 > 0) P = cmul(P, cnv);   // the one negative bin of this column not in the table
+    float A2 = 1.f;
+    if (FD) {
+      const bool neg = 2 * k1 > N1 || (2 * k1 == N1 && k2 > 0);
+      const long long kk = (long long)k2 + (long long)n2 * k1;
+      const unsigned long long ak = (unsigned long long)(neg ? n - kk : kk);
+      float c, sn;
+      const float A = fd_factor<float>(fd, ak, neg, c, sn);
+      P = cmul(P, make_float2(A * c, A * sn));
+      A2 = A * A;
+    }
+    zr += G.x * P.x - G.y * P.y;
+    zi += G.x * P.y + G.y * P.x;
+    shh += wv * (H.x * H.x + H.y * H.y) * A2;
+  }
+  const float sdh = a.x * zr - a.y * zi;
+  AccF acc;
+  acc.init();
+  acc.add(sdh, shh);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc.shfl_merge(off);
+  const int lane = t & 31, wid = t >> 5;
+  if (lane == 0) red[wid] = acc;
+  __syncthreads();
+  if (wid == 0) {
+    constexpr int NW = T / 32;
+    AccF r;
+    if (lane < NW) r = red[lane];
+    else r.init();
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) r.shfl_merge(off);
+    if (lane == 0) partial[(int64_t)wk * n2 + k2] = r.get();
+  }
+}
+
+template <int LG>
+constexpr size_t r8_smem() {
+  return (size_t)((1 << LG) + (1 << LG) / 16) * sizeof(float2) + (size_t)(1 << LG) * (2 * sizeof(float2) + sizeof(float));
+}
+
 // --------------------------------------------------------------- finalize
 __global__ void k5_finalize(const double2* __restrict__ partial, int n2, const WalkerC* __restrict__ wcs, int w,
                             double dh_scale, double hh_scale, double* __restrict__ lnl, double* __restrict__ dh,
@@ -786,9 +1034,33 @@ static void pass1_dispatch(C2* z, int batch, const FftPlan& p, int sign, const C
   }
 }
 
+static int log2i(int v) {
+  int lg = 0;
+  while ((1 << lg) < v) ++lg;
+  return lg;
+}
+
+// columns per CTA of the FP32 register pass 1 (8 x 8 B = 64-byte row segments)
+constexpr int kP1Cols = 8;
+
 void launch_fft_pass1(void* z, int batch, const FftPlan& p, bool fp32, int sign, const Twiddles& t,
                       cudaStream_t s) {
   if (batch <= 0) return;
+  const int lg2 = log2i(p.n2);
+  if (fp32 && sign < 0 && lg2 >= 8 && p.n1 % kP1Cols == 0) {   // forward, columns of 256..1024 points
+    dim3 g(p.n1 / kP1Cols, batch);
+    const int shift = 22 - p.log2n;
+    float2* zz = (float2*)z;
+#define CALLP1(L) k3_pass1_r8<L, kP1Cols><<<g, kP1Cols * (1 << L) / 8, r8p1_smem<L, kP1Cols>(), s>>>( \
+      zz, p.n, p.n1, shift, t.ta32, t.tb32, t.tt32)
+    switch (lg2) {
+      case 8: CALLP1(8); break;
+      case 9: CALLP1(9); break;
+      default: CALLP1(10); break;
+    }
+#undef CALLP1
+    return;
+  }
   if (fp32)
     pass1_dispatch<float2, FftCfg<float2>::kCols>((float2*)z, batch, p, sign, t.ta32, t.tb32, t.ta32, s);
   else
@@ -807,11 +1079,6 @@ void launch_fft_pass1(void* z, int batch, const FftPlan& p, bool fp32, int sign,
     default: CALL(12); break;     \
   }
 
-static int log2i(int v) {
-  int lg = 0;
-  while ((1 << lg) < v) ++lg;
-  return lg;
-}
 
 void launch_fft_pass2_store(const void* y, void* out, int batch, const FftPlan& p, bool fp32, int sign,
                             const Twiddles& t, cudaStream_t s) {
@@ -837,7 +1104,19 @@ static void pass2_ip_dispatch(const void* y, int w, const FftPlan& p, bool fp32,
                               const void* wt_perm, double2* partial, const FdW* fd, cudaStream_t s) {
   dim3 g(p.n2, w);
   const int lg = log2i(p.n1);
-  if (fp32) {
+  if (fp32 && lg >= 8) {   // rows of 256..4096 points: register-resident radix-8 kernel
+#define CALLR8(L) k4_pass2_ip_r8<L, FD><<<g, (1 << L) / 8, r8_smem<L>(), s>>>(                          \
+      (const float2*)y, p.n, p.n2, t.tt32, wc, (const float2*)delay_tab, (const float2*)row_tab,   \
+      (const float2*)data_perm, (const float*)wt_perm, partial, fd)
+    switch (lg) {
+      case 8: CALLR8(8); break;
+      case 9: CALLR8(9); break;
+      case 10: CALLR8(10); break;
+      case 11: CALLR8(11); break;
+      default: CALLR8(12); break;
+    }
+#undef CALLR8
+  } else if (fp32) {
 #define CALLI32(L) k4_pass2_ip<float2, float, AccF, L, FD><<<g, kPass2Threads, P2Smem<float2, float, L>::bytes(), s>>>( \
       (const float2*)y, p.n, p.n2, t.ta32, wc, (const float2*)delay_tab, (const float2*)row_tab,                \
       (const float2*)data_perm, (const float*)wt_perm, partial, fd)
@@ -902,6 +1181,10 @@ void fft_set_smem_limits() {
               raise(k4_pass2_ip<double2, double, AccD, L, true>), raise(k4_pass2_ip<float2, float, AccF, L, true>)
   P2(5); P2(6); P2(7); P2(8); P2(9); P2(10); P2(11); P2(12);
 #undef P2
+#define P3(L) raise(k4_pass2_ip_r8<L, false>), raise(k4_pass2_ip_r8<L, true>)
+  P3(8); P3(9); P3(10); P3(11); P3(12);
+#undef P3
+  raise(k3_pass1_r8<8, kP1Cols>), raise(k3_pass1_r8<9, kP1Cols>), raise(k3_pass1_r8<10, kP1Cols>);
 }
 
 }  // namespace emri

@@ -217,6 +217,7 @@ __device__ void build_iv_mixed(const Knot& a, const Knot& b, double h, int ks, I
   o.ph_c[0] = (float)c[2];
   o.ph_c[1] = (float)c[3];
   interval_phase(a.gam_hi, a.gam_lo, a.gam_rate, b.gam_hi, b.gam_lo, b.gam_rate, h, c);
+  for (int q = 0; q < 4; ++q) c[q] *= 2.0;   // the kernel uses 2 gamma~ (exact scaling)
   o.gm_base = to_q64(c[0]);
   o.gm_inc = to_q64s(c[1] / ks);
   o.gm_c[0] = (float)c[2];
@@ -423,9 +424,9 @@ __device__ __forceinline__ void harmonic_sums(T cph, T sph, T st, const T* __res
 __device__ __forceinline__ void harmonic_sums2(float cphA, float sphA, float stA, float cphB, float sphB, float stB,
                                                const float* __restrict__ bq, int n_max, bool cheb, float3& sA,
                                                float3& sB) {
-  const float2 stA2 = make_float2(stA, stA), stB2 = make_float2(stB, stB);
+  const float2 stA2 = make_float2(stA, stA), stB2 = make_float2(stB, stB), stAB = make_float2(stA, stB);
   float2 accA = make_float2(0.f, 0.f), accB = make_float2(0.f, 0.f);
-  float rA = 0.f, rB = 0.f;
+  float2 rAB = make_float2(0.f, 0.f);   // the c_n sums of both samples, paired
   // harmonic n at (cos n Phi, sin n Phi) = csA, csB
   auto harm = [&](int n, float2 csA, float2 csB) {
     const float4* b = reinterpret_cast<const float4*>(bq + 12 * n);
@@ -435,8 +436,9 @@ __device__ __forceinline__ void harmonic_sums2(float cphA, float sphA, float stA
     const float2 abB = __ffma2_rn(__ffma2_rn(a2, stB2, a1), stB2, a0);
     accA = __ffma2_rn(abA, csA, accA);
     accB = __ffma2_rn(abB, csB, accB);
-    rA = fmaf((z.x * stA + y.w) * stA + y.z, csA.x, rA);
-    rB = fmaf((z.x * stB + y.w) * stB + y.z, csB.x, rB);
+    const float2 rn = __ffma2_rn(__ffma2_rn(make_float2(z.x, z.x), stAB, make_float2(y.w, y.w)), stAB,
+                                 make_float2(y.z, y.z));
+    rAB = __ffma2_rn(rn, make_float2(csA.x, csB.x), rAB);
   };
   // Two harmonics per iteration, each new (cos, sin) pair written over the
   // one it replaces, so no register copies carry the recurrence.
@@ -445,6 +447,7 @@ __device__ __forceinline__ void harmonic_sums2(float cphA, float sphA, float stA
   if (cheb) {
     const float2 tcA = make_float2(2.f * cphA, 2.f * cphA), tcB = make_float2(2.f * cphB, 2.f * cphB);
     float2 vA = make_float2(1.f, 0.f), vB = make_float2(1.f, 0.f);      // harmonic n - 1
+#pragma unroll 2
     for (; n + 1 < n_max; n += 2) {
       harm(n, uA, uB);
       vA = __ffma2_rn(tcA, uA, make_float2(-vA.x, -vA.y));               // harmonic n + 1
@@ -454,6 +457,7 @@ __device__ __forceinline__ void harmonic_sums2(float cphA, float sphA, float stA
       uB = __ffma2_rn(tcB, vB, make_float2(-uB.x, -uB.y));
     }
   } else {
+#pragma unroll 2
     for (; n + 1 < n_max; n += 2) {
       harm(n, uA, uB);
       const float2 vA = make_float2(uA.x * cphA - uA.y * sphA, uA.y * cphA + uA.x * sphA);   // rotations by Phi
@@ -464,8 +468,8 @@ __device__ __forceinline__ void harmonic_sums2(float cphA, float sphA, float stA
     }
   }
   if (n < n_max) harm(n, uA, uB);
-  sA = make_float3(accA.x, accA.y, rA);
-  sB = make_float3(accB.x, accB.y, rB);
+  sA = make_float3(accA.x, accA.y, rAB.x);
+  sB = make_float3(accB.x, accB.y, rAB.y);
 }
 
 // ----------------------------------------------------------- response
@@ -777,8 +781,7 @@ __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict
     const float s = (float)tau * inv_ks;
     const IvM& v = iv[ki];
     const float fph = phase_fx(v.ph_base, v.ph_inc, v.ph_c, tau, s);
-    float c2[2] = {2.f * v.gm_c[0], 2.f * v.gm_c[1]};
-    const float fgm = phase_fx(v.gm_base << 1, (long long)((unsigned long long)v.gm_inc << 1), c2, tau, s);
+    const float fgm = phase_fx(v.gm_base, v.gm_inc, v.gm_c, tau, s);   // 2 gamma~
     const float fal = phase_fx(v.al_base, v.al_inc, v.al_c, tau, s);
     A = poly3<float>(v.am, s);
     // hardware sin/cos of the reduced angles (|x| <= pi, absolute error ~5e-7)

@@ -42,12 +42,6 @@ class Opts(C.Structure):
                 ("omega_m", C.c_double), ("h0", C.c_double)]
 
 
-class Work(C.Structure):
-    _fields_ = [("ds", C.c_void_p), ("theta_dev", C.c_void_p), ("w", C.c_int), ("opts", Opts),
-                ("lnl_dev", C.c_void_p), ("dh_dev", C.c_void_p), ("hh_dev", C.c_void_p),
-                ("status_dev", C.c_void_p)]
-
-
 class ServeCfg(C.Structure):
     _fields_ = [("slots", C.c_int), ("queue_capacity", C.c_int), ("budget_bytes", C.c_size_t)]
 
@@ -59,6 +53,12 @@ class ReqStats(C.Structure):
 
 class FdProp(C.Structure):
     _fields_ = [("q_m", C.c_int), ("q_t", C.c_int), ("f_star", C.c_double), ("coef_dev", C.c_void_p)]
+
+
+class Work(C.Structure):
+    _fields_ = [("ds", C.c_void_p), ("theta_dev", C.c_void_p), ("w", C.c_int), ("opts", Opts),
+                ("lnl_dev", C.c_void_p), ("dh_dev", C.c_void_p), ("hh_dev", C.c_void_p),
+                ("status_dev", C.c_void_p), ("fd", C.POINTER(FdProp))]
 
 
 class StretchCfg(C.Structure):
@@ -100,6 +100,8 @@ _SIGS = {
                                     C.POINTER(C.c_uint64)]),
     "emri_serve_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.POINTER(ReqStats),
                                   C.c_int64]),
+    "emri_serve_submit_fd": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(Opts), C.c_int,
+                                       C.c_int, C.c_double, C.c_void_p, C.POINTER(C.c_uint64)]),
     "emri_serve_request_bytes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(Opts),
                                            C.POINTER(C.c_size_t)]),
     "emri_stretch_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(Opts),
@@ -276,11 +278,20 @@ class Context:
                                               _ptr(dh), _ptr(hh), _ptr(status), _stream(stream)))
 
     def loglike_multi(self, items, stream=None):
+        """items: (ds, theta, opts, lnl, dh, hh, status[, fd]) per chain, fd =
+        (q_m, q_t, f_star, coef device tensor [q_m + q_t][w]) or None."""
         arr = (Work * len(items))()
+        fds = []
         for i, it in enumerate(items):
-            ds, theta, o, lnl, dh, hh, st = it
+            ds, theta, o, lnl, dh, hh, st = it[:7]
+            fd = it[7] if len(it) > 7 else None
+            fp = None
+            if fd is not None:
+                q_m, q_t, f_star, coef = fd
+                fds.append(FdProp(int(q_m), int(q_t), float(f_star), _ptr(coef)))
+                fp = C.pointer(fds[-1])
             arr[i] = Work(ds.h.value, _ptr(theta), int(theta.shape[1]), o, _ptr(lnl), _ptr(dh), _ptr(hh),
-                          _ptr(st))
+                          _ptr(st), fp)
         _check(self.lib.emri_loglike_multi(self.h, arr, len(items), _stream(stream)))
 
     def stretch_step(self, ds: "Dataset", theta, lnp, o: Opts, cfg: StretchCfg, u, accepted=None, stream=None):
@@ -312,6 +323,18 @@ class Context:
         th = np.ascontiguousarray(theta_host, dtype=np.float64)
         t = C.c_uint64()
         _check(self.lib.emri_serve_submit(self.h, ds.h, th.ctypes.data, int(th.shape[1]), C.byref(o), C.byref(t)))
+        return t.value
+
+    def serve_submit_fd(self, ds: "Dataset", theta_host, o: Opts, q_m: int, q_t: int, f_star: float,
+                        coef_host=None) -> int:
+        """emri_serve_submit_fd: coef_host [q_m + q_t][W] host array."""
+        import numpy as np
+        th = np.ascontiguousarray(theta_host, dtype=np.float64)
+        cf = None if coef_host is None else np.ascontiguousarray(coef_host, dtype=np.float64)
+        t = C.c_uint64()
+        _check(self.lib.emri_serve_submit_fd(self.h, ds.h, th.ctypes.data, int(th.shape[1]), C.byref(o), int(q_m),
+                                             int(q_t), float(f_star), None if cf is None else cf.ctypes.data,
+                                             C.byref(t)))
         return t.value
 
     def serve_request_bytes(self, ds: "Dataset", w: int, o: Opts) -> int:

@@ -58,3 +58,53 @@ def test_fdprop_matches_oracle():
         assert ei.value.code == emri.EINVAL
     ds.close()
     ctx.close()
+
+
+def test_fdprop_in_multi_chain_graph_and_serving():
+    """The frequency-dependent model through the uneven-batching graph (one
+    chain with it, one without) and through the serving loop: each result
+    equals emri_loglike_batch_fd (or emri_loglike_batch) on the same walkers,
+    bit for bit, in both precisions."""
+    from paper_2311_17174_gb300 import emri
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ctx = emri.Context(0)
+    try:
+        n, dt, nm = 1 << 14, 15.0, 6
+        inj = I.draw_sources(95, 1, n)[0]
+        psd = I.psd_bc04(n, dt)
+        d, inj2, _, _ = O.injection_data(inj, n, dt, psd, 96, O.Opts(n_max=nm), snr=40.0)
+        ds = ctx.dataset(emri.grid(n, dt), d, psd, 1e-4, 1.0 / (2 * dt))
+        g = np.random.default_rng(97)
+        qm, qt, fstar = 2, 1, 3e-3
+        for prec in (0, 1):
+            o = emri.opts(precision=prec, n_max=nm)
+            ths = [I.scatter_walkers(98 + k, inj2, w) for k, w in enumerate((9, 14))]
+            coef = np.concatenate([g.normal(0, 0.3, (9, qm)), g.normal(0, 0.05, (9, qt))], axis=1).T.copy()
+            theta = [torch.tensor(t.T.copy(), device="cuda:0") for t in ths]
+            cdev = torch.tensor(coef, device="cuda:0")
+            alone = [torch.zeros(t.shape[0], dtype=torch.float64, device="cuda:0") for t in ths]
+            ctx.loglike_batch_fd(ds, theta[0], o, qm, qt, fstar, cdev, alone[0])
+            ctx.loglike_batch(ds, theta[1], o, alone[1])
+            outs = [torch.zeros(t.shape[0], dtype=torch.float64, device="cuda:0") for t in ths]
+            items = [(ds, theta[0], o, outs[0], None, None, None, (qm, qt, fstar, cdev)),
+                     (ds, theta[1], o, outs[1], None, None, None)]
+            ctx.loglike_multi(items)
+            ctx.loglike_multi(items)   # the replayed graph
+            torch.cuda.synchronize()
+            for a, b in zip(alone, outs):
+                assert torch.equal(a, b)
+            ctx.serve_start(slots=2, queue_capacity=8, budget_bytes=1 << 30)
+            try:
+                t0 = ctx.serve_submit_fd(ds, ths[0].T.copy(), o, qm, qt, fstar, coef)
+                t1 = ctx.serve_submit(ds, ths[1].T.copy(), o)
+                rc, l0, _, _ = ctx.serve_poll(t0, 9)
+                rc1, l1, _, _ = ctx.serve_poll(t1, 14)
+            finally:
+                ctx.serve_stop()
+            assert rc == emri.OK and rc1 == emri.OK
+            np.testing.assert_array_equal(l0, alone[0].cpu().numpy())
+            np.testing.assert_array_equal(l1, alone[1].cpu().numpy())
+        ds.close()
+    finally:
+        ctx.close()

@@ -145,6 +145,84 @@ def test_fma_folded_stockham_equals_dft(lg, sign):
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 2e-15 * lg
 
 
+def r8_rows_fft(x):
+    """The register-resident FP32 pass-2 row FFT, replayed with the kernel's
+    indexing (threads as array lanes): T = N1/8 threads hold points t + q T;
+    radix-8 Stockham stages with stage twiddles W_{8 NS}^k (powers by
+    products), outputs to (t / NS) 8 NS + k + q NS, then a radix-4 (two
+    butterflies) or radix-2 (four) last stage; slot q ends as bin t + q T."""
+    n1 = x.size
+    lg = n1.bit_length() - 1
+    T = n1 // 8
+    t = np.arange(T)
+    h = np.sqrt(0.5)
+
+    def dft4(a0, a1, a2, a3):
+        s0, s1, s2, s3 = a0 + a2, a0 - a2, a1 + a3, -1j * (a1 - a3)
+        return s0 + s2, s1 + s3, s0 - s2, s1 - s3
+
+    def dft8(a):
+        b = [a[r] + a[r + 4] for r in range(4)]
+        d = [a[r] - a[r + 4] for r in range(4)]
+        c = [d[0], h * (1 - 1j) * d[1], -1j * d[2], -h * (1 + 1j) * d[3]]
+        e, o = dft4(*b), dft4(*c)
+        return [e[0], o[0], e[1], o[1], e[2], o[2], e[3], o[3]]
+
+    def tw(m, k):
+        return np.exp(-2j * np.pi * k / m)
+
+    v = [x[t + q * T] for q in range(8)]
+    for st in range(lg // 3):
+        ns = 8 ** st
+        k = t & (ns - 1)
+        if ns > 1:
+            w1 = tw(8 * ns, k)
+            w2 = w1 * w1; w3 = w2 * w1; w4 = w2 * w2
+            w = [1, w1, w2, w3, w4, w4 * w1, w4 * w2, w4 * w3]
+            v = [v[q] * w[q] for q in range(8)]
+        v = dft8(v)
+        if 8 * ns < n1:
+            xb = np.zeros(n1, dtype=complex)
+            d0 = (t // ns) * ns * 8 + k
+            for q in range(8):
+                xb[d0 + q * ns] = v[q]
+            v = [xb[t + q * T] for q in range(8)]
+    if lg % 3 == 2:
+        for hh in range(2):
+            w1 = tw(n1, t + hh * T)
+            a = dft4(v[hh], v[hh + 2] * w1, v[hh + 4] * w1 * w1, v[hh + 6] * w1 * w1 * w1)
+            v[hh], v[hh + 2], v[hh + 4], v[hh + 6] = a
+    elif lg % 3 == 1:
+        for i in range(4):
+            b = v[i + 4] * tw(n1, t + i * T)
+            v[i], v[i + 4] = v[i] + b, v[i] - b
+    out = np.zeros(n1, dtype=complex)
+    for q in range(8):
+        out[t + q * T] = v[q]
+    return out
+
+
+@pytest.mark.parametrize("lg", [8, 9, 10, 11, 12])
+def test_register_radix8_rows_equal_dft(lg):
+    """Pass 2 of the FP32 path (rows of 256..4096 points): the kernel's
+    stage structure and bin mapping give the forward DFT."""
+    g = np.random.default_rng(lg)
+    x = g.standard_normal(1 << lg) + 1j * g.standard_normal(1 << lg)
+    got = r8_rows_fft(x)
+    ref = np.fft.fft(x)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-14
+
+
+def test_stage_twiddle_table_layout():
+    """tt[M/2 + k] = exp(-2 pi i k / M): entry i belongs to M = 2 * 2^floor(log2 i)
+    and equals the 4096-point table at k * 4096 / M (same double angle)."""
+    for i in range(1, 4096):
+        half = 1 << (i.bit_length() - 1)
+        k, m = i - half, 2 * half
+        assert k < m // 2
+        assert (-2.0 * k / m) == (-2.0 * (k * (4096 // m)) / 4096.0)
+
+
 def test_sincos_512_table():
     """The FP64 kernel's sin/cos of phases in cycles (whole cycles kept):
     nearest integer k of 512 f by adding 1.5 * 2^52 (the sum's low word is k,

@@ -448,37 +448,44 @@ struct FftCfg<float2> {
 namespace r8 {
 
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+// plain componentwise complex add / subtract as paired FP32 instructions
 __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
-__device__ __forceinline__ float2 mul(float2 a, float2 b) {   // complex a b
-  return __ffma2_rn(make_float2(-a.y, a.y), make_float2(b.y, b.x), __fmul2_rn(make_float2(a.x, a.x), b));
+// complex a b in scalar FMAs (a paired form would need swizzled operand pairs)
+__device__ __forceinline__ float2 mul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
-__device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }   // -i a
 
-// X_q = sum_r a_r exp(-2 pi i q r / 4), in place
+// X_q = sum_r a_r exp(-2 pi i q r / 4), in place; the -i rotation in scalar adds
 __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
-  const float2 s0 = add(a0, a2), s1 = sub(a0, a2), s2 = add(a1, a3), s3 = mul_mi(sub(a1, a3));
+  const float2 s0 = add(a0, a2), s1 = sub(a0, a2), s2 = add(a1, a3), d = sub(a1, a3);
   a0 = add(s0, s2);
   a2 = sub(s0, s2);
-  a1 = add(s1, s3);
-  a3 = sub(s1, s3);
+  a1 = make_float2(s1.x + d.y, s1.y - d.x);   // s1 - i d
+  a3 = make_float2(s1.x - d.y, s1.y + d.x);   // s1 + i d
 }
 
 // X_q = sum_r a_r exp(-2 pi i q r / 8), in place (natural order): split in
 // halves b_r = a_r + a_{r+4} (even outputs) and c_r = (a_r - a_{r+4}) W8^r
-// (odd outputs), then two 4-point DFTs.
+// (odd outputs), then two 4-point DFTs; c_2 = -i d_2 enters the second one
+// in scalar adds.
 __device__ __forceinline__ void dft8(float2 (&a)[8]) {
   constexpr float h = 0.70710678118654752440f;
   float2 b0 = add(a[0], a[4]), b1 = add(a[1], a[5]), b2 = add(a[2], a[6]), b3 = add(a[3], a[7]);
-  float2 c0 = sub(a[0], a[4]), d1 = sub(a[1], a[5]), d2 = sub(a[2], a[6]), d3 = sub(a[3], a[7]);
-  // W8 = h (1 - i): W8 d = h (dx + dy, dy - dx); W8^3 = -h (1 + i): h (dy - dx, -(dx + dy))
-  float2 c1 = __fmul2_rn(make_float2(h, h), add(d1, make_float2(d1.y, -d1.x)));
-  float2 c2 = mul_mi(d2);
-  float2 c3 = __fmul2_rn(make_float2(h, h), make_float2(d3.y - d3.x, -(d3.x + d3.y)));
+  const float2 d0 = sub(a[0], a[4]), d1 = sub(a[1], a[5]), d2 = sub(a[2], a[6]), d3 = sub(a[3], a[7]);
+  // W8 d1 = h (d1.x + d1.y, d1.y - d1.x); W8^3 d3 = h (d3.y - d3.x, -(d3.x + d3.y))
+  const float2 c1 = __fmul2_rn(make_float2(h, h), make_float2(d1.x + d1.y, d1.y - d1.x));
+  const float2 c3 = __fmul2_rn(make_float2(h, h), make_float2(d3.y - d3.x, -(d3.x + d3.y)));
   dft4(b0, b1, b2, b3);
-  dft4(c0, c1, c2, c3);
+  // 4-point DFT of (d0, c1, -i d2, c3)
+  const float2 s0 = make_float2(d0.x + d2.y, d0.y - d2.x);   // d0 + (-i d2)
+  const float2 s1 = make_float2(d0.x - d2.y, d0.y + d2.x);   // d0 - (-i d2)
+  const float2 s2 = add(c1, c3), dd = sub(c1, c3);
   a[0] = b0; a[2] = b1; a[4] = b2; a[6] = b3;
-  a[1] = c0; a[3] = c1; a[5] = c2; a[7] = c3;
+  a[1] = add(s0, s2);
+  a[5] = sub(s0, s2);
+  a[3] = make_float2(s1.x + dd.y, s1.y - dd.x);
+  a[7] = make_float2(s1.x - dd.y, s1.y + dd.x);
 }
 
 // multiply a[q] by w^q, q = 1..7 (w^2..w^7 by products)
@@ -489,32 +496,36 @@ __device__ __forceinline__ void twiddle8(float2 (&a)[8], float2 w1) {
   a[5] = mul(a[5], w5); a[6] = mul(a[6], w6); a[7] = mul(a[7], w7);
 }
 
-// Radix-8 stage S (sub-transform length NS = 8^S) of an N1-point row; the
-// inputs are in v, the outputs go to xb (or stay in v for the last stage).
-// NB interleaved transforms: transform c's element i at xb[pad16(i) NB + c];
-// t is the thread's index within its transform.
-template <int LG, int S, int NB = 1>
-__device__ __forceinline__ void stage8(float2 (&v)[8], float2* xb, const float2* __restrict__ tt, int t, int c) {
-  constexpr int N1 = 1 << LG, T = N1 / 8, NS = 1 << (3 * S);
+// Radix-8 stage S (sub-transform length NS = 8^S) of an N-point transform
+// whose element i sits at xb[pad16(i)]; t is the thread's index.  The
+// padded positions of a thread's writes d0 + q NS and reads t + q T are
+// pad16(base) plus the compile-time offsets q NS + (q NS >> 4) and
+// q (T + T/16): the low four bits of base and of q NS never carry into
+// bit 4 (d0 mod 16 + q NS mod 16 < 16 for NS = 1, 8 and every larger NS).
+template <int LG, int S>
+__device__ __forceinline__ void stage8(float2 (&v)[8], float2* xb, const float2* __restrict__ tt, int t) {
+  constexpr int N = 1 << LG, T = N / 8, NS = 1 << (3 * S);
+  static_assert(T % 16 == 0, "eight points per thread and at least 16 threads per transform");
   const int k = t & (NS - 1);
   if constexpr (NS > 1) twiddle8(v, tt[4 * NS + k]);   // W_{8 NS}^k
   dft8(v);
-  if constexpr (8 * NS < N1) {
-    const int d0 = (t / NS) * NS * 8 + k;
+  if constexpr (8 * NS < N) {
+    float2* wp = xb + pad16((t / NS) * NS * 8 + k);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) xb[pad16(d0 + q * NS) * NB + c] = v[q];
+    for (int q = 0; q < 8; ++q) wp[q * NS + ((q * NS) >> 4)] = v[q];
     __syncthreads();
+    const float2* rp = xb + pad16(t);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = xb[pad16(t + q * T) * NB + c];
+    for (int q = 0; q < 8; ++q) v[q] = rp[q * (T + T / 16)];
     __syncthreads();   // every read done before the next stage writes
   }
 }
 
-template <int LG, int S, int NB = 1>
-__device__ __forceinline__ void stages8(float2 (&v)[8], float2* xb, const float2* __restrict__ tt, int t, int c) {
+template <int LG, int S>
+__device__ __forceinline__ void stages8(float2 (&v)[8], float2* xb, const float2* __restrict__ tt, int t) {
   if constexpr (S < LG / 3) {
-    stage8<LG, S, NB>(v, xb, tt, t, c);
-    stages8<LG, S + 1, NB>(v, xb, tt, t, c);
+    stage8<LG, S>(v, xb, tt, t);
+    stages8<LG, S + 1>(v, xb, tt, t);
   }
 }
 
@@ -575,47 +586,6 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(C2) == 8 ? 2 : 1) k3_pass1
     w = (i & 3) == 0 ? twiddle22(ta, tb, (uint32_t)((j10 + c) * k2) << shift22, sign) : cmul(w, wstep);
     zw[j10 + c + (int64_t)n1 * k2] = cmul(buf[idx], w);
   }
-}
-
-// ------------------------------------------- pass 1, FP32, in registers
-// Forward column transforms of N2 = 2^LG points (LG 8..10), NB adjacent
-// columns per CTA, N2/8 threads per column with eight points each in
-// registers (the radix-8 stages of the pass-2 kernel, the NB columns
-// interleaved in the exchange buffer); thread (c, t) loads column j1 = j10 + c
-// at rows t + q T and, after the transform, holds its bins k2 = t + q T, which
-// it writes back in place times the inter-pass twiddle W_n^{j1 k2}.  The
-// twiddles of a thread are read from the tables at k2 = t and t + 4T and
-// stepped three times by W_n^{j1 T} from each.
-template <int LG, int NB>
-__global__ void __launch_bounds__(NB * (1 << LG) / 8)
-    k3_pass1_r8(float2* __restrict__ z, int64_t n, int n1, int shift22, const float2* __restrict__ ta,
-                const float2* __restrict__ tb, const float2* __restrict__ tt) {
-  constexpr int N2 = 1 << LG, T = N2 / 8;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  float2* xb = reinterpret_cast<float2*>(smraw);
-  const int c = threadIdx.x % NB, t = threadIdx.x / NB;
-  const int j1 = blockIdx.x * NB + c;
-  float2* col = z + (int64_t)blockIdx.y * n + j1;
-  float2 v[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = col[(int64_t)n1 * (t + q * T)];
-  r8::stages8<LG, 0, NB>(v, xb, tt, t, c);
-  r8::last_stage<LG>(v, tt, t);
-  const float2 step = twiddle22(ta, tb, (uint32_t)(j1 * T) << shift22, -1);
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    float2 w = twiddle22(ta, tb, (uint32_t)(j1 * (t + 4 * h * T)) << shift22, -1);
-#pragma unroll
-    for (int q = 4 * h; q < 4 * h + 4; ++q) {
-      col[(int64_t)n1 * (t + q * T)] = r8::mul(v[q], w);
-      w = r8::mul(w, step);
-    }
-  }
-}
-
-template <int LG, int NB>
-constexpr size_t r8p1_smem() {
-  return (size_t)((1 << LG) + (1 << LG) / 16) * NB * sizeof(float2);
 }
 
 // --------------------------------------------------- pass 2, natural order
@@ -867,7 +837,7 @@ __global__ void __launch_bounds__((1 << LG) / 8)
   for (int q = 0; q < 8; ++q) v[q] = row[t + q * T];
   const float2 a = rtab[(int64_t)wk * n2 + k2];   // exp(-2 pi i frac(k2 r))
   const float2 cnv = make_float2(wcs[wk].cnf[0], wcs[wk].cnf[1]);
-  r8::stages8<LG, 0>(v, xb, tt, t, 0);
+  r8::stages8<LG, 0>(v, xb, tt, t);
   r8::last_stage<LG>(v, tt, t);
   cp_async_wait<0>();
   __syncthreads();
@@ -1040,27 +1010,10 @@ static int log2i(int v) {
   return lg;
 }
 
-// columns per CTA of the FP32 register pass 1 (8 x 8 B = 64-byte row segments)
-constexpr int kP1Cols = 8;
 
 void launch_fft_pass1(void* z, int batch, const FftPlan& p, bool fp32, int sign, const Twiddles& t,
                       cudaStream_t s) {
   if (batch <= 0) return;
-  const int lg2 = log2i(p.n2);
-  if (fp32 && sign < 0 && lg2 >= 8 && p.n1 % kP1Cols == 0) {   // forward, columns of 256..1024 points
-    dim3 g(p.n1 / kP1Cols, batch);
-    const int shift = 22 - p.log2n;
-    float2* zz = (float2*)z;
-#define CALLP1(L) k3_pass1_r8<L, kP1Cols><<<g, kP1Cols * (1 << L) / 8, r8p1_smem<L, kP1Cols>(), s>>>( \
-      zz, p.n, p.n1, shift, t.ta32, t.tb32, t.tt32)
-    switch (lg2) {
-      case 8: CALLP1(8); break;
-      case 9: CALLP1(9); break;
-      default: CALLP1(10); break;
-    }
-#undef CALLP1
-    return;
-  }
   if (fp32)
     pass1_dispatch<float2, FftCfg<float2>::kCols>((float2*)z, batch, p, sign, t.ta32, t.tb32, t.ta32, s);
   else
@@ -1184,7 +1137,6 @@ void fft_set_smem_limits() {
 #define P3(L) raise(k4_pass2_ip_r8<L, false>), raise(k4_pass2_ip_r8<L, true>)
   P3(8); P3(9); P3(10); P3(11); P3(12);
 #undef P3
-  raise(k3_pass1_r8<8, kP1Cols>), raise(k3_pass1_r8<9, kP1Cols>), raise(k3_pass1_r8<10, kP1Cols>);
 }
 
 }  // namespace emri

@@ -323,153 +323,103 @@ struct HarmStep {
   __device__ __forceinline__ void next();
 };
 template <>
-__device__ __forceinline__ void HarmStep<float>::next() {
-  const float t = cn * c1 - sn * s1;
-  sn = sn * c1 + cn * s1;
-  cn = t;
-}
-template <>
 __device__ __forceinline__ void HarmStep<double>::next() {
   const double tc = 2.0 * c1 * cn - cp, ts = 2.0 * c1 * sn - sp;
   cp = cn; sp = sn; cn = tc; sn = ts;
 }
 
-// a_n, b_n, c_n of harmonic index n at fit time st
-template <typename T>
-__device__ __forceinline__ void amps_at(const T* __restrict__ bq, int n, T st, T& an, T& bn, T& rn);
-template <>
-__device__ __forceinline__ void amps_at<double>(const double* __restrict__ bq, int n, double st, double& an,
-                                                double& bn, double& rn) {
+// a_n, b_n, c_n of harmonic index n at fit time st (FP64 layout: 9 per harmonic)
+__device__ __forceinline__ void amps_at(const double* __restrict__ bq, int n, double st, double& an, double& bn,
+                                        double& rn) {
   const double* b = bq + 9 * n;
   an = (b[2] * st + b[1]) * st + b[0];
   bn = (b[5] * st + b[4]) * st + b[3];
   rn = (b[8] * st + b[7]) * st + b[6];
 }
-template <>
-__device__ __forceinline__ void amps_at<float>(const float* __restrict__ bq, int n, float st, float& an, float& bn,
-                                               float& rn) {
-  const float4* b = reinterpret_cast<const float4*>(bq + 12 * n);   // (a0 b0 a1 b1)(a2 b2 r0 r1)(r2 -)
-  const float4 x = b[0], y = b[1], z = b[2];
-  an = (y.x * st + x.z) * st + x.x;
-  bn = (y.y * st + x.w) * st + x.y;
-  rn = (z.x * st + y.w) * st + y.z;
-}
 
-// Harmonic sums at one sample: Cs = sum_n a_n cos(n Phi), Ss = sum_n b_n
-// sin(n Phi), Rs = sum_n c_n cos(n Phi), with the amplitudes from the tile's
-// fit bq at time st in [0, 1]; cph/sph: cos/sin of the Doppler orbital phase.
-template <typename T>
-__device__ __forceinline__ void harmonic_sums(T cph, T sph, T st, const T* __restrict__ bq, int n_max, bool cheb,
-                                              T& Cs, T& Ss, T& Rs) {
-  Cs = T(0);
-  Ss = T(0);
-  Rs = T(0);
-  if constexpr (sizeof(T) == 4) {
-    // FP32: the a_n, b_n quadratics and the (C, S) sums as paired (f32x2)
-    // instructions; coefficients per harmonic (a0 b0 a1 b1)(a2 b2 r0 r1)(r2 -)
-    const float2 st2 = make_float2(st, st);
-    float2 cs = make_float2(cph, sph), acc = make_float2(0.f, 0.f);
-    float r = 0.f;
-    if (cheb) {
-      // (cos, sin)(n+1) = 2 cos(Phi) (cos, sin)(n) - (cos, sin)(n-1): one paired
-      // FMA per harmonic (used below e = 0.5, where its rounding stays at the
-      // level of the accumulation's; the rotation is kept above)
-      const float2 tc = make_float2(2.f * cph, 2.f * cph);
-      float2 prev = make_float2(1.f, 0.f);
-      for (int n = 0; n < n_max; ++n) {
-        const float4* b = reinterpret_cast<const float4*>(bq + 12 * n);
-        const float4 x = b[0], y = b[1], z = b[2];
-        const float2 ab = __ffma2_rn(__ffma2_rn(make_float2(y.x, y.y), st2, make_float2(x.z, x.w)), st2,
-                                     make_float2(x.x, x.y));
-        const float rn = (z.x * st + y.w) * st + y.z;
-        acc = __ffma2_rn(ab, cs, acc);
-        r = fmaf(rn, cs.x, r);
-        const float2 nxt = __ffma2_rn(tc, cs, make_float2(-prev.x, -prev.y));
-        prev = cs;
-        cs = nxt;
-      }
-    } else {
-      for (int n = 0; n < n_max; ++n) {
-        const float4* b = reinterpret_cast<const float4*>(bq + 12 * n);
-        const float4 x = b[0], y = b[1], z = b[2];
-        const float2 ab = __ffma2_rn(__ffma2_rn(make_float2(y.x, y.y), st2, make_float2(x.z, x.w)), st2,
-                                     make_float2(x.x, x.y));
-        const float rn = (z.x * st + y.w) * st + y.z;
-        acc = __ffma2_rn(ab, cs, acc);
-        r = fmaf(rn, cs.x, r);
-        const float cn = cs.x * cph - cs.y * sph;   // rotation by Phi
-        cs.y = cs.y * cph + cs.x * sph;
-        cs.x = cn;
-      }
-    }
-    Cs = acc.x;
-    Ss = acc.y;
-    Rs = r;
-  } else {
-    HarmStep<T> hs;
-    hs.init(cph, sph);
-    for (int n = 0; n < n_max; ++n) {
-      T an, bn, rn;
-      amps_at<T>(bq, n, st, an, bn, rn);
-      Cs += an * hs.cn;
-      Ss += bn * hs.sn;
-      Rs += rn * hs.cn;
-      hs.next();
-    }
+// Harmonic sums at one sample (FP64): Cs = sum_n a_n cos(n Phi), Ss =
+// sum_n b_n sin(n Phi), Rs = sum_n c_n cos(n Phi), with the amplitudes from
+// the tile's fit bq at time st in [0, 1]; cph/sph: cos/sin of the Doppler
+// orbital phase; (cos, sin)(n Phi) by the Chebyshev recurrence.
+__device__ __forceinline__ void harmonic_sums(double cph, double sph, double st, const double* __restrict__ bq,
+                                              int n_max, double& Cs, double& Ss, double& Rs) {
+  Cs = 0.0;
+  Ss = 0.0;
+  Rs = 0.0;
+  HarmStep<double> hs;
+  hs.init(cph, sph);
+  for (int n = 0; n < n_max; ++n) {
+    double an, bn, rn;
+    amps_at(bq, n, st, an, bn, rn);
+    Cs += an * hs.cn;
+    Ss += bn * hs.sn;
+    Rs += rn * hs.cn;
+    hs.next();
   }
 }
 
-// FP32, two samples at once (same tile fit, times stA, stB): the amplitude
-// coefficients of each harmonic are loaded once for both.
+// FP32, two samples A and B at once (same segment fit, times stA, stB): the
+// amplitude coefficients of a harmonic are loaded once for both, and every
+// quantity is carried as an (A, B) pair -- cos(n Phi), sin(n Phi), the three
+// amplitudes and the three sums -- so each step is one paired (f32x2)
+// instruction on operands that are natural register pairs.  Coefficients per
+// harmonic, each stored twice: (a0 a0 a1 a1)(a2 a2 b0 b0)(b1 b1 b2 b2)
+// (r0 r0 r1 r1)(r2 r2 - -).
+constexpr int kAmpStrideM = 20;
+
 __device__ __forceinline__ void harmonic_sums2(float cphA, float sphA, float stA, float cphB, float sphB, float stB,
                                                const float* __restrict__ bq, int n_max, bool cheb, float3& sA,
                                                float3& sB) {
-  const float2 stA2 = make_float2(stA, stA), stB2 = make_float2(stB, stB), stAB = make_float2(stA, stB);
-  float2 accA = make_float2(0.f, 0.f), accB = make_float2(0.f, 0.f);
-  float2 rAB = make_float2(0.f, 0.f);   // the c_n sums of both samples, paired
-  // harmonic n at (cos n Phi, sin n Phi) = csA, csB
-  auto harm = [&](int n, float2 csA, float2 csB) {
-    const float4* b = reinterpret_cast<const float4*>(bq + 12 * n);
-    const float4 x = b[0], y = b[1], z = b[2];
-    const float2 a2 = make_float2(y.x, y.y), a1 = make_float2(x.z, x.w), a0 = make_float2(x.x, x.y);
-    const float2 abA = __ffma2_rn(__ffma2_rn(a2, stA2, a1), stA2, a0);
-    const float2 abB = __ffma2_rn(__ffma2_rn(a2, stB2, a1), stB2, a0);
-    accA = __ffma2_rn(abA, csA, accA);
-    accB = __ffma2_rn(abB, csB, accB);
-    const float2 rn = __ffma2_rn(__ffma2_rn(make_float2(z.x, z.x), stAB, make_float2(y.w, y.w)), stAB,
-                                 make_float2(y.z, y.z));
-    rAB = __ffma2_rn(rn, make_float2(csA.x, csB.x), rAB);
+  const float2 st = make_float2(stA, stB);
+  float2 accC = make_float2(0.f, 0.f), accS = make_float2(0.f, 0.f), accR = make_float2(0.f, 0.f);
+  auto harm = [&](int n, float2 c, float2 sn) {
+    const float4* b = reinterpret_cast<const float4*>(bq + kAmpStrideM * n);
+    const float4 x0 = b[0], x1 = b[1], x2 = b[2], x3 = b[3], x4 = b[4];
+    const float2 a = __ffma2_rn(__ffma2_rn(make_float2(x1.x, x1.y), st, make_float2(x0.z, x0.w)), st,
+                                make_float2(x0.x, x0.y));
+    const float2 bb = __ffma2_rn(__ffma2_rn(make_float2(x2.z, x2.w), st, make_float2(x2.x, x2.y)), st,
+                                 make_float2(x1.z, x1.w));
+    const float2 r = __ffma2_rn(__ffma2_rn(make_float2(x4.x, x4.y), st, make_float2(x3.z, x3.w)), st,
+                                make_float2(x3.x, x3.y));
+    accC = __ffma2_rn(a, c, accC);
+    accS = __ffma2_rn(bb, sn, accS);
+    accR = __ffma2_rn(r, c, accR);
   };
-  // Two harmonics per iteration, each new (cos, sin) pair written over the
-  // one it replaces, so no register copies carry the recurrence.
-  float2 uA = make_float2(cphA, sphA), uB = make_float2(cphB, sphB);   // harmonic n
+  // Two harmonics per iteration, each new pair written over the one it
+  // replaces, so no register copies carry the recurrence.
+  const float2 c1 = make_float2(cphA, cphB), s1 = make_float2(sphA, sphB);
+  float2 cu = c1, su = s1;   // harmonic n
   int n = 0;
   if (cheb) {
-    const float2 tcA = make_float2(2.f * cphA, 2.f * cphA), tcB = make_float2(2.f * cphB, 2.f * cphB);
-    float2 vA = make_float2(1.f, 0.f), vB = make_float2(1.f, 0.f);      // harmonic n - 1
+    // (cos, sin)((n+1) Phi) = 2 cos(Phi) (cos, sin)(n Phi) - (cos, sin)((n-1) Phi)
+    // (used below e = 0.5, where its rounding stays at the level of the
+    // accumulation's; the rotation is kept above)
+    const float2 tc = make_float2(2.f * cphA, 2.f * cphB);
+    float2 cv = make_float2(1.f, 1.f), sv = make_float2(0.f, 0.f);   // harmonic n - 1
 #pragma unroll 2
     for (; n + 1 < n_max; n += 2) {
-      harm(n, uA, uB);
-      vA = __ffma2_rn(tcA, uA, make_float2(-vA.x, -vA.y));               // harmonic n + 1
-      vB = __ffma2_rn(tcB, uB, make_float2(-vB.x, -vB.y));
-      harm(n + 1, vA, vB);
-      uA = __ffma2_rn(tcA, vA, make_float2(-uA.x, -uA.y));               // harmonic n + 2
-      uB = __ffma2_rn(tcB, vB, make_float2(-uB.x, -uB.y));
+      harm(n, cu, su);
+      cv = __ffma2_rn(tc, cu, make_float2(-cv.x, -cv.y));   // harmonic n + 1
+      sv = __ffma2_rn(tc, su, make_float2(-sv.x, -sv.y));
+      harm(n + 1, cv, sv);
+      cu = __ffma2_rn(tc, cv, make_float2(-cu.x, -cu.y));   // harmonic n + 2
+      su = __ffma2_rn(tc, sv, make_float2(-su.x, -su.y));
     }
   } else {
+    // rotations by Phi: c' = c cos - s sin, s' = s cos + c sin
 #pragma unroll 2
     for (; n + 1 < n_max; n += 2) {
-      harm(n, uA, uB);
-      const float2 vA = make_float2(uA.x * cphA - uA.y * sphA, uA.y * cphA + uA.x * sphA);   // rotations by Phi
-      const float2 vB = make_float2(uB.x * cphB - uB.y * sphB, uB.y * cphB + uB.x * sphB);
-      harm(n + 1, vA, vB);
-      uA = make_float2(vA.x * cphA - vA.y * sphA, vA.y * cphA + vA.x * sphA);
-      uB = make_float2(vB.x * cphB - vB.y * sphB, vB.y * cphB + vB.x * sphB);
+      harm(n, cu, su);
+      const float2 cv = __ffma2_rn(cu, c1, __fmul2_rn(su, make_float2(-sphA, -sphB)));
+      const float2 sv = __ffma2_rn(su, c1, __fmul2_rn(cu, s1));
+      harm(n + 1, cv, sv);
+      cu = __ffma2_rn(cv, c1, __fmul2_rn(sv, make_float2(-sphA, -sphB)));
+      su = __ffma2_rn(sv, c1, __fmul2_rn(cv, s1));
     }
   }
-  if (n < n_max) harm(n, uA, uB);
-  sA = make_float3(accA.x, accA.y, rAB.x);
-  sB = make_float3(accB.x, accB.y, rAB.y);
+  if (n < n_max) harm(n, cu, su);
+  sA = make_float3(accC.x, accS.x, accR.x);
+  sB = make_float3(accC.y, accS.y, accR.y);
 }
 
 // ----------------------------------------------------------- response
@@ -545,19 +495,17 @@ __device__ __forceinline__ void response(const Geo<T>& g, T c2gt, T s2gt, T ca, 
 }
 
 // Channels at one sample (harmonic sums, then the response).
-template <typename T>
-__device__ __forceinline__ void channels(const Geo<T>& g, T cph, T sph, T c2gt, T s2gt, T ca, T sa, T A, T st,
-                                         const T* __restrict__ bq, int n_max, const T F[4], T& hI, T& hII,
-                                         bool cheb = false) {
-  T Cs, Ss, Rs;
-  harmonic_sums<T>(cph, sph, st, bq, n_max, cheb, Cs, Ss, Rs);
-  response<T>(g, c2gt, s2gt, ca, sa, A, Cs, Ss, Rs, F, hI, hII);
+__device__ __forceinline__ void channels(const Geo<double>& g, double cph, double sph, double c2gt, double s2gt,
+                                         double ca, double sa, double A, double st, const double* __restrict__ bq,
+                                         int n_max, const double F[4], double& hI, double& hII) {
+  double Cs, Ss, Rs;
+  harmonic_sums(cph, sph, st, bq, n_max, Cs, Ss, Rs);
+  response<double>(g, c2gt, s2gt, ca, sa, A, Cs, Ss, Rs, F, hI, hII);
 }
 
 // Per-harmonic amplitude coefficients in shared memory: 9 values (a, b, c
-// quadratics) at stride AmpStride<T>; FP32 pads to 12 so one harmonic is
-// three 16-byte loads, and interleaves a and b (a0 b0 a1 b1 a2 b2 r0 r1 r2)
-// for the paired evaluation.
+// quadratics) at stride AmpStride<T>; FP32 stores each twice in the layout
+// of harmonic_sums2 (five 16-byte loads per harmonic).
 template <typename T>
 struct AmpStride;
 template <>
@@ -566,7 +514,7 @@ struct AmpStride<double> {
 };
 template <>
 struct AmpStride<float> {
-  static constexpr int v = 12;
+  static constexpr int v = kAmpStrideM;
 };
 
 // Bessel amplitude fit for the tile: nodes at tile-relative sample offsets
@@ -602,14 +550,13 @@ __device__ __forceinline__ void tile_harmonics(const IV* iv, int ni, int64_t j0,
     const T f0 = bnode[(0 * 32 + n) * 3 + f], fh = bnode[(1 * 32 + n) * 3 + f], f1 = bnode[(2 * 32 + n) * 3 + f];
     const T q0 = f0, q1 = T(-3) * f0 + T(4) * fh - f1, q2 = T(2) * f0 - T(4) * fh + T(2) * f1;
     T* o = bq + AmpStride<T>::v * n;
-    if (sizeof(T) == 4 && f < 2) {      // FP32: a and b interleaved for the paired evaluation
-      o[f] = q0;
-      o[2 + f] = q1;
-      o[4 + f] = q2;
-    } else if (sizeof(T) == 4) {         // FP32: r after them
-      o[6] = q0;
-      o[7] = q1;
-      o[8] = q2;
+    if (sizeof(T) == 4) {                // FP32: quantity f, coefficient p at 6 f + 2 p and the next
+      o[6 * f + 0] = q0;
+      o[6 * f + 1] = q0;
+      o[6 * f + 2] = q1;
+      o[6 * f + 3] = q1;
+      o[6 * f + 4] = q2;
+      o[6 * f + 5] = q2;
     } else {
       o[3 * f + 0] = q0;
       o[3 * f + 1] = q1;
@@ -707,21 +654,25 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
     sincos2pi_tab(fgm, ex, s2g, c2g);
     sincos2pi_tab(fal, ex, sa, ca);
     double hI, hII;
-    channels<double>(g, cph, sph, c2g, s2g, ca, sa, A, (double)t * inv_span, bq, n_max, F, hI, hII);
+    channels(g, cph, sph, c2g, s2g, ca, sa, A, (double)t * inv_span, bq, n_max, F, hI, hII);
     out = make_double2(hI, hII);
   }
   z[(int64_t)wk * n + j] = out;
 }
 
-// Mixed kernel: one CTA per segment of kSegM = 1024 samples (four tiles of
-// 256, one per pass of the sample loop), so the Bessel amplitude fit -- a
-// quadratic in time per harmonic, from three nodes -- is made once per 1024
-// samples; over that span its error is far below FP32 resolution.
-constexpr int kSegM = 1024;
-
+// Mixed kernel: one CTA per segment of kSegM = 1024, 2048 or 4096 samples
+// (tiles of 256, two per pass of the sample loop), so the Bessel amplitude
+// fit -- a quadratic in time per harmonic, from three nodes -- is made once
+// per segment.  The eccentricity moves by ~1e-4 relative per 256 samples, and
+// the fit's error grows as the cube of the segment: ~5e-14 of the amplitudes
+// over 2048 samples, far below FP32 resolution.  Longer segments spend less
+// of the kernel in that set-up (its barrier waits); the launch takes the
+// length from the series length alone (at least 16 segments per walker).
+//
 // exact_f: exact patterns per sample (long sample intervals), dphib: the
 // LISA orbital phase step per sample [cycles] for them.  No FP64 instruction
 // runs per thread: e0 is tested once per CTA.
+template <int kSegM>
 __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
                                                           int64_t n, int exact_f, float dphib, int ks, int n_max,
                                                           float2* __restrict__ z, int unit_scale,
@@ -729,7 +680,7 @@ __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict
                                                           const double* __restrict__ lisa, const IvM* __restrict__ ivs) {
   __shared__ IvM iv[kSegM / 64];
   __shared__ float bnode[3 * 32 * 3];
-  __shared__ __align__(16) float bq[32 * 12];
+  __shared__ __align__(16) float bq[32 * kAmpStrideM];
   constexpr int kTiles = kSegM / kTile;
   static_assert(kTiles % 2 == 0, "tiles are processed in pairs");
   __shared__ float fn[kTiles][4][4];   // the four patterns at the fit nodes of each tile
@@ -837,10 +788,22 @@ void launch_wave(const Knot* knots, const WalkerC* wc, int w, int64_t n, double 
       k2_wave_f64<<<grid, kTile, 0, s>>>(kn, wc + w0, n, dt, t0, o.ks, o.n_max, (double2*)z + (int64_t)w0 * n,
                                          unit_scale ? 1 : 0, dt > kPatternFitDtMax64 ? 1 : 0, bt.c64, bt.f64, lisa);
     } else {
-      dim3 grid((unsigned)(n / kSegM), (unsigned)ww);
-      k2_wave_mixed<<<grid, kTile, 0, s>>>(kn, wc + w0, n, dt > kPatternFitDtMaxM ? 1 : 0, (float)(dt / kYear),
-                                           o.ks, o.n_max, (float2*)z + (int64_t)w0 * n, unit_scale ? 1 : 0, bt.c32,
-                                           bt.f32, lisa, (const IvM*)ivs + (int64_t)w0 * nk);
+      // segment length from the series length alone (so a walker's result
+      // does not depend on the batch it is in): at least 16 segments per
+      // walker, 1024 to 4096 samples
+      const int seg = n >= (1 << 16) ? 4096 : n >= (1 << 15) ? 2048 : 1024;
+      dim3 grid((unsigned)(n / seg), (unsigned)ww);
+      const int ef = dt > kPatternFitDtMaxM ? 1 : 0;
+      const float dpb = (float)(dt / kYear);
+      float2* zz = (float2*)z + (int64_t)w0 * n;
+      const IvM* iv = (const IvM*)ivs + (int64_t)w0 * nk;
+      const int us = unit_scale ? 1 : 0;
+      if (seg == 4096)
+        k2_wave_mixed<4096><<<grid, kTile, 0, s>>>(kn, wc + w0, n, ef, dpb, o.ks, o.n_max, zz, us, bt.c32, bt.f32, lisa, iv);
+      else if (seg == 2048)
+        k2_wave_mixed<2048><<<grid, kTile, 0, s>>>(kn, wc + w0, n, ef, dpb, o.ks, o.n_max, zz, us, bt.c32, bt.f32, lisa, iv);
+      else
+        k2_wave_mixed<1024><<<grid, kTile, 0, s>>>(kn, wc + w0, n, ef, dpb, o.ks, o.n_max, zz, us, bt.c32, bt.f32, lisa, iv);
     }
   }
 }

@@ -213,6 +213,30 @@ def test_register_radix8_rows_equal_dft(lg):
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-14
 
 
+@pytest.mark.parametrize("lg", [8, 9, 10, 11, 12])
+def test_register_stage_padded_addresses_are_affine(lg):
+    """The register kernels address the padded exchange buffer (element i at
+    i + i // 16) as pad(base) plus compile-time offsets: writes d0 + q NS at
+    pad(d0) + q NS + (q NS >> 4), reads t + q T at pad(t) + q (T + T/16),
+    for every thread and radix-8 stage that writes."""
+    n = 1 << lg
+    T = n // 8
+
+    def pad(i):
+        return i + (i >> 4)
+
+    t = np.arange(T)
+    for st in range(lg // 3):
+        ns = 8 ** st
+        if 8 * ns >= n:
+            continue
+        d0 = (t // ns) * ns * 8 + (t & (ns - 1))
+        for q in range(8):
+            assert np.array_equal(pad(d0 + q * ns), pad(d0) + q * ns + ((q * ns) >> 4)), (lg, st, q)
+    for q in range(8):
+        assert np.array_equal(pad(t + q * T), pad(t) + q * (T + T // 16))
+
+
 def test_stage_twiddle_table_layout():
     """tt[M/2 + k] = exp(-2 pi i k / M): entry i belongs to M = 2 * 2^floor(log2 i)
     and equals the 4096-point table at k * 4096 / M (same double angle)."""

@@ -393,6 +393,18 @@ __device__ __forceinline__ void row_async(void* smem, const void* gmem, int byte
     cp_async16((char*)smem + 16 * i, (const char*)gmem + 16 * (size_t)i);
 }
 
+// the same for a compile-time size and thread count (the loop unrolls)
+template <int BYTES, int NTH>
+__device__ __forceinline__ void row_async_n(void* smem, const void* gmem) {
+  static_assert(BYTES % 16 == 0, "16-byte copies");
+  constexpr int V = BYTES / 16;
+#pragma unroll
+  for (int i0 = 0; i0 < V; i0 += NTH) {
+    const int i = i0 + (int)threadIdx.x;
+    if (V % NTH == 0 || i < V) cp_async16((char*)smem + 16 * i, (const char*)gmem + 16 * (size_t)i);
+  }
+}
+
 // Copy nrow rows of rowlen contiguous complex values (global row stride gs)
 // to/from a row-major shared tile, with LPT independent 16-byte accesses per
 // thread in flight (rowlen * sizeof(C2) must be a multiple of 16).
@@ -827,9 +839,9 @@ __global__ void __launch_bounds__((1 << LG) / 8)
   const int k2 = blockIdx.x, wk = blockIdx.y;
   const int64_t base = (int64_t)k2 * N1;
   // the inner product's operands, asynchronously while the row is transformed
-  row_async(ds, dperm + base, N1 * (int)sizeof(float2));
-  row_async(ts, dtab + (int64_t)wk * N1, N1 * (int)sizeof(float2));
-  row_async(ws, wperm + base, N1 * (int)sizeof(float));
+  row_async_n<N1 * 8, T>(ds, dperm + base);
+  row_async_n<N1 * 8, T>(ts, dtab + (int64_t)wk * N1);
+  row_async_n<N1 * 4, T>(ws, wperm + base);
   cp_async_commit();
   const float2* row = y + (int64_t)wk * n + (int64_t)N1 * k2;
   float2 v[8];
@@ -852,10 +864,12 @@ __global__ void __launch_bounds__((1 << LG) / 8)
     const float wv = ws[k1];
     const float2 G = ds[k1];
     float2 P = cmul(H, ts[k1]);
-    if (2 * k1 == N1 && k2 > 0) P = cmul(P, cnv);   // the one negative bin of this column not in the table
+    // the one negative bin of this column not in the table: k1 = N1/2 = 4 T,
+    // i.e. slot 4 of thread 0
+    if (q == 4 && t == 0 && k2 > 0) P = cmul(P, cnv);
     float A2 = 1.f;
     if (FD) {
-      const bool neg = 2 * k1 > N1 || (2 * k1 == N1 && k2 > 0);
+      const bool neg = q > 4 || (q == 4 && t > 0) || (q == 4 && t == 0 && k2 > 0);
       const long long kk = (long long)k2 + (long long)n2 * k1;
       const unsigned long long ak = (unsigned long long)(neg ? n - kk : kk);
       float c, sn;

@@ -13,7 +13,7 @@
 //  * the four antenna patterns in a fixed sky polarisation basis at four
 //    nodes, fitted by a cubic in time (they depend on time only through the
 //    LISA orbital phase, a one-year period).
-// Per sample (one thread each; two per thread in the mixed kernel):
+// Per sample (one thread each; four per thread in the mixed kernel):
 //  * phases Phi_D (Doppler folded in), 2 gamma~ and alpha from the Hermite
 //    polynomials, reduced modulo one cycle, and their sin/cos;
 //  * the harmonic sum written as three running sums
@@ -358,69 +358,10 @@ __device__ __forceinline__ void harmonic_sums(double cph, double sph, double st,
   }
 }
 
-// FP32, two samples A and B at once (same segment fit, times stA, stB): the
-// amplitude coefficients of a harmonic are loaded once for both, and every
-// quantity is carried as an (A, B) pair -- cos(n Phi), sin(n Phi), the three
-// amplitudes and the three sums -- so each step is one paired (f32x2)
-// instruction on operands that are natural register pairs.  Coefficients per
-// harmonic, each stored twice: (a0 a0 a1 a1)(a2 a2 b0 b0)(b1 b1 b2 b2)
-// (r0 r0 r1 r1)(r2 r2 - -).
+// FP32 amplitude coefficients per harmonic, each stored twice so that the
+// paired (f32x2) instructions of harmonic_sums4 take natural register pairs:
+// (a0 a0 a1 a1)(a2 a2 b0 b0)(b1 b1 b2 b2)(r0 r0 r1 r1)(r2 r2 - -).
 constexpr int kAmpStrideM = 20;
-
-__device__ __forceinline__ void harmonic_sums2(float cphA, float sphA, float stA, float cphB, float sphB, float stB,
-                                               const float* __restrict__ bq, int n_max, bool cheb, float3& sA,
-                                               float3& sB) {
-  const float2 st = make_float2(stA, stB);
-  float2 accC = make_float2(0.f, 0.f), accS = make_float2(0.f, 0.f), accR = make_float2(0.f, 0.f);
-  auto harm = [&](int n, float2 c, float2 sn) {
-    const float4* b = reinterpret_cast<const float4*>(bq + kAmpStrideM * n);
-    const float4 x0 = b[0], x1 = b[1], x2 = b[2], x3 = b[3], x4 = b[4];
-    const float2 a = __ffma2_rn(__ffma2_rn(make_float2(x1.x, x1.y), st, make_float2(x0.z, x0.w)), st,
-                                make_float2(x0.x, x0.y));
-    const float2 bb = __ffma2_rn(__ffma2_rn(make_float2(x2.z, x2.w), st, make_float2(x2.x, x2.y)), st,
-                                 make_float2(x1.z, x1.w));
-    const float2 r = __ffma2_rn(__ffma2_rn(make_float2(x4.x, x4.y), st, make_float2(x3.z, x3.w)), st,
-                                make_float2(x3.x, x3.y));
-    accC = __ffma2_rn(a, c, accC);
-    accS = __ffma2_rn(bb, sn, accS);
-    accR = __ffma2_rn(r, c, accR);
-  };
-  // Two harmonics per iteration, each new pair written over the one it
-  // replaces, so no register copies carry the recurrence.
-  const float2 c1 = make_float2(cphA, cphB), s1 = make_float2(sphA, sphB);
-  float2 cu = c1, su = s1;   // harmonic n
-  int n = 0;
-  if (cheb) {
-    // (cos, sin)((n+1) Phi) = 2 cos(Phi) (cos, sin)(n Phi) - (cos, sin)((n-1) Phi)
-    // (used below e = 0.5, where its rounding stays at the level of the
-    // accumulation's; the rotation is kept above)
-    const float2 tc = make_float2(2.f * cphA, 2.f * cphB);
-    float2 cv = make_float2(1.f, 1.f), sv = make_float2(0.f, 0.f);   // harmonic n - 1
-#pragma unroll 2
-    for (; n + 1 < n_max; n += 2) {
-      harm(n, cu, su);
-      cv = __ffma2_rn(tc, cu, make_float2(-cv.x, -cv.y));   // harmonic n + 1
-      sv = __ffma2_rn(tc, su, make_float2(-sv.x, -sv.y));
-      harm(n + 1, cv, sv);
-      cu = __ffma2_rn(tc, cv, make_float2(-cu.x, -cu.y));   // harmonic n + 2
-      su = __ffma2_rn(tc, sv, make_float2(-su.x, -su.y));
-    }
-  } else {
-    // rotations by Phi: c' = c cos - s sin, s' = s cos + c sin
-#pragma unroll 2
-    for (; n + 1 < n_max; n += 2) {
-      harm(n, cu, su);
-      const float2 cv = __ffma2_rn(cu, c1, __fmul2_rn(su, make_float2(-sphA, -sphB)));
-      const float2 sv = __ffma2_rn(su, c1, __fmul2_rn(cu, s1));
-      harm(n + 1, cv, sv);
-      cu = __ffma2_rn(cv, c1, __fmul2_rn(sv, make_float2(-sphA, -sphB)));
-      su = __ffma2_rn(sv, c1, __fmul2_rn(cv, s1));
-    }
-  }
-  if (n < n_max) harm(n, cu, su);
-  sA = make_float3(accC.x, accS.x, accR.x);
-  sB = make_float3(accC.y, accS.y, accR.y);
-}
 
 // ----------------------------------------------------------- response
 // The LISA response of Sec. 2 (Eq. 2 with the Barack-Cutler antenna
@@ -503,9 +444,77 @@ __device__ __forceinline__ void channels(const Geo<double>& g, double cph, doubl
   response<double>(g, c2gt, s2gt, ca, sa, A, Cs, Ss, Rs, F, hI, hII);
 }
 
+
+// FP32, four samples at once, as two (A, B) pairs of every quantity --
+// cos(n Phi), sin(n Phi), the three amplitudes and the three sums -- so each
+// step is one paired (f32x2) instruction on operands that are natural
+// register pairs, and the coefficients of a harmonic (five 16-byte loads) are
+// loaded once for all four samples.  c1, s1: cos, sin of the Doppler orbital
+// phase; st: fit times in [0, 1]; C, S, R: sum_n a_n cos(n Phi),
+// sum_n b_n sin(n Phi), sum_n c_n cos(n Phi).
+__device__ __forceinline__ void harmonic_sums4(const float2 (&c1)[2], const float2 (&s1)[2], const float2 (&st)[2],
+                                               const float* __restrict__ bq, int n_max, bool cheb, float2 (&C)[2],
+                                               float2 (&S)[2], float2 (&R)[2]) {
+  for (int p = 0; p < 2; ++p) C[p] = S[p] = R[p] = make_float2(0.f, 0.f);
+  auto harm = [&](int n, const float2 (&c)[2], const float2 (&sn)[2]) {
+    const float4* b = reinterpret_cast<const float4*>(bq + kAmpStrideM * n);
+    const float4 x0 = b[0], x1 = b[1], x2 = b[2], x3 = b[3], x4 = b[4];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const float2 a = __ffma2_rn(__ffma2_rn(make_float2(x1.x, x1.y), st[p], make_float2(x0.z, x0.w)), st[p],
+                                  make_float2(x0.x, x0.y));
+      const float2 bb = __ffma2_rn(__ffma2_rn(make_float2(x2.z, x2.w), st[p], make_float2(x2.x, x2.y)), st[p],
+                                   make_float2(x1.z, x1.w));
+      const float2 r = __ffma2_rn(__ffma2_rn(make_float2(x4.x, x4.y), st[p], make_float2(x3.z, x3.w)), st[p],
+                                  make_float2(x3.x, x3.y));
+      C[p] = __ffma2_rn(a, c[p], C[p]);
+      S[p] = __ffma2_rn(bb, sn[p], S[p]);
+      R[p] = __ffma2_rn(r, c[p], R[p]);
+    }
+  };
+  float2 cu[2] = {c1[0], c1[1]}, su[2] = {s1[0], s1[1]};
+  int n = 0;
+  if (cheb) {
+    const float2 tc[2] = {make_float2(2.f * c1[0].x, 2.f * c1[0].y), make_float2(2.f * c1[1].x, 2.f * c1[1].y)};
+    float2 cv[2] = {make_float2(1.f, 1.f), make_float2(1.f, 1.f)}, sv[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    for (; n + 1 < n_max; n += 2) {
+      harm(n, cu, su);
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        cv[p] = __ffma2_rn(tc[p], cu[p], make_float2(-cv[p].x, -cv[p].y));
+        sv[p] = __ffma2_rn(tc[p], su[p], make_float2(-sv[p].x, -sv[p].y));
+      }
+      harm(n + 1, cv, sv);
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        cu[p] = __ffma2_rn(tc[p], cv[p], make_float2(-cu[p].x, -cu[p].y));
+        su[p] = __ffma2_rn(tc[p], sv[p], make_float2(-su[p].x, -su[p].y));
+      }
+    }
+  } else {
+    const float2 ns[2] = {make_float2(-s1[0].x, -s1[0].y), make_float2(-s1[1].x, -s1[1].y)};
+    for (; n + 1 < n_max; n += 2) {
+      harm(n, cu, su);
+      float2 cv[2], sv[2];
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        cv[p] = __ffma2_rn(cu[p], c1[p], __fmul2_rn(su[p], ns[p]));
+        sv[p] = __ffma2_rn(su[p], c1[p], __fmul2_rn(cu[p], s1[p]));
+      }
+      harm(n + 1, cv, sv);
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        cu[p] = __ffma2_rn(cv[p], c1[p], __fmul2_rn(sv[p], ns[p]));
+        su[p] = __ffma2_rn(sv[p], c1[p], __fmul2_rn(cv[p], s1[p]));
+      }
+    }
+  }
+  if (n < n_max) harm(n, cu, su);
+}
+
 // Per-harmonic amplitude coefficients in shared memory: 9 values (a, b, c
 // quadratics) at stride AmpStride<T>; FP32 stores each twice in the layout
-// of harmonic_sums2 (five 16-byte loads per harmonic).
+// of harmonic_sums4 (five 16-byte loads per harmonic).
 template <typename T>
 struct AmpStride;
 template <>
@@ -628,8 +637,8 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
   const int64_t j = j0 + t;
   double2 out = make_double2(0.0, 0.0);
   if (j < C.j_plunge) {
-    const int ki = ks >= kTile ? 0 : t / ks;
-    const double s = (double)(j - (kfirst + ki) * ks) * (1.0 / (double)ks);   // ks: a power of two
+    const int ki = ks >= kTile ? 0 : t >> (__ffs(ks) - 1);   // ks: a power of two
+    const double s = (double)(j - (kfirst + ki) * ks) * (1.0 / (double)ks);
     const IvD& v = iv[ki];
     // phases in cycles over the knot interval (|f| < 2^20: the table index
     // wraps them, no reduction to one cycle is needed)
@@ -661,7 +670,9 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
 }
 
 // Mixed kernel: one CTA per segment of kSegM = 1024, 2048 or 4096 samples
-// (tiles of 256, two per pass of the sample loop), so the Bessel amplitude
+// (tiles of 256, four per pass of the sample loop: each thread evaluates the
+// samples at its offset in four tiles at once, three CTAs per SM at up to 85
+// registers), so the Bessel amplitude
 // fit -- a quadratic in time per harmonic, from three nodes -- is made once
 // per segment.  The eccentricity moves by ~1e-4 relative per 256 samples, and
 // the fit's error grows as the cube of the segment: ~5e-14 of the amplitudes
@@ -673,7 +684,7 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
 // LISA orbital phase step per sample [cycles] for them.  No FP64 instruction
 // runs per thread: e0 is tested once per CTA.
 template <int kSegM>
-__global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
+__global__ void __launch_bounds__(kTile, 3) k2_wave_mixed(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
                                                           int64_t n, int exact_f, float dphib, int ks, int n_max,
                                                           float2* __restrict__ z, int unit_scale,
                                                           const float* __restrict__ bc, const float* __restrict__ ifact,
@@ -682,7 +693,7 @@ __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict
   __shared__ float bnode[3 * 32 * 3];
   __shared__ __align__(16) float bq[32 * kAmpStrideM];
   constexpr int kTiles = kSegM / kTile;
-  static_assert(kTiles % 2 == 0, "tiles are processed in pairs");
+  static_assert(kTiles % 4 == 0, "tiles are processed in fours");
   __shared__ float fn[kTiles][4][4];   // the four patterns at the fit nodes of each tile
   __shared__ float fq[kTiles][4][4];   // their cubics in (t mod 256) / 256
   __shared__ float cs0[kTiles][2];     // cos, sin phibar at each tile's start
@@ -724,19 +735,27 @@ __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict
   __syncthreads();
   const float inv_span = 1.f / (float)span;
   const float inv_ks = 1.f / (float)ks;
+  const int lks = __ffs(ks) - 1;   // ks is a power of two: the interval index by a shift
   constexpr float kTwoPiF = 6.283185307179586f;
-  // per-sample inputs of the response and of the harmonic sums
-  auto inputs = [&](int r, float& cph, float& sph, float& c2g, float& s2g, float& ca, float& sa, float& A) {
-    const int ki = ks >= kSegM ? 0 : r / ks;
+  // per-sample inputs: the orbital phase (for the harmonic sums) first, the
+  // response's angles and amplitude after the sums (fewer registers live
+  // across the harmonic loop)
+  auto orb = [&](int r, float& cph, float& sph) {
+    const int ki = ks >= kSegM ? 0 : r >> lks;
     const int tau = r - ki * ks;
     const float s = (float)tau * inv_ks;
     const IvM& v = iv[ki];
     const float fph = phase_fx(v.ph_base, v.ph_inc, v.ph_c, tau, s);
+    __sincosf(kTwoPiF * fph, &sph, &cph);
+  };
+  auto resp_in = [&](int r, float& c2g, float& s2g, float& ca, float& sa, float& A) {
+    const int ki = ks >= kSegM ? 0 : r >> lks;
+    const int tau = r - ki * ks;
+    const float s = (float)tau * inv_ks;
+    const IvM& v = iv[ki];
     const float fgm = phase_fx(v.gm_base, v.gm_inc, v.gm_c, tau, s);   // 2 gamma~
     const float fal = phase_fx(v.al_base, v.al_inc, v.al_c, tau, s);
     A = poly3<float>(v.am, s);
-    // hardware sin/cos of the reduced angles (|x| <= pi, absolute error ~5e-7)
-    __sincosf(kTwoPiF * fph, &sph, &cph);
     __sincosf(kTwoPiF * fgm, &s2g, &c2g);
     __sincosf(kTwoPiF * fal, &sa, &ca);
   };
@@ -752,25 +771,36 @@ __global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict
       antenna_fixed<float>(g, cs0[tt][0] * cd - cs0[tt][1] * sd, cs0[tt][1] * cd + cs0[tt][0] * sd, scale, F);
     }
   };
-  // two samples per thread (tiles tt and tt+1): the amplitude coefficients
-  // of each harmonic are loaded once for both
+  // four samples per thread (tiles tt..tt+3, offset t): the amplitude
+  // coefficients of each harmonic are loaded once for all four
 #pragma unroll 1
-  for (int tt = 0; tt < kTiles; tt += 2) {
-    const int rA = tt * kTile + t, rB = rA + kTile;   // offsets in the segment
-    float cphA, sphA, c2gA, s2gA, caA, saA, AA;
-    float cphB, sphB, c2gB, s2gB, caB, saB, AB;
-    inputs(rA, cphA, sphA, c2gA, s2gA, caA, saA, AA);
-    inputs(rB, cphB, sphB, c2gB, s2gB, caB, saB, AB);
-    float3 hsA, hsB;
-    harmonic_sums2(cphA, sphA, (float)rA * inv_span, cphB, sphB, (float)rB * inv_span, bq, n_max, cheb, hsA, hsB);
-    float hIA, hIIA, hIB, hIIB, F[4];
-    patterns(tt, F);
-    response<float>(g, c2gA, s2gA, caA, saA, AA, hsA.x, hsA.y, hsA.z, F, hIA, hIIA);
-    patterns(tt + 1, F);
-    response<float>(g, c2gB, s2gB, caB, saB, AB, hsB.x, hsB.y, hsB.z, F, hIB, hIIB);
-    const int64_t jA = j0 + rA, jB = j0 + rB;
-    z[(int64_t)wk * n + jA] = jA < jplunge ? make_float2(hIA, hIIA) : make_float2(0.f, 0.f);
-    z[(int64_t)wk * n + jB] = jB < jplunge ? make_float2(hIB, hIIB) : make_float2(0.f, 0.f);
+  for (int tt = 0; tt < kTiles; tt += 4) {
+    int r[4];
+    float2 c1[2], s1[2], st[2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) r[i] = (tt + i) * kTile + t;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      float ca_, sa_, cb_, sb_;
+      orb(r[2 * p], ca_, sa_);
+      orb(r[2 * p + 1], cb_, sb_);
+      c1[p] = make_float2(ca_, cb_);
+      s1[p] = make_float2(sa_, sb_);
+      st[p] = make_float2((float)r[2 * p] * inv_span, (float)r[2 * p + 1] * inv_span);
+    }
+    float2 Cs[2], Ss[2], Rs[2];
+    harmonic_sums4(c1, s1, st, bq, n_max, cheb, Cs, Ss, Rs);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int p = i >> 1;
+      const float cs = (i & 1) ? Cs[p].y : Cs[p].x, ss = (i & 1) ? Ss[p].y : Ss[p].x, rs = (i & 1) ? Rs[p].y : Rs[p].x;
+      float c2g, s2g, ca, sa, A, F[4], hI, hII;
+      resp_in(r[i], c2g, s2g, ca, sa, A);
+      patterns(tt + i, F);
+      response<float>(g, c2g, s2g, ca, sa, A, cs, ss, rs, F, hI, hII);
+      const int64_t j = j0 + r[i];
+      z[(int64_t)wk * n + j] = j < jplunge ? make_float2(hI, hII) : make_float2(0.f, 0.f);
+    }
   }
 }
 

@@ -359,14 +359,25 @@ int emri_stretch_step(emri_ctx* ctx, const emri_dataset* ds, double* theta_dev, 
  * for them: theta_dev[EMRI_NPARAM][W] and lnp_dev[W] hold the whole ensemble
  * (the other half must be current on this device), and only the block's
  * columns, lnp and accepted entries are written; u_dev[3][W] as for
- * emri_stretch_step.  Running half 0 over blocks that cover it, making the
+ * emri_stretch_step; fd (nullable) as in emri_stretch_step_fd.  Running
+ * half 0 over blocks that cover it, making the
  * updated half 0 current everywhere, then half 1 likewise, gives the same
  * ensemble bit for bit as one emri_stretch_step.  Errors as
  * emri_stretch_step, plus EMRI_EINVAL for a block outside the half; an empty
  * block is a no-op. */
 int emri_stretch_half(emri_ctx* ctx, const emri_dataset* ds, double* theta_dev, double* lnp_dev, int w, int half,
-                      int k0, int k1, const emri_opts* opts, const emri_stretch_cfg* cfg, const double* u_dev,
-                      int32_t* accepted_dev, void* stream);
+                      int k0, int k1, const emri_opts* opts, const emri_stretch_cfg* cfg, const emri_fdprop* fd,
+                      const double* u_dev, int32_t* accepted_dev, void* stream);
+
+/* emri_stretch_step with the frequency-dependent propagation of
+ * emri_loglike_batch_fd (paper Sec. 2, alpha_M(f), alpha_T(f)) held fixed per
+ * walker: fd->coef_dev [q_m + q_t][W] (device, caller-owned), and the
+ * proposal of walker k is evaluated with walker k's coefficients (the
+ * coefficients are not moved).  emri_stretch_half takes the same model
+ * through its nullable fd argument. */
+int emri_stretch_step_fd(emri_ctx* ctx, const emri_dataset* ds, double* theta_dev, double* lnp_dev, int w,
+                         const emri_opts* opts, const emri_stretch_cfg* cfg, const emri_fdprop* fd,
+                         const double* u_dev, int32_t* accepted_dev, void* stream);
 
 /* ------------------------------------------------------------- serving
  * A continuous-batching request loop on the context's device (the serving

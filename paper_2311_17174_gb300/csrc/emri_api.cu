@@ -807,7 +807,7 @@ extern "C" int emri_loglike_batch_fd(emri_ctx* ctx, const emri_dataset* ds, cons
   FdW* fdw = cv.take<FdW>(w);
   LoglikeBufs b;
   loglike_layout(ds->plan, o, w, wave, &cv, &b);
-  launch_fdprop(theta, w, w, ds->n, ds->dt, o, fd->q_m, fd->q_t, fd->f_star, fd->coef_dev, fdw, s);
+  launch_fdprop(theta, w, w, ds->n, ds->dt, o, fd->q_m, fd->q_t, fd->f_star, fd->coef_dev, w, fdw, s);
   int64_t nl = 1;
   int64_t nr = 0;
   rc = run_loglike(ctx, ds, theta, w, w, o, wave, b, lnl, dh, hh, status, s, &nr, fdw);

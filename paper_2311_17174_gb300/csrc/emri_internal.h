@@ -66,9 +66,9 @@ void launch_prologue(const double* theta, int64_t ld, int w, int64_t n, double d
 // tab[w][n1] = exp(-2 pi i frac(n2 k1 r)), rtab[w][n2] = exp(-2 pi i frac(k2 r))
 void launch_delay_table(const WalkerC* wc, int w, int n1, int n2, bool fp32, void* tab, void* rtab, cudaStream_t s);
 void launch_prologue_export(const WalkerC* wc, int w, double* out, cudaStream_t s);
-// frequency-dependent propagation records fd[w] from theta and coef[qm+qt][w]
+// frequency-dependent propagation records fd[w] from theta and coef[qm+qt][ldc]
 void launch_fdprop(const double* theta, int64_t ld, int w, int64_t n, double dt, const OptsN& o, int qm, int qt,
-                   double fstar, const double* coef, FdW* fd, cudaStream_t s);
+                   double fstar, const double* coef, int64_t ldc, FdW* fd, cudaStream_t s);
 
 // orbit: knots[w][nk+1], nk = n / ks
 // mcpi_tab: Chebyshev-Picard tables (qn then qk), required

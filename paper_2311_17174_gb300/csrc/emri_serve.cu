@@ -201,7 +201,8 @@ static void launch_request(Server* sv, Slot& sl, const std::shared_ptr<Request>&
   if (r->fd) {
     fdw = cv.take<FdW>(r->w);
     cv.off = round256(cv.off);
-    launch_fdprop(d_theta, r->w, r->w, r->ds->n, r->ds->dt, r->o, r->qm, r->qt, r->fstar, d_coef, fdw, sl.stream);
+    launch_fdprop(d_theta, r->w, r->w, r->ds->n, r->ds->dt, r->o, r->qm, r->qt, r->fstar, d_coef, r->w, fdw,
+                  sl.stream);
     nl += 1;
   }
   LoglikeBufs b;
@@ -665,7 +666,7 @@ extern "C" int emri_loglike_multi(emri_ctx* ctx, const emri_work* items, int n_i
             fdw = cv.take<FdW>(items[i].w);
             cv.off = (cv.off + 255) & ~(size_t)255;
             launch_fdprop(items[i].theta_dev, items[i].w, items[i].w, items[i].ds->n, items[i].ds->dt, on[i],
-                          fd->q_m, fd->q_t, fd->f_star, fd->coef_dev, fdw, br);
+                          fd->q_m, fd->q_t, fd->f_star, fd->coef_dev, items[i].w, fdw, br);
             m->launches += 1;
           }
           LoglikeBufs b;

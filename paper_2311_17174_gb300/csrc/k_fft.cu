@@ -454,7 +454,8 @@ struct FftCfg<float2> {
 // the previous stage wrote (element i at i + i/16, which keeps the stride-8
 // writes of the first stage free of bank conflicts), and the last stage
 // leaves the bins k1 = t + q T in registers, where the inner products take
-// them.  Complex arithmetic runs as paired FP32 instructions (f32x2).  The
+// them (a thread's bins in FP32, the row's threads in TwoSum-compensated
+// FP32 pairs).  Complex additions run as paired FP32 instructions (f32x2).  The
 // stage twiddles W_M^k (M = R NS) come from the stage table tt, W^2..W^7 by
 // complex products.
 namespace r8 {
@@ -881,10 +882,11 @@ __global__ void __launch_bounds__((1 << LG) / 8)
     zi += G.x * P.y + G.y * P.x;
     shh += wv * (H.x * H.x + H.y * H.y) * A2;
   }
-  const float sdh = a.x * zr - a.y * zi;
+  // fixed-shape reduction in TwoSum-compensated FP32 pairs: warp xor tree,
+  // then warp 0 over the warp partials
   AccF acc;
   acc.init();
-  acc.add(sdh, shh);
+  acc.add(a.x * zr - a.y * zi, shh);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) acc.shfl_merge(off);
   const int lane = t & 31, wid = t >> 5;

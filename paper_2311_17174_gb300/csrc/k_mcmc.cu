@@ -14,6 +14,8 @@
 // The proposal and the acceptance margin are evaluated with explicitly
 // rounded operations (no fused multiply-add), in the same order as the plain
 // definition, so that a proposal is bit-identical to the textbook formula.
+#include <math.h>
+
 #include <algorithm>
 
 #include "../../include/emri.h"
@@ -118,7 +120,7 @@ int stretch_args(const emri_stretch_cfg* cfg, StretchArgs* sa) {
 // half 1 = [W/2, W)).
 int stretch_run(emri_ctx* ctx, const emri_dataset* ds, double* theta, double* lnp, int w, const emri_opts* opts,
                 const StretchArgs& sa, const double* u, int32_t* accepted, cudaStream_t s, int first, int last,
-                int k0, int k1) {
+                int k0, int k1, const emri_fdprop* fd) {
   OptsN o;
   int rc = normalize_opts(opts, ds->n, &o);
   if (rc) return rc;
@@ -148,6 +150,7 @@ int stretch_run(emri_ctx* ctx, const emri_dataset* ds, double* theta, double* ln
   probe.take<double>(mmax);
   probe.take<double>(mmax);
   probe.take<uint32_t>(mmax);
+  if (fd) probe.take<FdW>(mmax);
   probe.off = (probe.off + 255) & ~(size_t)255;
   const size_t need = probe.off + loglike_layout(ds->plan, o, mmax, wave, nullptr, nullptr);
   if ((rc = ctx->ws.reserve(ctx, need, s))) return rc;
@@ -157,6 +160,7 @@ int stretch_run(emri_ctx* ctx, const emri_dataset* ds, double* theta, double* ln
   double* zs = cv.take<double>(mmax);
   double* lly = cv.take<double>(mmax);
   uint32_t* sty = cv.take<uint32_t>(mmax);
+  FdW* fdw = fd ? cv.take<FdW>(mmax) : nullptr;
   LoglikeBufs b;
   loglike_layout(ds->plan, o, mmax, wave, &cv, &b);
   int64_t nl = 0;
@@ -167,7 +171,11 @@ int stretch_run(emri_ctx* ctx, const emri_dataset* ds, double* theta, double* ln
     if (m == 0 || nc == 0) continue;
     const int tb = 128, gb = (m + tb - 1) / tb;
     k_stretch_propose<<<gb, tb, 0, s>>>(theta, w, a0, m, o0, nc, u, sa, y, zs);
-    rc = run_loglike(ctx, ds, y, m, m, o, std::min(wave, m), b, lly, nullptr, nullptr, sty, s, &nl);
+    if (fd) {   // each proposal with its walker's propagation coefficients
+      launch_fdprop(y, m, m, ds->n, ds->dt, o, fd->q_m, fd->q_t, fd->f_star, fd->coef_dev + a0, w, fdw, s);
+      nl += 1;
+    }
+    rc = run_loglike(ctx, ds, y, m, m, o, std::min(wave, m), b, lly, nullptr, nullptr, sty, s, &nl, fdw);
     k_stretch_accept<<<gb, tb, 0, s>>>(theta, lnp, w, a0, m, y, zs, lly, sty, u, sa, accepted);
     nl += 2;
   }
@@ -193,12 +201,37 @@ extern "C" int emri_stretch_step(emri_ctx* ctx, const emri_dataset* ds, double* 
   StretchArgs sa;
   int rc = stretch_args(cfg, &sa);
   if (rc) return rc;
-  return stretch_run(ctx, ds, theta, lnp, w, opts, sa, u, accepted, (cudaStream_t)stream, 0, 1, 0, w);
+  return stretch_run(ctx, ds, theta, lnp, w, opts, sa, u, accepted, (cudaStream_t)stream, 0, 1, 0, w, nullptr);
+}
+
+static int check_fd(const emri_fdprop* fd) {
+  if (!fd) return EMRI_OK;
+  if (fd->q_m < 0 || fd->q_m > 3 || fd->q_t < 0 || fd->q_t > 3)
+    return set_err(EMRI_EINVAL, "q_m and q_t must be in [0, 3]");
+  if (!(fd->f_star > 0) || !isfinite(fd->f_star)) return set_err(EMRI_EINVAL, "f_star must be positive and finite");
+  if (fd->q_m + fd->q_t > 0 && !fd->coef_dev) return set_err(EMRI_EINVAL, "NULL propagation coefficients");
+  return EMRI_OK;
+}
+
+extern "C" int emri_stretch_step_fd(emri_ctx* ctx, const emri_dataset* ds, double* theta, double* lnp, int w,
+                                    const emri_opts* opts, const emri_stretch_cfg* cfg, const emri_fdprop* fd,
+                                    const double* u, int32_t* accepted, void* stream) {
+  if (!ctx || !ds || !cfg || !fd) return set_err(EMRI_EINVAL, "NULL context, dataset, configuration or model");
+  if (ds->ctx != ctx) return set_err(EMRI_EINVAL, "dataset belongs to another context");
+  if (w < 0) return set_err(EMRI_EINVAL, "w must be >= 0");
+  if (w == 0) return EMRI_OK;
+  if (w < 2) return set_err(EMRI_EINVAL, "the stretch move needs at least 2 walkers");
+  if (!theta || !lnp || !u) return set_err(EMRI_EINVAL, "NULL pointer");
+  int rc = check_fd(fd);
+  if (rc) return rc;
+  StretchArgs sa;
+  if ((rc = stretch_args(cfg, &sa))) return rc;
+  return stretch_run(ctx, ds, theta, lnp, w, opts, sa, u, accepted, (cudaStream_t)stream, 0, 1, 0, w, fd);
 }
 
 extern "C" int emri_stretch_half(emri_ctx* ctx, const emri_dataset* ds, double* theta, double* lnp, int w, int half,
-                                 int k0, int k1, const emri_opts* opts, const emri_stretch_cfg* cfg, const double* u,
-                                 int32_t* accepted, void* stream) {
+                                 int k0, int k1, const emri_opts* opts, const emri_stretch_cfg* cfg,
+                                 const emri_fdprop* fd, const double* u, int32_t* accepted, void* stream) {
   if (!ctx || !ds || !cfg) return set_err(EMRI_EINVAL, "NULL context, dataset or configuration");
   if (ds->ctx != ctx) return set_err(EMRI_EINVAL, "dataset belongs to another context");
   if (w < 2) return set_err(EMRI_EINVAL, "the stretch move needs at least 2 walkers");
@@ -208,8 +241,9 @@ extern "C" int emri_stretch_half(emri_ctx* ctx, const emri_dataset* ds, double* 
     return set_err(EMRI_EINVAL, "walker block [%d, %d) is not inside half %d = [%d, %d)", k0, k1, half, lo, hi);
   if (k0 == k1) return EMRI_OK;
   if (!theta || !lnp || !u) return set_err(EMRI_EINVAL, "NULL pointer");
-  StretchArgs sa;
-  int rc = stretch_args(cfg, &sa);
+  int rc = check_fd(fd);
   if (rc) return rc;
-  return stretch_run(ctx, ds, theta, lnp, w, opts, sa, u, accepted, (cudaStream_t)stream, half, half, k0, k1);
+  StretchArgs sa;
+  if ((rc = stretch_args(cfg, &sa))) return rc;
+  return stretch_run(ctx, ds, theta, lnp, w, opts, sa, u, accepted, (cudaStream_t)stream, half, half, k0, k1, fd);
 }

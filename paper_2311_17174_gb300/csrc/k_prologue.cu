@@ -266,7 +266,7 @@ __device__ void dd_to_fx128(dd x, unsigned long long& hi, unsigned long long& lo
 // beta_m = -(t_LB/2) b_m df^(m+1) / f_*^m (cycles per |k|^(m+1)), reduced mod 1
 // in dd before the conversion to fixed point.
 __global__ void k0_fdprop(const double* __restrict__ theta, int64_t ld, int w, int64_t n, double dt, double omega_m,
-                          double h0, int qm, int qt, double fstar, const double* __restrict__ coef,
+                          double h0, int qm, int qt, double fstar, const double* __restrict__ coef, int64_t ldc,
                           FdW* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= w) return;
@@ -279,14 +279,14 @@ __global__ void k0_fdprop(const double* __restrict__ theta, int64_t ld, int w, i
   const dd tobs = two_prod((double)n, dt);
   const dd df = dd_div(dd_make(1.0), tobs);
   f.xs = dd_div(df, dd_make(fstar)).hi;
-  for (int m = 0; m < qm; ++m) f.a[m] = coef[(int64_t)m * w + i];
+  for (int m = 0; m < qm; ++m) f.a[m] = coef[(int64_t)m * ldc + i];
   if (qt > 0) {
     const dd tlb = z > 0.0 ? lookback_dd(z, omega_m, h0) : dd_make(0.0);
     const dd q = dd_div(df, dd_make(fstar));
     dd base = dd_mul(dd_mul_d(tlb, -0.5), df);   // -(t_LB/2) df
     for (int m = 0; m < qt; ++m) {
       base = dd_mul(base, q);                     // -(t_LB/2) df (df/f_*)^(m+1)
-      const dd beta = dd_frac(dd_mul_d(base, coef[(int64_t)(qm + m) * w + i]));
+      const dd beta = dd_frac(dd_mul_d(base, coef[(int64_t)(qm + m) * ldc + i]));
       dd_to_fx128(beta, f.bhi[m], f.blo[m]);
     }
   }
@@ -294,9 +294,9 @@ __global__ void k0_fdprop(const double* __restrict__ theta, int64_t ld, int w, i
 }
 
 void launch_fdprop(const double* theta, int64_t ld, int w, int64_t n, double dt, const OptsN& o, int qm, int qt,
-                   double fstar, const double* coef, FdW* fd, cudaStream_t s) {
+                   double fstar, const double* coef, int64_t ldc, FdW* fd, cudaStream_t s) {
   if (w <= 0) return;
-  k0_fdprop<<<(w + 127) / 128, 128, 0, s>>>(theta, ld, w, n, dt, o.omega_m, o.h0, qm, qt, fstar, coef, fd);
+  k0_fdprop<<<(w + 127) / 128, 128, 0, s>>>(theta, ld, w, n, dt, o.omega_m, o.h0, qm, qt, fstar, coef, ldc, fd);
 }
 
 }  // namespace emri

@@ -107,8 +107,11 @@ _SIGS = {
     "emri_stretch_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(Opts),
                                     C.POINTER(StretchCfg), C.c_void_p, C.c_void_p, C.c_void_p]),
     "emri_stretch_half": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
-                                    C.c_int, C.POINTER(Opts), C.POINTER(StretchCfg), C.c_void_p, C.c_void_p,
-                                    C.c_void_p]),
+                                    C.c_int, C.POINTER(Opts), C.POINTER(StretchCfg), C.POINTER(FdProp), C.c_void_p,
+                                    C.c_void_p, C.c_void_p]),
+    "emri_stretch_step_fd": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(Opts),
+                                       C.POINTER(StretchCfg), C.POINTER(FdProp), C.c_void_p, C.c_void_p,
+                                       C.c_void_p]),
     "emri_autotune": (C.c_int, [C.c_void_p, C.POINTER(Grid), C.c_int, C.c_int, C.c_char_p,
                                 C.POINTER(C.c_int64)]),
 }
@@ -303,12 +306,23 @@ class Context:
                                           _ptr(u), _ptr(accepted), _stream(stream)))
 
     def stretch_half(self, ds: "Dataset", theta, lnp, o: Opts, cfg: StretchCfg, u, half: int, k0: int, k1: int,
-                     accepted=None, stream=None):
+                     accepted=None, stream=None, fd=None):
         """emri_stretch_half: walkers k0..k1-1 of half ``half`` of the ensemble
-        theta [16][W] / lnp [W] (device tensors holding the whole ensemble)."""
+        theta [16][W] / lnp [W] (device tensors holding the whole ensemble);
+        fd = (q_m, q_t, f_star, coef device tensor [q_m + q_t][W]) or None."""
         w = int(theta.shape[1])
+        fp = None if fd is None else C.byref(FdProp(int(fd[0]), int(fd[1]), float(fd[2]), _ptr(fd[3])))
         _check(self.lib.emri_stretch_half(self.h, ds.h, _ptr(theta), _ptr(lnp), w, int(half), int(k0), int(k1),
-                                          C.byref(o), C.byref(cfg), _ptr(u), _ptr(accepted), _stream(stream)))
+                                          C.byref(o), C.byref(cfg), fp, _ptr(u), _ptr(accepted), _stream(stream)))
+
+    def stretch_step_fd(self, ds: "Dataset", theta, lnp, o: Opts, cfg: StretchCfg, q_m: int, q_t: int,
+                        f_star: float, coef, u, accepted=None, stream=None):
+        """emri_stretch_step_fd: the ensemble step with a fixed frequency-dependent
+        propagation model per walker (coef device tensor [q_m + q_t][W])."""
+        w = int(theta.shape[1])
+        fd = FdProp(int(q_m), int(q_t), float(f_star), _ptr(coef))
+        _check(self.lib.emri_stretch_step_fd(self.h, ds.h, _ptr(theta), _ptr(lnp), w, C.byref(o), C.byref(cfg),
+                                             C.byref(fd), _ptr(u), _ptr(accepted), _stream(stream)))
 
     # ------------------------------------------------------------ serving
     def serve_start(self, slots: int = 4, queue_capacity: int = 1024, budget_bytes: int = 0):

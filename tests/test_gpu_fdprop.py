@@ -108,3 +108,50 @@ def test_fdprop_in_multi_chain_graph_and_serving():
         ds.close()
     finally:
         ctx.close()
+
+
+def test_fdprop_in_the_ensemble_step():
+    """emri_stretch_step_fd with a fixed model per walker: after a step, the
+    stored log-posterior of every walker (moved or not) is emri_loglike_batch_fd
+    at its new position with its own coefficients, bit for bit; the step
+    moves walkers, and the model changes its outcome."""
+    from paper_2311_17174_gb300 import emri
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ctx = emri.Context(0)
+    try:
+        n, dt, nm, w = 1 << 14, 15.0, 6, 24
+        inj = I.draw_sources(101, 1, n)[0]
+        psd = I.psd_bc04(n, dt)
+        d, inj2, _, _ = O.injection_data(inj, n, dt, psd, 102, O.Opts(n_max=nm), snr=40.0)
+        ds = ctx.dataset(emri.grid(n, dt), d, psd, 1e-4, 1.0 / (2 * dt))
+        th = I.scatter_walkers(103, inj2, w)
+        g = np.random.default_rng(104)
+        qm, qt, fstar = 1, 1, 3e-3
+        coef = torch.tensor(np.concatenate([g.normal(0, 0.3, (1, w)), g.normal(0, 0.05, (1, w))]), device="cuda:0")
+        free = [I.I_M, I.I_MU, I.I_SPIN, I.I_XI0]
+        lo, hi = np.full(16, -np.inf), np.full(16, np.inf)
+        for p in free:
+            lo[p], hi[p] = inj2[p] * (1 - 1e-3), inj2[p] * (1 + 1e-3)
+        lo[I.I_SPIN], hi[I.I_SPIN] = 0.0, 1.0
+        cfg = emri.stretch_cfg(free, lo, hi)
+        o = emri.opts(precision=emri.FP64, n_max=nm)
+        u = torch.tensor(g.random((3, w)), device="cuda:0")
+        theta = torch.tensor(th.T.copy(), device="cuda:0")
+        lnp = torch.zeros(w, dtype=torch.float64, device="cuda:0")
+        ctx.loglike_batch_fd(ds, theta, o, qm, qt, fstar, coef, lnp)
+        theta_b, lnp_b = theta.clone(), torch.zeros(w, dtype=torch.float64, device="cuda:0")
+        ctx.loglike_batch(ds, theta_b, o, lnp_b)
+        acc = torch.zeros(w, dtype=torch.int32, device="cuda:0")
+        ctx.stretch_step_fd(ds, theta, lnp, o, cfg, qm, qt, fstar, coef, u, acc)
+        acc_b = torch.zeros(w, dtype=torch.int32, device="cuda:0")
+        ctx.stretch_step(ds, theta_b, lnp_b, o, cfg, u, acc_b)
+        again = torch.zeros(w, dtype=torch.float64, device="cuda:0")
+        ctx.loglike_batch_fd(ds, theta, o, qm, qt, fstar, coef, again)
+        torch.cuda.synchronize()
+        assert int(acc.sum()) > 0
+        assert torch.equal(again, lnp)
+        assert not torch.equal(lnp, lnp_b)
+        ds.close()
+    finally:
+        ctx.close()

@@ -522,7 +522,7 @@ def mixed_roofline(kt, walkers: int, n: int, n_max: int, steps: int):
         out["k2_wave_mixed"] = {"bound": "alu", "achieved": tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                                 "frac": tf / FP32_PEAK_TFLOPS, "ms_per_step": ms / steps,
                                 "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x 2.07 GHz"}
-    for name, key, per_sample in (("k3_pass1<float2>", "fft_pass1", 16.0), ("k4_pass2_ip<float2>", "fft_pass2_ip", 8.0)):
+    for name, key, per_sample in (("k3_pass1<float2>", "fft_pass1", 16.0), ("k4_pass2_ip_r8", "fft_pass2_ip", 8.0)):
         if kt.get(key, (0, 0))[1]:
             ms = kt[key][0]
             gbs = per_sample * samples / (ms / 1e3) / 1e9

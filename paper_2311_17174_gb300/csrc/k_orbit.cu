@@ -257,6 +257,12 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi(WalkerC* __res
     jp = 0;
     st |= ST_PLUNGE;
     last = 0;
+  } else {
+    // knot 0 from the start state; each segment then writes its knots 1..K
+    // (knot K, its end state, is the next segment's first)
+    double r[5];
+    ak_rhs_v(s, y.v_hi, y.e_hi, r[0], r[1], r[2], r[3], r[4]);
+    if (lane == 0) write_knot(kn, y, r, c, t0, doppler);
   }
   const int64_t nseg = n / seg;
   bool warm = false;
@@ -313,10 +319,10 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi(WalkerC* __res
 #pragma unroll
       for (int q = 0; q < 5; ++q) f[q * 32 + lane] = r[q];
       __syncwarp();
-      // knots q = 0..K-1 of this segment (q = 0 is the start), and the end
-      // state (q = K), which every lane takes as the next segment's start
+      // knots q = 1..K of this segment (the start, q = 0, is already
+      // written); the end state (q = K) is every lane's next start
       bool anybad = false;
-      for (int q0 = 0; q0 <= K; q0 += 32) {
+      for (int q0 = 1; q0 <= K; q0 += 32) {
         const int q = q0 + lane;
         bool bad = false;
         OrbState yk = y;
@@ -333,8 +339,8 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi(WalkerC* __res
           comp_add(yk.p_hi, yk.p_lo, H * sm[2]);
           comp_add(yk.g_hi, yk.g_lo, H * sm[3]);
           comp_add(yk.a_hi, yk.a_lo, H * sm[4]);
-          bad = q > 0 && (!state_finite(yk) || plunged(yk.v_hi, yk.e_hi));
-          if (q < K && !bad) {
+          bad = !state_finite(yk) || plunged(yk.v_hi, yk.e_hi);
+          if (!bad) {
             double rk[5];
             ak_rhs_v(s, yk.v_hi, yk.e_hi, rk[0], rk[1], rk[2], rk[3], rk[4]);
             write_knot(kn + kbase + q, yk, rk, c, t0 + (double)((kbase + q) * ks) * dt, doppler);
@@ -456,6 +462,13 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi_back(WalkerC* 
   const double taui = 0.5 * (1.0 - cospi((double)lane / 31.0));
   double* f = fs + wq * 5 * 32;
   bool fail = !state_finite(y);
+  if (!fail) {
+    // knot nk from the start state; each segment then writes its knots
+    // kend - 1 .. kend - K (the last is the next segment's start)
+    double r[5];
+    ak_rhs_v(s, y.v_hi, y.e_hi, r[0], r[1], r[2], r[3], r[4]);
+    if (lane == 0) write_knot(kn + nk, y, r, c, t0 + (double)(nk * ks) * dt, doppler);
+  }
   const int64_t nseg = n / seg;
   bool warm = false;
   double dv_prev = 0.0, de_prev = 0.0, f0v_prev = 0.0, f0e_prev = 0.0;
@@ -507,7 +520,7 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi_back(WalkerC* 
       for (int q = 0; q < 5; ++q) f[q * 32 + lane] = r[q];
       __syncwarp();
       bool anybad = false;
-      for (int q0 = 0; q0 <= K; q0 += 32) {
+      for (int q0 = 1; q0 <= K; q0 += 32) {
         const int q = q0 + lane;
         bool bad = false;
         OrbState yk = y;
@@ -524,8 +537,8 @@ __global__ void __launch_bounds__(32 * kOrbitWarps) k1_orbit_mcpi_back(WalkerC* 
           comp_add(yk.p_hi, yk.p_lo, H * sm[2]);
           comp_add(yk.g_hi, yk.g_lo, H * sm[3]);
           comp_add(yk.a_hi, yk.a_lo, H * sm[4]);
-          bad = q > 0 && !state_finite(yk);
-          if (q < K && !bad) {
+          bad = !state_finite(yk);
+          if (!bad) {
             double rk[5];
             ak_rhs_v(s, yk.v_hi, yk.e_hi, rk[0], rk[1], rk[2], rk[3], rk[4]);
             write_knot(kn + kend - q, yk, rk, c, t0 + (double)((kend - q) * ks) * dt, doppler);

@@ -595,78 +595,92 @@ __device__ __forceinline__ void fit3(T f0, T fh, T f1, T* q) {
 constexpr double kPatternFitDtMax64 = 64.0;     // [s]; fit error < 2e-12 below
 constexpr double kPatternFitDtMaxM = 1024.0;    // [s]; fit error < 1e-7 below
 
+// FP64 kernel: one CTA per segment of kSegF = 1024 samples (four tiles of
+// 256; each thread evaluates its offset in the four tiles in turn), so the
+// Bessel amplitude fit is made once per 1024 samples (its error over that
+// span is ~1e-14 of the amplitudes) and the set-up's FP64 work, ~6 % of the
+// kernel's at one fit per tile, drops four-fold.
+constexpr int kSegF = 1024;
+
 __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
                                                         int64_t n, double dt, double t0, int ks, int n_max,
                                                         double2* __restrict__ z, int unit_scale, int exact_f,
                                                         const double* __restrict__ bc, const double* __restrict__ ifact,
                                                         const double* __restrict__ lisa) {
-  __shared__ IvD iv[kTile / 64];
+  constexpr int kTiles = kSegF / kTile;
+  __shared__ IvD iv[kSegF / 64];
   __shared__ double bnode[3 * 32 * 3];
   __shared__ double bq[32 * 9];
-  __shared__ double fn[4][4];   // the four patterns at the four fit nodes
-  __shared__ double fq[4][4];   // their cubics in t / 256
+  __shared__ double fn[kTiles][4][4];   // the four patterns at the four fit nodes of each tile
+  __shared__ double fq[kTiles][4][4];   // their cubics in (t mod 256) / 256
   __shared__ double2 ex[kExpLen];
   __shared__ Geo<double> g;
   const int wk = blockIdx.y;
   const WalkerC& C = wcs[wk];
   const int64_t nk = n / ks;
   const Knot* kn = knots + (int64_t)wk * (nk + 1);
-  const int64_t j0 = (int64_t)blockIdx.x * kTile;
+  const int64_t j0 = (int64_t)blockIdx.x * kSegF;
   const int64_t kfirst = j0 / ks;
-  const int ni = ks >= kTile ? 1 : kTile / ks;
+  const int ni = ks >= kSegF ? 1 : kSegF / ks;
   const int t = threadIdx.x;
   const double h = (double)ks * dt;
   const double scale = unit_scale ? C.gd.amp_scale : 1.0;
   if (t < ni) build_iv(kn[kfirst + t], kn[kfirst + t + 1], h, iv[t]);
-  if (t >= 224 && t < 228 && !exact_f) {
-    const int q = t - 224;
-    antenna_fixed<double>(C.gd, lisa[blockIdx.x * 8 + 2 * q], lisa[blockIdx.x * 8 + 2 * q + 1], scale, fn[q]);
+  if (t >= 224 && t < 224 + 4 * kTiles && !exact_f) {   // node q of tile tt
+    const int i = t - 224, tt = i / 4, q = i % 4;
+    const double* L = lisa + ((int64_t)blockIdx.x * kTiles + tt) * 8 + 2 * q;
+    antenna_fixed<double>(C.gd, L[0], L[1], scale, fn[tt][q]);
   }
   if (t == 160) g = C.gd;
   for (int i = t; i < kExpLen; i += kTile) ex[i] = g_exp512[i];
   __syncthreads();
-  if (t >= 224 && t < 228 && !exact_f) {
-    const int q = t - 224;
-    fit_cubic4<double>(fn[0][q], fn[1][q], fn[2][q], fn[3][q], fq[q]);
+  if (t >= 224 && t < 224 + 4 * kTiles && !exact_f) {   // pattern q of tile tt
+    const int i = t - 224, tt = i / 4, q = i % 4;
+    fit_cubic4<double>(fn[tt][0][q], fn[tt][1][q], fn[tt][2][q], fn[tt][3][q], fq[tt][q]);
   }
-  const int span = tile_span(j0, C.j_plunge);
+  const int64_t jplunge = C.j_plunge;
+  const int span = tile_span(j0, jplunge, kSegF);
   tile_harmonics<double, IvD>(iv, ni, j0, kfirst, ks, n_max, span, bnode, bq, bc, ifact);
   __syncthreads();
   const double inv_span = 1.0 / (double)span;
-
-  const int64_t j = j0 + t;
-  double2 out = make_double2(0.0, 0.0);
-  if (j < C.j_plunge) {
-    const int ki = ks >= kTile ? 0 : t >> (__ffs(ks) - 1);   // ks: a power of two
-    const double s = (double)(j - (kfirst + ki) * ks) * (1.0 / (double)ks);
-    const IvD& v = iv[ki];
-    // phases in cycles over the knot interval (|f| < 2^20: the table index
-    // wraps them, no reduction to one cycle is needed)
-    const double fph = poly3<double>(v.ph, s);
-    const double fgm = poly3<double>(v.gm, s);
-    const double fal = poly3<double>(v.al, s);
-    const double A = poly3<double>(v.am, s);
-    double F[4];
-    if (!exact_f) {
-      const double so = (double)t * (1.0 / kTile);
+  const int lks = __ffs(ks) - 1;   // ks: a power of two
+  const double so = (double)t * (1.0 / kTile);
+#pragma unroll 1
+  for (int tt = 0; tt < kTiles; ++tt) {
+    const int r = tt * kTile + t;   // offset in the segment
+    const int64_t j = j0 + r;
+    double2 out = make_double2(0.0, 0.0);
+    if (j < jplunge) {
+      const int ki = ks >= kSegF ? 0 : r >> lks;
+      const double s = (double)(j - (kfirst + ki) * ks) * (1.0 / (double)ks);
+      const IvD& v = iv[ki];
+      // phases in cycles over the knot interval (|f| < 2^20: the table index
+      // wraps them, no reduction to one cycle is needed)
+      const double fph = poly3<double>(v.ph, s);
+      const double fgm = poly3<double>(v.gm, s);
+      const double fal = poly3<double>(v.al, s);
+      const double A = poly3<double>(v.am, s);
+      double F[4];
+      if (!exact_f) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) F[q] = cubic_at<double>(fq[q], so);
-    } else {
-      double f = (t0 + (double)j * dt) / kYear;
-      f -= floor(f);
-      double sb, cb;
-      sincospi(2.0 * f, &sb, &cb);
-      antenna_fixed<double>(g, cb, sb, scale, F);
+        for (int q = 0; q < 4; ++q) F[q] = cubic_at<double>(fq[tt][q], so);
+      } else {
+        double f = (t0 + (double)j * dt) / kYear;
+        f -= floor(f);
+        double sb, cb;
+        sincospi(2.0 * f, &sb, &cb);
+        antenna_fixed<double>(g, cb, sb, scale, F);
+      }
+      double sph, cph, s2g, c2g, sa, ca;
+      sincos2pi_tab(fph, ex, sph, cph);
+      sincos2pi_tab(fgm, ex, s2g, c2g);
+      sincos2pi_tab(fal, ex, sa, ca);
+      double hI, hII;
+      channels(g, cph, sph, c2g, s2g, ca, sa, A, (double)r * inv_span, bq, n_max, F, hI, hII);
+      out = make_double2(hI, hII);
     }
-    double sph, cph, s2g, c2g, sa, ca;
-    sincos2pi_tab(fph, ex, sph, cph);
-    sincos2pi_tab(fgm, ex, s2g, c2g);
-    sincos2pi_tab(fal, ex, sa, ca);
-    double hI, hII;
-    channels(g, cph, sph, c2g, s2g, ca, sa, A, (double)t * inv_span, bq, n_max, F, hI, hII);
-    out = make_double2(hI, hII);
+    z[(int64_t)wk * n + j] = out;
   }
-  z[(int64_t)wk * n + j] = out;
 }
 
 // Mixed kernel: one CTA per segment of kSegM = 1024, 2048 or 4096 samples
@@ -814,7 +828,7 @@ void launch_wave(const Knot* knots, const WalkerC* wc, int w, int64_t n, double 
     const int ww = w - w0 < kMaxGridY ? w - w0 : kMaxGridY;
     const Knot* kn = knots + (int64_t)w0 * (nk + 1);
     if (o.precision == 0) {
-      dim3 grid((unsigned)(n / kTile), (unsigned)ww);
+      dim3 grid((unsigned)(n / kSegF), (unsigned)ww);
       k2_wave_f64<<<grid, kTile, 0, s>>>(kn, wc + w0, n, dt, t0, o.ks, o.n_max, (double2*)z + (int64_t)w0 * n,
                                          unit_scale ? 1 : 0, dt > kPatternFitDtMax64 ? 1 : 0, bt.c64, bt.f64, lisa);
     } else {

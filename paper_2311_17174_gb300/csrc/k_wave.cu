@@ -435,6 +435,40 @@ __device__ __forceinline__ void response(const Geo<T>& g, T c2gt, T s2gt, T ca, 
   hII = F[2] * Hp + F[3] * Hx;
 }
 
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+// response<float> for two samples at once, every quantity a (sample A,
+// sample B) pair and every step one paired FP32 instruction.  gk: the
+// walker's geometry constants as duplicated pairs,
+//   gk[0] = (pe1 pe1 -pe2 -pe2), gk[1] = (qe1 qe1 -qe2 -qe2),
+//   gk[2] = (cpe1 cpe1 cpe2 cpe2), gk[3] = (cqe1 cqe1 cqe2 cqe2),
+//   gk[4] = (-spS -spS -sqS -sqS).
+__device__ __forceinline__ void response_pair(const float4* gk, float2 c2gt, float2 s2gt, float2 ca, float2 sa,
+                                              float2 A, float2 Cs, float2 Ss, float2 Rs, const float2 F[4],
+                                              float2& hI, float2& hII) {
+  const float4 k0 = gk[0], k1 = gk[1], k2 = gk[2], k3 = gk[3], k4 = gk[4];
+  const float2 z1r = __ffma2_rn(sa, lo2(k0), __fmul2_rn(ca, hi2(k0)));
+  const float2 z1i = __ffma2_rn(sa, lo2(k1), __fmul2_rn(ca, hi2(k1)));
+  const float2 z2r = __ffma2_rn(ca, lo2(k2), __ffma2_rn(sa, hi2(k2), lo2(k4)));
+  const float2 z2i = __ffma2_rn(ca, lo2(k3), __ffma2_rn(sa, hi2(k3), hi2(k4)));
+  const float2 X = __ffma2_rn(Cs, c2gt, neg2(__fmul2_rn(Ss, s2gt)));
+  const float2 Y = __ffma2_rn(Cs, s2gt, __fmul2_rn(Ss, c2gt));
+  const float2 a = __fmul2_rn(A, __fadd2_rn(Rs, X));
+  const float2 b = __fmul2_rn(A, __fadd2_rn(Rs, neg2(X)));
+  const float2 y = __fmul2_rn(__fadd2_rn(A, A), Y);
+  const float2 u1 = __ffma2_rn(z1r, z1r, neg2(__fmul2_rn(z1i, z1i)));
+  const float2 u2 = __ffma2_rn(z2r, z2r, neg2(__fmul2_rn(z2i, z2i)));
+  const float2 u3 = __ffma2_rn(z1r, z2r, neg2(__fmul2_rn(z1i, z2i)));
+  const float2 Hp = __ffma2_rn(a, u1, __ffma2_rn(b, u2, __fmul2_rn(y, u3)));
+  const float2 v3 = __ffma2_rn(z1r, z2i, __fmul2_rn(z1i, z2r));
+  const float2 w = __ffma2_rn(a, __fmul2_rn(z1r, z1i), __fmul2_rn(b, __fmul2_rn(z2r, z2i)));
+  const float2 Hx = __ffma2_rn(y, v3, __fadd2_rn(w, w));
+  hI = __ffma2_rn(F[0], Hp, __fmul2_rn(F[1], Hx));
+  hII = __ffma2_rn(F[2], Hp, __fmul2_rn(F[3], Hx));
+}
+
 // Channels at one sample (harmonic sums, then the response).
 __device__ __forceinline__ void channels(const Geo<double>& g, double cph, double sph, double c2gt, double s2gt,
                                          double ca, double sa, double A, double st, const double* __restrict__ bq,
@@ -709,9 +743,11 @@ __global__ void __launch_bounds__(kTile, 3) k2_wave_mixed(const Knot* __restrict
   constexpr int kTiles = kSegM / kTile;
   static_assert(kTiles % 4 == 0, "tiles are processed in fours");
   __shared__ float fn[kTiles][4][4];   // the four patterns at the fit nodes of each tile
-  __shared__ float fq[kTiles][4][4];   // their cubics in (t mod 256) / 256
+  // their cubics in (t mod 256) / 256, tiles paired: fq2[m][q][k] = (tile 2m, tile 2m + 1)
+  __shared__ __align__(16) float2 fq2[kTiles / 2][4][4];
   __shared__ float cs0[kTiles][2];     // cos, sin phibar at each tile's start
   __shared__ Geo<float> g;
+  __shared__ float4 gk[5];             // response_pair's duplicated geometry constants
   __shared__ int64_t jplunge;
   __shared__ int cheb_s;
   const int wk = blockIdx.y;
@@ -734,14 +770,24 @@ __global__ void __launch_bounds__(kTile, 3) k2_wave_mixed(const Knot* __restrict
     }
   }
   if (t == 224) {
-    g = C.gf;
+    const Geo<float>& G = C.gf;
+    g = G;
+    gk[0] = make_float4(G.pe1, G.pe1, -G.pe2, -G.pe2);
+    gk[1] = make_float4(G.qe1, G.qe1, -G.qe2, -G.qe2);
+    gk[2] = make_float4(G.cpe1, G.cpe1, G.cpe2, G.cpe2);
+    gk[3] = make_float4(G.cqe1, G.cqe1, G.cqe2, G.cqe2);
+    gk[4] = make_float4(-G.spS, -G.spS, -G.sqS, -G.sqS);
     jplunge = C.j_plunge;
     cheb_s = C.e0 < 0.5;
   }
   __syncthreads();
   if (t >= 128 && t < 128 + 4 * kTiles) {   // pattern q of tile tt
     const int i = t - 128, tt = i / 4, q = i % 4;
-    fit_cubic4<float>(fn[tt][0][q], fn[tt][1][q], fn[tt][2][q], fn[tt][3][q], fq[tt][q]);
+    float cf[4];
+    fit_cubic4<float>(fn[tt][0][q], fn[tt][1][q], fn[tt][2][q], fn[tt][3][q], cf);
+    float* o = reinterpret_cast<float*>(&fq2[tt >> 1][q][0]) + (tt & 1);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o[2 * k] = cf[k];
   }
   const int span = tile_span(j0, jplunge, kSegM);
   const bool cheb = cheb_s != 0;   // per walker (uniform in the CTA)
@@ -773,16 +819,24 @@ __global__ void __launch_bounds__(kTile, 3) k2_wave_mixed(const Knot* __restrict
     __sincosf(kTwoPiF * fgm, &s2g, &c2g);
     __sincosf(kTwoPiF * fal, &sa, &ca);
   };
-  // the four patterns at offset t of tile tt
+  // the four patterns at offset t of tiles tt (even) and tt + 1, paired
   const float so = (float)t * (1.f / kTile);
-  auto patterns = [&](int tt, float F[4]) {
+  const float2 so2 = make_float2(so, so);
+  auto patterns2 = [&](int tt, float2 F[4]) {
     if (!exact_f) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) F[q] = cubic_at<float>(fq[tt][q], so);
+      for (int q = 0; q < 4; ++q) {
+        const float2* c = fq2[tt >> 1][q];
+        F[q] = __ffma2_rn(__ffma2_rn(__ffma2_rn(c[3], so2, c[2]), so2, c[1]), so2, c[0]);
+      }
     } else {
-      float sd, cd;
+      float sd, cd, FA[4], FB[4];
       __sincosf(kTwoPiF * dphib * (float)t, &sd, &cd);
-      antenna_fixed<float>(g, cs0[tt][0] * cd - cs0[tt][1] * sd, cs0[tt][1] * cd + cs0[tt][0] * sd, scale, F);
+      antenna_fixed<float>(g, cs0[tt][0] * cd - cs0[tt][1] * sd, cs0[tt][1] * cd + cs0[tt][0] * sd, scale, FA);
+      antenna_fixed<float>(g, cs0[tt + 1][0] * cd - cs0[tt + 1][1] * sd, cs0[tt + 1][1] * cd + cs0[tt + 1][0] * sd,
+                           scale, FB);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) F[q] = make_float2(FA[q], FB[q]);
     }
   };
   // four samples per thread (tiles tt..tt+3, offset t): the amplitude
@@ -805,15 +859,15 @@ __global__ void __launch_bounds__(kTile, 3) k2_wave_mixed(const Knot* __restrict
     float2 Cs[2], Ss[2], Rs[2];
     harmonic_sums4(c1, s1, st, bq, n_max, cheb, Cs, Ss, Rs);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int p = i >> 1;
-      const float cs = (i & 1) ? Cs[p].y : Cs[p].x, ss = (i & 1) ? Ss[p].y : Ss[p].x, rs = (i & 1) ? Rs[p].y : Rs[p].x;
-      float c2g, s2g, ca, sa, A, F[4], hI, hII;
-      resp_in(r[i], c2g, s2g, ca, sa, A);
-      patterns(tt + i, F);
-      response<float>(g, c2g, s2g, ca, sa, A, cs, ss, rs, F, hI, hII);
-      const int64_t j = j0 + r[i];
-      z[(int64_t)wk * n + j] = j < jplunge ? make_float2(hI, hII) : make_float2(0.f, 0.f);
+    for (int p = 0; p < 2; ++p) {   // samples r[2p] (x) and r[2p + 1] (y)
+      float2 c2g, s2g, ca, sa, A, F[4], hI, hII;
+      resp_in(r[2 * p], c2g.x, s2g.x, ca.x, sa.x, A.x);
+      resp_in(r[2 * p + 1], c2g.y, s2g.y, ca.y, sa.y, A.y);
+      patterns2(tt + 2 * p, F);
+      response_pair(gk, c2g, s2g, ca, sa, A, Cs[p], Ss[p], Rs[p], F, hI, hII);
+      const int64_t ja = j0 + r[2 * p], jb = j0 + r[2 * p + 1];
+      z[(int64_t)wk * n + ja] = ja < jplunge ? make_float2(hI.x, hII.x) : make_float2(0.f, 0.f);
+      z[(int64_t)wk * n + jb] = jb < jplunge ? make_float2(hI.y, hII.y) : make_float2(0.f, 0.f);
     }
   }
 }

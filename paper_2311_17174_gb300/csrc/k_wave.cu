@@ -731,7 +731,7 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
 // exact_f: exact patterns per sample (long sample intervals), dphib: the
 // LISA orbital phase step per sample [cycles] for them.  No FP64 instruction
 // runs per thread: e0 is tested once per CTA.
-template <int kSegM>
+template <int kSegM, bool kOneIv>
 __global__ void __launch_bounds__(kTile, 3) k2_wave_mixed(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
                                                           int64_t n, int exact_f, float dphib, int ks, int n_max,
                                                           float2* __restrict__ z, int unit_scale,
@@ -800,17 +800,20 @@ __global__ void __launch_bounds__(kTile, 3) k2_wave_mixed(const Knot* __restrict
   // per-sample inputs: the orbital phase (for the harmonic sums) first, the
   // response's angles and amplitude after the sums (fewer registers live
   // across the harmonic loop)
-  auto orb = [&](int r, float& cph, float& sph) {
-    const int ki = ks >= kSegM ? 0 : r >> lks;
-    const int tau = r - ki * ks;
+  // knot interval ki and offset tau in it of sample r; with K_s >= four
+  // tiles (kOneIv) the four samples of a pass share the interval of the
+  // first, so its record is read once for the four
+  auto interval = [&](const int (&r)[4], int i, int& ki, int& tau) {
+    ki = ks >= kSegM ? 0 : (kOneIv ? r[0] : r[i]) >> lks;
+    tau = r[i] - ki * ks;
+  };
+  auto orb = [&](int ki, int tau, float& cph, float& sph) {
     const float s = (float)tau * inv_ks;
     const IvM& v = iv[ki];
     const float fph = phase_fx(v.ph_base, v.ph_inc, v.ph_c, tau, s);
     __sincosf(kTwoPiF * fph, &sph, &cph);
   };
-  auto resp_in = [&](int r, float& c2g, float& s2g, float& ca, float& sa, float& A) {
-    const int ki = ks >= kSegM ? 0 : r >> lks;
-    const int tau = r - ki * ks;
+  auto resp_in = [&](int ki, int tau, float& c2g, float& s2g, float& ca, float& sa, float& A) {
     const float s = (float)tau * inv_ks;
     const IvM& v = iv[ki];
     const float fgm = phase_fx(v.gm_base, v.gm_inc, v.gm_c, tau, s);   // 2 gamma~
@@ -843,15 +846,17 @@ __global__ void __launch_bounds__(kTile, 3) k2_wave_mixed(const Knot* __restrict
   // coefficients of each harmonic are loaded once for all four
 #pragma unroll 1
   for (int tt = 0; tt < kTiles; tt += 4) {
-    int r[4];
+    int r[4], ki[4], tau[4];
     float2 c1[2], s1[2], st[2];
 #pragma unroll
     for (int i = 0; i < 4; ++i) r[i] = (tt + i) * kTile + t;
 #pragma unroll
+    for (int i = 0; i < 4; ++i) interval(r, i, ki[i], tau[i]);
+#pragma unroll
     for (int p = 0; p < 2; ++p) {
       float ca_, sa_, cb_, sb_;
-      orb(r[2 * p], ca_, sa_);
-      orb(r[2 * p + 1], cb_, sb_);
+      orb(ki[2 * p], tau[2 * p], ca_, sa_);
+      orb(ki[2 * p + 1], tau[2 * p + 1], cb_, sb_);
       c1[p] = make_float2(ca_, cb_);
       s1[p] = make_float2(sa_, sb_);
       st[p] = make_float2((float)r[2 * p] * inv_span, (float)r[2 * p + 1] * inv_span);
@@ -861,8 +866,8 @@ __global__ void __launch_bounds__(kTile, 3) k2_wave_mixed(const Knot* __restrict
 #pragma unroll
     for (int p = 0; p < 2; ++p) {   // samples r[2p] (x) and r[2p + 1] (y)
       float2 c2g, s2g, ca, sa, A, F[4], hI, hII;
-      resp_in(r[2 * p], c2g.x, s2g.x, ca.x, sa.x, A.x);
-      resp_in(r[2 * p + 1], c2g.y, s2g.y, ca.y, sa.y, A.y);
+      resp_in(ki[2 * p], tau[2 * p], c2g.x, s2g.x, ca.x, sa.x, A.x);
+      resp_in(ki[2 * p + 1], tau[2 * p + 1], c2g.y, s2g.y, ca.y, sa.y, A.y);
       patterns2(tt + 2 * p, F);
       response_pair(gk, c2g, s2g, ca, sa, A, Cs[p], Ss[p], Rs[p], F, hI, hII);
       const int64_t ja = j0 + r[2 * p], jb = j0 + r[2 * p + 1];
@@ -896,12 +901,17 @@ void launch_wave(const Knot* knots, const WalkerC* wc, int w, int64_t n, double 
       float2* zz = (float2*)z + (int64_t)w0 * n;
       const IvM* iv = (const IvM*)ivs + (int64_t)w0 * nk;
       const int us = unit_scale ? 1 : 0;
-      if (seg == 4096)
-        k2_wave_mixed<4096><<<grid, kTile, 0, s>>>(kn, wc + w0, n, ef, dpb, o.ks, o.n_max, zz, us, bt.c32, bt.f32, lisa, iv);
-      else if (seg == 2048)
-        k2_wave_mixed<2048><<<grid, kTile, 0, s>>>(kn, wc + w0, n, ef, dpb, o.ks, o.n_max, zz, us, bt.c32, bt.f32, lisa, iv);
-      else
-        k2_wave_mixed<1024><<<grid, kTile, 0, s>>>(kn, wc + w0, n, ef, dpb, o.ks, o.n_max, zz, us, bt.c32, bt.f32, lisa, iv);
+#define EMRI_WAVE_MIXED(SEG, ONE) \
+  k2_wave_mixed<SEG, ONE><<<grid, kTile, 0, s>>>(kn, wc + w0, n, ef, dpb, o.ks, o.n_max, zz, us, bt.c32, bt.f32, lisa, iv)
+      const bool one = o.ks >= 4 * kTile;   // one knot interval per pass of four samples
+      if (seg == 4096) {
+        if (one) EMRI_WAVE_MIXED(4096, true); else EMRI_WAVE_MIXED(4096, false);
+      } else if (seg == 2048) {
+        if (one) EMRI_WAVE_MIXED(2048, true); else EMRI_WAVE_MIXED(2048, false);
+      } else {
+        if (one) EMRI_WAVE_MIXED(1024, true); else EMRI_WAVE_MIXED(1024, false);
+      }
+#undef EMRI_WAVE_MIXED
     }
   }
 }

@@ -328,11 +328,12 @@ def serve_bench(ctx, dsets, precision: int, rate: float, duration: float, n_max:
 
 
 # DRAM bytes per sample of k2_wave_f64 from one ncu capture of the kernel
-# (64 walkers x 2^20 samples, n_max 20: 71.52 MB read + 1013.74 MB written;
-# profiles/ncu_k2_wave_f64_64w_2p20.md), scaled to a launch by the samples it
-# processes (the kernel's traffic is its 16-byte output per sample plus the
-# per-tile orbit records, both proportional to walkers x samples).
-K2_F64_DRAM_BYTES_PER_SAMPLE = (71.517e6 + 1013.742e6) / (64 * 2 ** 20)
+# (64 walkers x 2^20 samples, n_max 20: 69.54 MB read + 1013.18 MB written;
+# profiles/ncu_k2_wave_f64_64w_2p20.md, the kernel with 1024-sample segments),
+# scaled to a launch by the samples it processes (the kernel's traffic is its
+# 16-byte output per sample plus the per-segment orbit records, both
+# proportional to walkers x samples).
+K2_F64_DRAM_BYTES_PER_SAMPLE = (69.544e6 + 1013.184e6) / (64 * 2 ** 20)
 
 
 def paper_bench(ctx, steps: int, warmup: int):

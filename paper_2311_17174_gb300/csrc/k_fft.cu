@@ -393,18 +393,6 @@ __device__ __forceinline__ void row_async(void* smem, const void* gmem, int byte
     cp_async16((char*)smem + 16 * i, (const char*)gmem + 16 * (size_t)i);
 }
 
-// the same for a compile-time size and thread count (the loop unrolls)
-template <int BYTES, int NTH>
-__device__ __forceinline__ void row_async_n(void* smem, const void* gmem) {
-  static_assert(BYTES % 16 == 0, "16-byte copies");
-  constexpr int V = BYTES / 16;
-#pragma unroll
-  for (int i0 = 0; i0 < V; i0 += NTH) {
-    const int i = i0 + (int)threadIdx.x;
-    if (V % NTH == 0 || i < V) cp_async16((char*)smem + 16 * i, (const char*)gmem + 16 * (size_t)i);
-  }
-}
-
 // Copy nrow rows of rowlen contiguous complex values (global row stride gs)
 // to/from a row-major shared tile, with LPT independent 16-byte accesses per
 // thread in flight (rowlen * sizeof(C2) must be a multiple of 16).
@@ -846,21 +834,22 @@ __global__ void __launch_bounds__((1 << LG) / 8)
                    const WalkerC* __restrict__ wcs, const float2* __restrict__ dtab, const float2* __restrict__ rtab,
                    const float2* __restrict__ dperm, const float* __restrict__ wperm, double2* __restrict__ partial,
                    const FdW* __restrict__ fdw) {
-  constexpr int N1 = 1 << LG, T = N1 / 8, PAD = N1 + N1 / 16;
+  constexpr int N1 = 1 << LG, T = N1 / 8;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* xb = reinterpret_cast<float2*>(smraw);   // stage exchange, padded
-  float2* ds = xb + PAD;                            // the row's g = w conj(D)
-  float2* ts = ds + N1;                             // the walker's delay factors
-  float* ws = reinterpret_cast<float*>(ts + N1);    // the row's weights
   __shared__ AccF red[T / 32];
   const int t = threadIdx.x;
   const int k2 = blockIdx.x, wk = blockIdx.y;
   const int64_t base = (int64_t)k2 * N1;
-  // the inner product's operands, asynchronously while the row is transformed
-  row_async_n<N1 * 8, T>(ds, dperm + base);
-  row_async_n<N1 * 8, T>(ts, dtab + (int64_t)wk * N1);
-  row_async_n<N1 * 4, T>(ws, wperm + base);
-  cp_async_commit();
+  // the inner product's operands, read where they are used (the row's
+  // dataset entries from L2, the walker's delay factors from L1/L2): shared
+  // memory holds only the exchange buffer (17 KB at 2048 points), and the
+  // registers, not shared memory, bound the CTAs per SM.  Staging the three
+  // rows in shared memory by cp.async (57 KB, three CTAs per SM) took
+  // 8.42 ms per 1024-walker 2^21 step against 6.67 ms.
+  const float2* ds = dperm + base;                  // the row's g = w conj(D)
+  const float2* ts = dtab + (int64_t)wk * N1;       // the walker's delay factors
+  const float* ws = wperm + base;                   // the row's weights
   const float2* row = y + (int64_t)wk * n + (int64_t)N1 * k2;
   float2 v[8];
 #pragma unroll
@@ -869,8 +858,6 @@ __global__ void __launch_bounds__((1 << LG) / 8)
   const float2 cnv = make_float2(wcs[wk].cnf[0], wcs[wk].cnf[1]);
   r8::stages8<LG, 0>(v, xb, tt, t);
   r8::last_stage<LG>(v, tt, t);
-  cp_async_wait<0>();
-  __syncthreads();
   // the thread's bins k1 = t + q T in plain FP32, then the compensated tree
   float zr = 0.f, zi = 0.f, shh = 0.f;
   FdW fd;
@@ -922,7 +909,7 @@ __global__ void __launch_bounds__((1 << LG) / 8)
 
 template <int LG>
 constexpr size_t r8_smem() {
-  return (size_t)((1 << LG) + (1 << LG) / 16) * sizeof(float2) + (size_t)(1 << LG) * (2 * sizeof(float2) + sizeof(float));
+  return (size_t)((1 << LG) + (1 << LG) / 16) * sizeof(float2);
 }
 
 // --------------------------------------------------------------- finalize

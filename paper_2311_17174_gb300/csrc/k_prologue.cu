@@ -184,6 +184,12 @@ __global__ void k0_prologue(const double* __restrict__ theta, int64_t ld, int w,
 // mult = 1 over k2 < n2).  fold_neg: the entries with 2 k > count also carry
 // exp(+2 pi i frac(N r)), the factor of the signed index k - N (negative
 // frequencies).
+// The FP32 tables take the fraction in fixed point: r as a 128-bit fraction,
+// m r mod 1 from two 64-bit integer products (exact), its top 32 bits as the
+// phase in [-1/2, 1/2) cycles, then the FP32 sincospif; no FP64 operation
+// per entry.  The FP64 tables take it in double-double and FP64 sincospi.
+__device__ void dd_to_fx128(dd x, unsigned long long& hi, unsigned long long& lo);
+
 template <typename C2>
 __global__ void k0_delay_table(const WalkerC* __restrict__ wc, int count, int mult, int fold_neg,
                                C2* __restrict__ tab) {
@@ -191,6 +197,24 @@ __global__ void k0_delay_table(const WalkerC* __restrict__ wc, int count, int mu
   const int wk = blockIdx.y;
   if (k1 >= count) return;
   const double rh = wc[wk].r_hi, rl = wc[wk].r_lo;
+  if constexpr (sizeof(C2) == 8) {
+    unsigned long long Rh, Rl;
+    dd_to_fx128(dd{rh, rl}, Rh, Rl);
+    const unsigned long long m = (unsigned long long)mult * (unsigned long long)k1;   // < 2^22
+    const unsigned long long ph = m * Rh + __umul64hi(m, Rl);                          // m r mod 1, Q0.64
+    const float f = (float)(int)(unsigned)(ph >> 32) * 2.3283064365386963e-10f;        // [-1/2, 1/2)
+    float sf, cf;
+    sincospif(2.f * f, &sf, &cf);
+    float vx = cf, vy = -sf;
+    if (fold_neg && 2 * k1 > count) {
+      const float cr = wc[wk].cnf[0], ci = wc[wk].cnf[1];
+      const float x = vx * cr - vy * ci;
+      vy = vx * ci + vy * cr;
+      vx = x;
+    }
+    tab[(int64_t)wk * count + k1] = make_float2(vx, vy);
+    return;
+  }
   double m = (double)mult * (double)k1;
   dd p = dd_add_d(two_prod(m, rh), m * rl);
   dd f = dd_frac(p);
@@ -204,8 +228,8 @@ __global__ void k0_delay_table(const WalkerC* __restrict__ wc, int count, int mu
     vx = x;
   }
   C2 v;
-  v.x = vx;
-  v.y = vy;
+  v.x = (decltype(v.x))vx;
+  v.y = (decltype(v.y))vy;
   tab[(int64_t)wk * count + k1] = v;
 }
 

@@ -317,3 +317,44 @@ def test_fixed_point_phase_wraps_mod_one(cycles_per_sample):
             exact = (c0 + c1 * tau / ks) % 1.0
             d = abs(got - exact)
             assert min(d, 1 - d) < 1e-9, (tau, got, exact)
+
+
+def dd_to_fx128(hi, lo):
+    """The kernels' double-double fraction -> 128-bit fixed point, replayed
+    in IEEE doubles (every step exact: scalings by 2^64, floor, and the
+    difference of a double and its floor)."""
+    two64 = 18446744073709551616.0
+    t = hi * two64
+    H = math.floor(t)
+    r = (t - H) + lo * two64
+    F = math.floor(r)
+    rem = r - F
+    return (int(H) + int(F)) % 2 ** 64, int(rem * two64) % 2 ** 64
+
+
+def test_fp32_delay_phase_in_fixed_point():
+    """FP32 delay tables: frac(m r) for m = mult * k < 2^22 from the 128-bit
+    fraction of r by two 64-bit products (m R_hi mod 2^64 plus the high word
+    of m R_lo), top 32 bits as a signed phase in [-1/2, 1/2) cycles.  Against
+    exact rational arithmetic the phase is within 2^-32 cycles (the
+    truncation to 32 bits) at every m."""
+    from fractions import Fraction
+    g = np.random.default_rng(11)
+    for _ in range(200):
+        hi = float(g.uniform(0.0, 1.0))
+        lo = float(g.uniform(-0.5, 0.5)) * math.ulp(hi)
+        if not (0.0 <= hi + lo < 1.0):
+            continue
+        Rh, Rl = dd_to_fx128(hi, lo)
+        r = Fraction(hi) + Fraction(lo)
+        assert abs(Fraction(Rh * 2 ** 64 + Rl, 2 ** 128) - r) <= Fraction(1, 2 ** 128)
+        for m in (1, 3, 1023, 1 << 20, (1 << 22) - 1, int(g.integers(1, 1 << 22))):
+            ph = (m * Rh + ((m * Rl) >> 64)) % 2 ** 64
+            top = ph >> 32
+            f = (top - 2 ** 32 if top >= 2 ** 31 else top) * 2.0 ** -32
+            exact = (m * r) % 1
+            if exact >= Fraction(1, 2):
+                exact -= 1
+            d = abs(Fraction(f) - exact)
+            d = min(d, 1 - d)   # on the circle
+            assert d <= Fraction(1, 2 ** 32) + Fraction(m + 1, 2 ** 128), (hi, lo, m, float(d))

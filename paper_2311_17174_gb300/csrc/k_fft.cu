@@ -270,6 +270,30 @@ __device__ __forceinline__ void dft_r(C2* a, int sign) {
     a[1] = csub(t, a[1]);
   } else if constexpr (R == 4) {
     dft4_inplace(a[0], a[1], a[2], a[3], sign);
+  } else if constexpr (R == 16) {
+    // even and odd halves (8-point transforms), then the W16^q combination
+    C2 e[8], o[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      e[q] = a[2 * q];
+      o[q] = a[2 * q + 1];
+    }
+    dft_r<C2, 8>(e, sign);
+    dft_r<C2, 8>(o, sign);
+    // W16^q = (cos(pi q/8), -+sin(pi q/8)); q = 4 is -+i
+    const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173), h = T(0.70710678118654752440);
+    const T cq[8] = {T(1), c1, h, s1, T(0), -s1, -h, -c1};
+    const T sq[8] = {T(0), s1, h, c1, T(1), c1, h, s1};
+#pragma unroll
+    for (int q = 1; q < 8; ++q) {
+      if (q == 4) o[q] = mul_i(o[q], sign);
+      else o[q] = cmul(o[q], CT<C2>::make(cq[q], sign < 0 ? -sq[q] : sq[q]));
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      a[q] = cadd(e[q], o[q]);
+      a[q + 8] = csub(e[q], o[q]);
+    }
   } else {
     // even and odd halves, then the W8^q combination
     C2 e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
@@ -322,11 +346,16 @@ __device__ __forceinline__ void stage_r(C2* buf, int sign, const C2* __restrict_
           w[2] = cmul(w[1], w[1]);
           w[3] = cmul(w[2], w[1]);
         }
-        if constexpr (R == 8) {
+        if constexpr (R >= 8) {
           w[4] = cmul(w[2], w[2]);
           w[5] = cmul(w[4], w[1]);
           w[6] = cmul(w[4], w[2]);
           w[7] = cmul(w[4], w[3]);
+        }
+        if constexpr (R == 16) {
+          w[8] = cmul(w[4], w[4]);
+#pragma unroll
+          for (int q = 9; q < 16; ++q) w[q] = cmul(w[8], w[q - 8]);
         }
 #pragma unroll
         for (int q = 1; q < R; ++q) y[m][q] = cmul(y[m][q], w[q]);
@@ -345,17 +374,22 @@ __device__ __forceinline__ void stage_r(C2* buf, int sign, const C2* __restrict_
   __syncthreads();
 }
 
+// Radix-8 stages, then radix 4 (LG = 3k + 2) or, for LG = 3k + 1, one
+// radix-16 stage in place of the last radix-8 and a radix-2 stage (one
+// shared-memory round trip fewer; 2^4 alone keeps radix 8 + 2).
 template <typename C2, int LG, int NB, int NTH, int ST>
 __device__ __forceinline__ void r8_stages(C2* buf, int sign, const C2* __restrict__ ta) {
   constexpr int L = 1 << LG;
-  constexpr int N8 = LG / 3;
+  constexpr bool R16 = LG % 3 == 1 && LG >= 7;
+  constexpr int N8 = R16 ? LG / 3 - 1 : LG / 3;
   if constexpr (ST < N8) {
     stage_r<C2, 8, NB, NTH, L, (1 << (3 * ST))>(buf, sign, ta);
     r8_stages<C2, LG, NB, NTH, ST + 1>(buf, sign, ta);
   } else {
     constexpr int NS = 1 << (3 * N8);
     if constexpr (LG % 3 == 2) stage_r<C2, 4, NB, NTH, L, NS>(buf, sign, ta);
-    if constexpr (LG % 3 == 1) stage_r<C2, 2, NB, NTH, L, NS>(buf, sign, ta);
+    if constexpr (R16) stage_r<C2, 16, NB, NTH, L, NS>(buf, sign, ta);
+    if constexpr (LG % 3 == 1 && !R16) stage_r<C2, 2, NB, NTH, L, NS>(buf, sign, ta);
   }
 }
 

@@ -358,3 +358,60 @@ def test_fp32_delay_phase_in_fixed_point():
             d = abs(Fraction(f) - exact)
             d = min(d, 1 - d)   # on the circle
             assert d <= Fraction(1, 2 ** 32) + Fraction(m + 1, 2 ** 128), (hi, lo, m, float(d))
+
+
+def smem_stage(buf, R, L, NS, sign):
+    """One shared-memory Stockham stage of the FP32 tile transform, replayed
+    with the kernel's indexing (one transform, NB = 1): butterfly j reads
+    j + q L/R, multiplies slot q by w^q (w = W_{R NS}^k from the 4096-point
+    table at k 4096/(R NS), k = j mod NS; conjugated for the inverse), takes
+    the R-point DFT and writes slot q to (j / NS) NS R + k + q NS.  The
+    16-point DFT is the kernel's: two 8-point halves, the odd one times
+    W16^q from the cos/sin(pi q / 8) constants (q = 4: -+i)."""
+    Q = L // R
+    out = np.empty_like(buf)
+    ta = np.exp(-2j * np.pi * np.arange(4096) / 4096)
+    step = 4096 // (R * NS)
+
+    def dft(a):
+        n = np.arange(len(a))
+        return np.exp(sign * 2j * np.pi * np.outer(n, n) / len(a)) @ a
+
+    c1, s1, h = 0.92387953251128675613, 0.38268343236508977173, np.sqrt(0.5)
+    cq = [1, c1, h, s1, 0, -s1, -h, -c1]
+    sq = [0, s1, h, c1, 1, c1, h, s1]
+    for j in range(Q):
+        k = j & (NS - 1)
+        y = np.array([buf[j + q * Q] for q in range(R)])
+        if NS > 1:
+            w1 = ta[k * step] if sign < 0 else np.conj(ta[k * step])
+            y = y * w1 ** np.arange(R)
+        if R == 16:
+            e, o = dft(y[0::2]), dft(y[1::2])
+            for q in range(1, 8):
+                o[q] = o[q] * (-1j if sign < 0 else 1j) if q == 4 else \
+                    o[q] * complex(cq[q], -sq[q] if sign < 0 else sq[q])
+            y = np.concatenate([e + o, e - o])
+        else:
+            y = dft(y)
+        d = (j // NS) * NS * R + k
+        for q in range(R):
+            out[d + q * NS] = y[q]
+    return out
+
+
+@pytest.mark.parametrize("lg", [7, 10])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_smem_radix16_last_stage_equals_dft(lg, sign):
+    """FP32 tile transforms of 2^(3k+1) points (pass 1 at 128 and 1024 rows):
+    radix-8 stages, then one radix-16 stage instead of radix 8 + radix 2."""
+    L = 1 << lg
+    g = np.random.default_rng(lg)
+    x = g.standard_normal(L) + 1j * g.standard_normal(L)
+    b, ns = x.copy(), 1
+    for _ in range(lg // 3 - 1):
+        b = smem_stage(b, 8, L, ns, sign)
+        ns *= 8
+    b = smem_stage(b, 16, L, ns, sign)
+    ref = np.fft.fft(x) if sign < 0 else np.fft.ifft(x) * L
+    assert np.abs(b - ref).max() / np.abs(ref).max() < 1e-14

@@ -44,6 +44,12 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
+# walker groups whose orbits, waveforms and FFT passes overlap in the mixed
+# step: 0 = the library's default for mixed precision (by size: two groups
+# for the 1024-walker 2^21 step)
+MIXED_GROUPS = 0
+
+
 def parse():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -56,6 +62,8 @@ def parse():
     ap.add_argument("--cpu-walkers", type=int, default=0, help="oracle sample size (0: one per core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--mixed-groups", type=int, default=MIXED_GROUPS,
+                    help="walker groups of the pipelined mixed schedule (emri_ctx_set_pipeline; 1: sequential, 0: by size)")
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="serving measurement per precision (0: skip)")
     ap.add_argument("--multi-chains", type=int, default=64, help="uneven-batching leg: chains (0: skip)")
     ap.add_argument("--no-extra", action="store_true", help="skip the paper-workload and ensemble-step legs")
@@ -647,20 +655,30 @@ def main():
     # ---- mixed precision on the same walkers
     mixed = None
     if not args.no_mixed:
+        ctx.set_pipeline(emri.MIXED, args.mixed_groups)
         for _ in range(args.warmup):
             ctx.loglike_batch(ds, theta_dev, omix, lnl)
         torch.cuda.synchronize()
-        ctx.profile(True)   # timed steps only
         tm = time_steps(ctx, ds, theta_dev, omix, lnl, args.steps, 0, flush, barrier)
+        lm = lnl.cpu().numpy()
+        # per-kernel device times from the same step with its kernels in
+        # sequence (in the pipelined schedule a launch's events would also
+        # span the other streams' kernels running beside it)
+        ctx.set_pipeline(emri.MIXED, 1)
+        ctx.profile(True)
+        tseq = time_steps(ctx, ds, theta_dev, omix, lnl, args.steps, 0, flush, barrier)
         kt_mix = ctx.kernel_times()
         ctx.profile(False)
+        ctx.set_pipeline(emri.MIXED, args.mixed_groups)
+        assert np.array_equal(lnl.cpu().numpy(), lm), "pipelined and sequential mixed steps differ"
         mt = float(sum(tm))
         if world > 1:
             t = torch.tensor([mt], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             mt = float(t.item())
-        lm = lnl.cpu().numpy()
         mixed = {"value": W * world * args.steps / (mt / 1e3), "unit": "lnL/s", "ms_per_step": mt / args.steps,
+                 "pipeline_groups": args.mixed_groups or "by size (2 at 1024 walkers x 2^21)",
+                 "ms_per_step_sequential": float(sum(tseq)) / args.steps,
                  "dlnl_max_vs_fp64": float(np.max(np.abs(lm - lnl64))),
                  "kernels_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in kt_mix.items() if v[1]},
                  "roofline": mixed_roofline(kt_mix, W, wl.n, wl.n_max, args.steps)}

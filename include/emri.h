@@ -145,6 +145,31 @@ int emri_ctx_create(int device, size_t hbm_budget_bytes, emri_ctx** out);
  * context).  NULL is a no-op. */
 int emri_ctx_destroy(emri_ctx* ctx);
 
+/* Overlap of the likelihood's steps across walker groups (a scheduling
+ * choice with no counterpart in the paper, whose Sec. 3 evaluates the
+ * walkers' likelihoods independently).  The walkers of each wave of a call
+ * are split into `groups` groups of consecutive walkers.  The first group's
+ * orbits (step S1) run first, then every other walker's in one launch, on a
+ * context-owned stream; each group's waveform (S2-S4) runs on the caller's
+ * stream once its orbits are done, and its FFT passes and reduction (S5-S7)
+ * on a second context-owned stream once its waveform is written.  Both
+ * context streams have the device's highest priority, so a group's passes
+ * are dispatched ahead of the next group's waveform.  groups = 1 runs every
+ * step in order on the caller's stream.  Applies to emri_loglike_batch(_fd)
+ * and the stretch-step entry points of this precision (EMRI_FP64 or
+ * EMRI_MIXED), except on a stream that is being captured (those calls use
+ * 1).  Each walker is computed by the same kernels on the same data, so the
+ * results are bitwise the same for every `groups`.  Before the call returns,
+ * the caller's stream is made to wait for both context streams, so
+ * stream-ordered use of the outputs is safe as usual.  The context streams
+ * and 132 events are created at the first call that uses them (no device
+ * memory).  groups: 1..64, or 0 = by the call's size: 2 groups when each
+ * holds at least 2^30 samples (walkers of a wave x n), else 1; smaller
+ * groups lose more to the extra orbit launch and the stream hand-offs than
+ * the overlap gains.  Default 1 (FP64: every kernel is bound by the FP64
+ * pipe) and 0 (mixed).  EMRI_EINVAL otherwise. */
+int emri_ctx_set_pipeline(emri_ctx* ctx, int precision, int groups);
+
 /* Number of CUDA kernels the library has launched on this context so far
  * (host counter, incremented at each launch). */
 int emri_ctx_launches(const emri_ctx* ctx, int64_t* count);

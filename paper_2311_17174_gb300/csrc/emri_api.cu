@@ -257,50 +257,155 @@ int pick_wave(emri_ctx* ctx, const FftPlan& p, const OptsN& o, int w) {
   return std::min({wave, w, kMaxGridY});
 }
 
+int pipe_groups(emri_ctx* ctx, const OptsN& o, cudaStream_t s) {
+  const int g = ctx->pipe[o.precision ? 1 : 0];
+  if (g == 1) return 1;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 1;
+  return g;
+}
+
+// The context's two pipeline streams, both at the device's highest priority
+// (a group's FFT passes are dispatched as soon as its waveform is written,
+// ahead of the next group's waveform CTAs, so they fill the SMs the
+// FP32-bound waveform leaves; a low-priority FFT stream would queue behind
+// every waveform and overlap nothing), and the events of the schedule:
+// [0] fork, [1] first group's orbits done, [2] waveform done / FFT join,
+// [3] every orbit done,
+// [4 + (wave & 1) kMaxPipe + q] group q of a wave has left the series buffer.
+static int pipe_resources(emri_ctx* ctx) {
+  if (ctx->pstream[1]) return EMRI_OK;
+  int lo = 0, hi = 0;
+  CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  if (ctx->pev.empty()) ctx->pev.assign(4 + 2 * kMaxPipe, nullptr);
+  for (cudaEvent_t& e : ctx->pev)
+    if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  for (int i = 0; i < 2; ++i)
+    if (!ctx->pstream[i]) CK(cudaStreamCreateWithPriority(&ctx->pstream[i], cudaStreamNonBlocking, hi));
+  return EMRI_OK;
+}
+
 // The launch sequence of steps S0-S7 for W walkers of one dataset.
+// pipe = 1: every step on s, in order (pipe = 0: 1 or 2 by the call's
+// size, below).  pipe = G > 1: the prologue, delay
+// tables and LISA tiles on s, then each wave's walkers in G groups whose
+// orbits run on the context's first pipeline stream, waveforms on s, and FFT
+// passes and reduction on the second, so group g's waveform (FP32- or
+// FP64-pipe bound) overlaps group g-1's passes (bound by memory latency and
+// issue), and the orbits of groups 1.. run beside group 0's waveform.  Each walker is computed by the same kernels on the same data
+// either way, so the results are bitwise the same for every G.
 int run_loglike(emri_ctx* ctx, const emri_dataset* ds, const double* theta, int64_t ld, int w, const OptsN& o,
                 int wave, const LoglikeBufs& b, double* lnl, double* dh, double* hh, uint32_t* status,
-                cudaStream_t s, int64_t* launches, const FdW* fd) {
+                cudaStream_t s, int64_t* launches, const FdW* fd, int pipe) {
   const FftPlan& p = ds->plan;
   const bool f32 = o.precision != 0;
   const size_t cs = f32 ? sizeof(float2) : sizeof(double2);
   int64_t nl = 0;
   Profiler* pf = &ctx->prof;
-  { KTimer t(pf, EMRI_K_PROLOGUE, s); launch_prologue(theta, ld, w, p.n, ds->dt, o, ctx->gl, b.wc, s); }
-  { KTimer t(pf, EMRI_K_DELAY, s); launch_delay_table(b.wc, w, p.n1, p.n2, f32, b.dtab, b.rtab, s); }
-  { KTimer t(pf, EMRI_K_ORBIT, s); launch_orbit(b.wc, w, p.n, ds->dt, ds->t0, o, b.knots, ctx->mcpi, s); }
-  launch_lisa_tiles(p.n, ds->t0, ds->dt, b.lisa, s);
-  nl += 5;
-  if (f32) {
-    KTimer t(pf, EMRI_K_ORBIT, s);
-    launch_intervals_mixed(b.knots, w, p.n, o.ks, ds->dt, b.ivs, s);
-    nl += 1;
-  }
   const int64_t nk = p.n / o.ks;
   const void* dperm = f32 ? (const void*)ds->g_perm32 : (const void*)ds->g_perm;
   const void* wperm = f32 ? (const void*)ds->w_perm32 : (const void*)ds->w_perm;
   const double dh_scale = f32 ? 1.0 / (ds->d_scale * ds->w_scale) : 1.0;
   const double hh_scale = f32 ? 1.0 / ds->w_scale : 1.0;
-  for (int i0 = 0; i0 < w; i0 += wave) {
-    const int ww = std::min(wave, w - i0);
+  // steps S5-S7 of walkers [j0, j0 + gw), whose series start at zg
+  auto passes = [&](int j0, int gw, char* zg, cudaStream_t st) {
+    { KTimer t(pf, EMRI_K_FFT1, st); launch_fft_pass1(zg, gw, p, f32, -1, ctx->tw, st); }
     {
-      KTimer t(pf, EMRI_K_WAVE, s);
-      launch_wave(b.knots + (size_t)i0 * (nk + 1), b.wc + i0, ww, p.n, ds->dt, ds->t0, o, b.z, false, ctx->bt, b.lisa,
-                  b.ivs + (size_t)i0 * nk * kIvMBytes, s);
-    }
-    { KTimer t(pf, EMRI_K_FFT1, s); launch_fft_pass1(b.z, ww, p, f32, -1, ctx->tw, s); }
-    {
-      KTimer t(pf, EMRI_K_FFT2_IP, s);
-      launch_fft_pass2_ip(b.z, ww, p, f32, ctx->tw, b.wc + i0, b.dtab + (size_t)i0 * p.n1 * cs,
-                          b.rtab + (size_t)i0 * p.n2 * cs, dperm, wperm, b.partial + (size_t)i0 * p.n2, s,
-                          fd ? fd + i0 : nullptr);
+      KTimer t(pf, EMRI_K_FFT2_IP, st);
+      launch_fft_pass2_ip(zg, gw, p, f32, ctx->tw, b.wc + j0, b.dtab + (size_t)j0 * p.n1 * cs,
+                          b.rtab + (size_t)j0 * p.n2 * cs, dperm, wperm, b.partial + (size_t)j0 * p.n2, st,
+                          fd ? fd + j0 : nullptr);
     }
     {
-      KTimer t(pf, EMRI_K_FINALIZE, s);
-      launch_finalize(b.partial + (size_t)i0 * p.n2, p.n2, b.wc + i0, ww, dh_scale, hh_scale, lnl + i0,
-                      dh ? dh + i0 : nullptr, hh ? hh + i0 : nullptr, status ? status + i0 : nullptr, s);
+      KTimer t(pf, EMRI_K_FINALIZE, st);
+      launch_finalize(b.partial + (size_t)j0 * p.n2, p.n2, b.wc + j0, gw, dh_scale, hh_scale, lnl + j0,
+                      dh ? dh + j0 : nullptr, hh ? hh + j0 : nullptr, status ? status + j0 : nullptr, st);
     }
+  };
+  auto wave_of = [&](int j0, int gw, char* zg, cudaStream_t st) {
+    KTimer t(pf, EMRI_K_WAVE, st);
+    launch_wave(b.knots + (size_t)j0 * (nk + 1), b.wc + j0, gw, p.n, ds->dt, ds->t0, o, zg, false, ctx->bt,
+                b.lisa, b.ivs + (size_t)j0 * nk * kIvMBytes, st);
+  };
+  auto orbit_of = [&](int j0, int gw, cudaStream_t st) {
+    { KTimer t(pf, EMRI_K_ORBIT, st); launch_orbit(b.wc + j0, gw, p.n, ds->dt, ds->t0, o, b.knots + (size_t)j0 * (nk + 1), ctx->mcpi, st); }
+    if (f32) {
+      KTimer t(pf, EMRI_K_ORBIT, st);
+      launch_intervals_mixed(b.knots + (size_t)j0 * (nk + 1), gw, p.n, o.ks, ds->dt, b.ivs + (size_t)j0 * nk * kIvMBytes,
+                             st);
+    }
+  };
+  if (pipe == 0) {
+    // by size: two groups when each holds at least 2^30 samples (walkers x
+    // n).  On the 1024-walker 2^21 mixed step two groups take 44.5 against
+    // 45.3 ms; smaller groups lose more to the extra orbit launch and the
+    // stream hand-offs than the overlap gains (8 walkers: 2.5 -> 4.4 ms).
+    const int64_t w1 = std::min(wave, w);
+    pipe = w1 * p.n >= ((int64_t)1 << 31) ? 2 : 1;
+  }
+  { KTimer t(pf, EMRI_K_PROLOGUE, s); launch_prologue(theta, ld, w, p.n, ds->dt, o, ctx->gl, b.wc, s); }
+  { KTimer t(pf, EMRI_K_DELAY, s); launch_delay_table(b.wc, w, p.n1, p.n2, f32, b.dtab, b.rtab, s); }
+  if (pipe <= 1) {
+    orbit_of(0, w, s);
+    launch_lisa_tiles(p.n, ds->t0, ds->dt, b.lisa, s);
+    nl += f32 ? 6 : 5;
+    for (int i0 = 0; i0 < w; i0 += wave) {
+      const int ww = std::min(wave, w - i0);
+      wave_of(i0, ww, b.z, s);
+      passes(i0, ww, b.z, s);
+      nl += 4;
+    }
+  } else {
+    int rc = pipe_resources(ctx);
+    if (rc) return rc;
+    launch_lisa_tiles(p.n, ds->t0, ds->dt, b.lisa, s);
     nl += 4;
+    cudaStream_t so = ctx->pstream[0], sf = ctx->pstream[1];
+    cudaEvent_t* ev = ctx->pev.data();
+    cudaEventRecord(ev[0], s);
+    cudaStreamWaitEvent(so, ev[0], 0);
+    cudaStreamWaitEvent(sf, ev[0], 0);
+    // orbits: the first group's alone, then every other walker's in one
+    // launch that runs beside the first group's waveform (an orbit launch
+    // takes about as long for a few walkers as for a thousand: each walker's
+    // integration is sequential in time, so one launch per group would queue
+    // G of those latencies)
+    const int w1 = std::min(wave, w);
+    const int g0 = (w1 + std::min(pipe, w1) - 1) / std::min(pipe, w1);
+    orbit_of(0, g0, so);
+    cudaEventRecord(ev[1], so);
+    if (g0 < w) orbit_of(g0, w - g0, so);
+    cudaEventRecord(ev[3], so);
+    nl += f32 ? 2 : 1;
+    if (g0 < w) nl += f32 ? 2 : 1;
+    int prev_gs = 0, prev_g = 0;   // group size and count of the previous wave
+    for (int i0 = 0, wv = 0; i0 < w; i0 += wave, ++wv) {
+      const int ww = std::min(wave, w - i0);
+      const int G = std::min(pipe, ww);
+      const int gs = (ww + G - 1) / G;
+      cudaEvent_t* gone = ev + 4 + (wv & 1) * kMaxPipe;        // this wave's groups
+      cudaEvent_t* gone_prev = ev + 4 + ((wv + 1) & 1) * kMaxPipe;
+      for (int q = 0, j0 = i0; j0 < i0 + ww; ++q, j0 += gs) {
+        const int gw = std::min(gs, i0 + ww - j0);
+        cudaStreamWaitEvent(s, j0 == 0 ? ev[1] : ev[3], 0);   // the group's orbits
+        if (wv > 0) {   // the previous wave's groups that used this part of the series buffer
+          const int qa = (j0 - i0) / prev_gs, qb = std::min((j0 - i0 + gw - 1) / prev_gs, prev_g - 1);
+          for (int r = qa; r <= qb; ++r) cudaStreamWaitEvent(s, gone_prev[r], 0);
+        }
+        char* zg = b.z + (size_t)(j0 - i0) * p.n * cs;
+        wave_of(j0, gw, zg, s);
+        cudaEventRecord(ev[2], s);
+        cudaStreamWaitEvent(sf, ev[2], 0);
+        passes(j0, gw, zg, sf);
+        cudaEventRecord(gone[q], sf);
+        nl += 4;
+      }
+      prev_gs = gs;
+      prev_g = (ww + gs - 1) / gs;
+    }
+    cudaStreamWaitEvent(s, ev[3], 0);
+    cudaEventRecord(ev[2], sf);
+    cudaStreamWaitEvent(s, ev[2], 0);
   }
   if (launches) *launches = nl;
   cudaError_t e = cudaGetLastError();
@@ -470,8 +575,21 @@ extern "C" int emri_ctx_destroy(emri_ctx* c) {
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
   c->ws.destroy(c);
   if (c->tables) cudaFree(c->tables);
+  for (cudaStream_t st : c->pstream)
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t e : c->pev)
+    if (e) cudaEventDestroy(e);
   cudaStreamDestroy(c->stream);
   delete c;
+  return EMRI_OK;
+}
+
+extern "C" int emri_ctx_set_pipeline(emri_ctx* c, int precision, int groups) {
+  if (!c) return set_err(EMRI_EINVAL, "NULL context");
+  if (precision != EMRI_FP64 && precision != EMRI_MIXED) return set_err(EMRI_EINVAL, "unknown precision %d", precision);
+  if (groups < 0 || groups > kMaxPipe) return set_err(EMRI_EINVAL, "groups must be in [0, %d]", kMaxPipe);
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->pipe[precision == EMRI_MIXED ? 1 : 0] = groups;
   return EMRI_OK;
 }
 
@@ -769,7 +887,7 @@ extern "C" int emri_loglike_batch(emri_ctx* ctx, const emri_dataset* ds, const d
   LoglikeBufs b;
   loglike_layout(ds->plan, o, w, wave, &cv, &b);
   int64_t nl = 0;
-  rc = run_loglike(ctx, ds, theta, w, w, o, wave, b, lnl, dh, hh, status, s, &nl);
+  rc = run_loglike(ctx, ds, theta, w, w, o, wave, b, lnl, dh, hh, status, s, &nl, nullptr, pipe_groups(ctx, o, s));
   ctx->ws.release(s);
   ctx->launches += nl;
   return rc;
@@ -810,7 +928,7 @@ extern "C" int emri_loglike_batch_fd(emri_ctx* ctx, const emri_dataset* ds, cons
   launch_fdprop(theta, w, w, ds->n, ds->dt, o, fd->q_m, fd->q_t, fd->f_star, fd->coef_dev, w, fdw, s);
   int64_t nl = 1;
   int64_t nr = 0;
-  rc = run_loglike(ctx, ds, theta, w, w, o, wave, b, lnl, dh, hh, status, s, &nr, fdw);
+  rc = run_loglike(ctx, ds, theta, w, w, o, wave, b, lnl, dh, hh, status, s, &nr, fdw, pipe_groups(ctx, o, s));
   ctx->ws.release(s);
   ctx->launches += nl + nr;
   return rc;

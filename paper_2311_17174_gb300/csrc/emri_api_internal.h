@@ -92,6 +92,9 @@ struct KTimer {
   }
 };
 
+// most walker groups of a pipelined likelihood call (emri_ctx_set_pipeline)
+constexpr int kMaxPipe = 64;
+
 // autotuned schedule of one (n, n_max, precision) shape
 struct Plan {
   int ks = 0;
@@ -122,6 +125,14 @@ struct emri_ctx {
   emri::Profiler prof;
   std::map<std::tuple<int64_t, int, int>, emri::Plan> plans;   // (n, n_max, precision)
   std::map<int64_t, int> fft_split;                             // n -> n2 for new datasets
+  // pipelined likelihood schedule (emri_ctx_set_pipeline): walker groups
+  // per wave by precision (1 = the steps in sequence on the caller's
+  // stream, 0 = by the call's size), the two context streams it adds
+  // (orbits; FFT passes and reduction) and its events, created at the first
+  // pipelined call
+  int pipe[2] = {1, 0};
+  cudaStream_t pstream[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> pev;
 };
 
 struct emri_dataset {
@@ -148,7 +159,10 @@ size_t loglike_layout(const FftPlan& p, const OptsN& o, int w, int wave, Carve* 
 int pick_wave(emri_ctx* ctx, const FftPlan& p, const OptsN& o, int w);
 int run_loglike(emri_ctx* ctx, const emri_dataset* ds, const double* theta, int64_t ld, int w, const OptsN& o,
                 int wave, const LoglikeBufs& b, double* lnl, double* dh, double* hh, uint32_t* status,
-                cudaStream_t s, int64_t* launches, const FdW* fd = nullptr);
+                cudaStream_t s, int64_t* launches, const FdW* fd = nullptr, int pipe = 1);
+// walker groups for a likelihood call on stream s: the context's setting for
+// the precision (0: by the call's size), 1 while s is being captured
+int pipe_groups(emri_ctx* ctx, const OptsN& o, cudaStream_t s);
 int ctx_plan_wave(emri_ctx* ctx, int64_t n, const OptsN& o);
 int ctx_plan_ks(emri_ctx* ctx, int64_t n, const OptsN& o);
 void serve_shutdown(emri_ctx* ctx);

@@ -175,7 +175,8 @@ int stretch_run(emri_ctx* ctx, const emri_dataset* ds, double* theta, double* ln
       launch_fdprop(y, m, m, ds->n, ds->dt, o, fd->q_m, fd->q_t, fd->f_star, fd->coef_dev + a0, w, fdw, s);
       nl += 1;
     }
-    rc = run_loglike(ctx, ds, y, m, m, o, std::min(wave, m), b, lly, nullptr, nullptr, sty, s, &nl, fdw);
+    rc = run_loglike(ctx, ds, y, m, m, o, std::min(wave, m), b, lly, nullptr, nullptr, sty, s, &nl, fdw,
+                     pipe_groups(ctx, o, s));
     k_stretch_accept<<<gb, tb, 0, s>>>(theta, lnp, w, a0, m, y, zs, lly, sty, u, sa, accepted);
     nl += 2;
   }

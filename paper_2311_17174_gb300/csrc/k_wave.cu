@@ -719,8 +719,9 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
 
 // Mixed kernel: one CTA per segment of kSegM = 1024, 2048 or 4096 samples
 // (tiles of 256, four per pass of the sample loop: each thread evaluates the
-// samples at its offset in four tiles at once, three CTAs per SM at up to 85
-// registers), so the Bessel amplitude
+// samples at its offset in four tiles at once, four CTAs per SM at 64
+// registers: as fast as three at 78 alone, and one CTA's registers then hold
+// a pass-2 CTA of the pipelined schedule), so the Bessel amplitude
 // fit -- a quadratic in time per harmonic, from three nodes -- is made once
 // per segment.  The eccentricity moves by ~1e-4 relative per 256 samples, and
 // the fit's error grows as the cube of the segment: ~5e-14 of the amplitudes
@@ -732,7 +733,7 @@ __global__ void __launch_bounds__(kTile, 2) k2_wave_f64(const Knot* __restrict__
 // LISA orbital phase step per sample [cycles] for them.  No FP64 instruction
 // runs per thread: e0 is tested once per CTA.
 template <int kSegM, bool kOneIv>
-__global__ void __launch_bounds__(kTile, 3) k2_wave_mixed(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
+__global__ void __launch_bounds__(kTile, 4) k2_wave_mixed(const Knot* __restrict__ knots, const WalkerC* __restrict__ wcs,
                                                           int64_t n, int exact_f, float dphib, int ks, int n_max,
                                                           float2* __restrict__ z, int unit_scale,
                                                           const float* __restrict__ bc, const float* __restrict__ ifact,

@@ -74,6 +74,7 @@ _SIGS = {
     "emri_version": (C.c_char_p, []),
     "emri_ctx_create": (C.c_int, [C.c_int, C.c_size_t, C.POINTER(C.c_void_p)]),
     "emri_ctx_destroy": (C.c_int, [C.c_void_p]),
+    "emri_ctx_set_pipeline": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "emri_ctx_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "emri_ctx_memory": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
     "emri_ctx_profile": (C.c_int, [C.c_void_p, C.c_int]),
@@ -206,6 +207,10 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_pipeline(self, precision: int, groups: int):
+        """Walker groups whose steps overlap on the device (emri_ctx_set_pipeline)."""
+        _check(self.lib.emri_ctx_set_pipeline(self.h, int(precision), int(groups)))
 
     def launches(self) -> int:
         v = C.c_int64()

@@ -109,6 +109,19 @@ template <typename C2>
 __device__ __forceinline__ C2 csub(C2 a, C2 b) {
   return CT<C2>::make(a.x - b.x, a.y - b.y);
 }
+// FP32: one paired (f32x2) instruction each (a - b as fma(b, -1, a), rounded
+// once).  Unlike scalar additions they are not contracted with a preceding
+// product into one FMA, so the FP32 tile transforms round differently in the
+// last bit than with scalar forms; FP32 pass 1 takes 7.81 instead of 8.19 ms
+// per 1024-walker 2^21 step with them.
+template <>
+__device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) {
+  return __fadd2_rn(a, b);
+}
+template <>
+__device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
 template <typename C2>
 __device__ __forceinline__ C2 conj_if(C2 a, int sign) {
   return sign > 0 ? CT<C2>::make(a.x, -a.y) : a;

@@ -58,6 +58,18 @@ def test_no_device_fails_loudly(lib_path):
     assert ei.value.code == emri.ECUDA
 
 
+def test_context_calls_reject_a_null_context(lib_path):
+    """Entry points that take a context check it before touching a device:
+    EMRI_EINVAL and a message, with or without a GPU."""
+    from paper_2311_17174_gb300 import emri
+    lib = emri.load()
+    for call in (lambda: lib.emri_ctx_set_pipeline(None, emri.MIXED, 2),
+                 lambda: lib.emri_ctx_profile(None, 1),
+                 lambda: lib.emri_ctx_launches(None, None)):
+        assert call() == emri.EINVAL
+        assert lib.emri_last_error()
+
+
 def test_opts_default_roundtrip(lib_path):
     from paper_2311_17174_gb300 import emri
     o = emri.Opts()

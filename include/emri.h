@@ -193,7 +193,10 @@ enum emri_kernel {
 
 /* Enable (1) or disable (0) per-kernel timing on this context and reset the
  * accumulators.  While enabled, every launch of the likelihood path is
- * bracketed by CUDA events recorded on the stream it is launched on. */
+ * bracketed by CUDA events recorded on the stream it is launched on.  Under
+ * the pipelined schedule (emri_ctx_set_pipeline) kernels of different walker
+ * groups run at the same time, so a launch's interval also covers the
+ * kernels beside it; set groups to 1 for a per-kernel breakdown. */
 int emri_ctx_profile(emri_ctx* ctx, int enable);
 
 /* Wait for the recorded events and return, per enum emri_kernel, the summed

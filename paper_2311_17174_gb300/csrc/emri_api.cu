@@ -267,9 +267,9 @@ int pipe_groups(emri_ctx* ctx, const OptsN& o, cudaStream_t s) {
 
 // The context's two pipeline streams, both at the device's highest priority
 // (a group's FFT passes are dispatched as soon as its waveform is written,
-// ahead of the next group's waveform CTAs, so they fill the SMs the
-// FP32-bound waveform leaves; a low-priority FFT stream would queue behind
-// every waveform and overlap nothing), and the events of the schedule:
+// ahead of the next group's waveform CTAs; at normal priority the schedule
+// measured no faster than the sequential one), and the events of the
+// schedule:
 // [0] fork, [1] first group's orbits done, [2] waveform done / FFT join,
 // [3] every orbit done,
 // [4 + (wave & 1) kMaxPipe + q] group q of a wave has left the series buffer.
@@ -286,14 +286,14 @@ static int pipe_resources(emri_ctx* ctx) {
 }
 
 // The launch sequence of steps S0-S7 for W walkers of one dataset.
-// pipe = 1: every step on s, in order (pipe = 0: 1 or 2 by the call's
-// size, below).  pipe = G > 1: the prologue, delay
-// tables and LISA tiles on s, then each wave's walkers in G groups whose
-// orbits run on the context's first pipeline stream, waveforms on s, and FFT
-// passes and reduction on the second, so group g's waveform (FP32- or
-// FP64-pipe bound) overlaps group g-1's passes (bound by memory latency and
-// issue), and the orbits of groups 1.. run beside group 0's waveform.  Each walker is computed by the same kernels on the same data
-// either way, so the results are bitwise the same for every G.
+// pipe = 1: every step on s, in order (pipe = 0: 1 or 2 by the call's size,
+// below).  pipe = G > 1: the prologue, delay tables and LISA tiles on s,
+// then each wave's walkers in G groups whose orbits run on the context's
+// first pipeline stream, waveforms on s, and FFT passes and reduction on the
+// second, so group g's waveform can run beside group g-1's passes and the
+// orbits of groups 1.. beside group 0's waveform.  Each walker is computed
+// by the same kernels on the same data either way, so the results are
+// bitwise the same for every G.
 int run_loglike(emri_ctx* ctx, const emri_dataset* ds, const double* theta, int64_t ld, int w, const OptsN& o,
                 int wave, const LoglikeBufs& b, double* lnl, double* dh, double* hh, uint32_t* status,
                 cudaStream_t s, int64_t* launches, const FdW* fd, int pipe) {
@@ -328,11 +328,11 @@ int run_loglike(emri_ctx* ctx, const emri_dataset* ds, const double* theta, int6
                 b.lisa, b.ivs + (size_t)j0 * nk * kIvMBytes, st);
   };
   auto orbit_of = [&](int j0, int gw, cudaStream_t st) {
-    { KTimer t(pf, EMRI_K_ORBIT, st); launch_orbit(b.wc + j0, gw, p.n, ds->dt, ds->t0, o, b.knots + (size_t)j0 * (nk + 1), ctx->mcpi, st); }
+    Knot* kj = b.knots + (size_t)j0 * (nk + 1);
+    { KTimer t(pf, EMRI_K_ORBIT, st); launch_orbit(b.wc + j0, gw, p.n, ds->dt, ds->t0, o, kj, ctx->mcpi, st); }
     if (f32) {
       KTimer t(pf, EMRI_K_ORBIT, st);
-      launch_intervals_mixed(b.knots + (size_t)j0 * (nk + 1), gw, p.n, o.ks, ds->dt, b.ivs + (size_t)j0 * nk * kIvMBytes,
-                             st);
+      launch_intervals_mixed(kj, gw, p.n, o.ks, ds->dt, b.ivs + (size_t)j0 * nk * kIvMBytes, st);
     }
   };
   if (pipe == 0) {

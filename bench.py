@@ -542,7 +542,7 @@ def mixed_roofline(kt, walkers: int, n: int, n_max: int, steps: int):
 
 def flop_model(n_max: int) -> float:
     """Algorithmic FP64 flops per sample of the factored harmonic sum and
-    response (see the design notes; an FMA counts two): 24 per harmonic
+    response (an FMA counts two): 24 per harmonic
     (rotation 6, three quadratic amplitudes 12, three accumulations 6) plus
     172 per sample (three phase cubics and x^(2/3) 28, three table sin/cos
     60, four antenna-pattern cubics 25, fixed-basis response and the two
